@@ -1,0 +1,133 @@
+"""Multigrid hierarchy, smoother, transfers, V-cycle and solve (oracle; test infrastructure only).
+
+Sect. 4.1 / Alg. 1 of the paper: multiplicative V(mu_pre, mu_post) cycles with
+omega-damped point Jacobi, u <- u + omega diag(A)^-1 (b - A u).  On a uniform
+grid with Galerkin coarse operators the FAS / HTMG coarse equation of Sect. 3
+reduces exactly to the correction scheme A_{l-1} e = R r, so the textbook
+recursive V-cycle written here is the paper's method.  The coarsest level is
+solved directly (dense FP64), as in the paper's exact coarse-grid variants.
+
+Hierarchy options:
+* transfer = 'dlinear' | 'boxmg' (Sect. 4.4)
+* coarse   = 'redisc'  | 'galerkin' (Sect. 4.3)
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+from . import boxmg, fem, galerkin
+from .spacetree import Spacetree
+
+
+@dataclass
+class LevelOps:
+    A: sp.csr_matrix            # operator over DoF rows/cols (slot numbering)
+    st: np.ndarray              # full 3^d stencils (slot x offset)
+    st_redisc: np.ndarray       # rediscretised 3^d stencils from the level's cell eps
+    diag: np.ndarray            # diagonal per slot (1 on non-DoF slots)
+    dof: np.ndarray
+    P: sp.csr_matrix | None = None      # prolongation from level l-1 to l
+    a_hat: np.ndarray | None = None     # A - A_redisc (coarse levels)
+    p_hat: np.ndarray | None = None     # P - P_dlin, 5^d per slot of level l-1 (stored on this object for transfer l-1 -> l)
+    extra: dict = field(default_factory=dict)
+
+
+class Hierarchy:
+    """Operators of a uniform spacetree hierarchy (levels ``coarsest`` .. max_level)."""
+
+    def __init__(self, tree: Spacetree, leaf_eps: dict[int, np.ndarray], transfer: str = "boxmg",
+                 coarse: str = "galerkin", omega: float = 0.6, nu1: int = 2, nu2: int = 2,
+                 coarsest: int = 1):
+        self.tree, self.omega, self.nu1, self.nu2, self.coarsest = tree, omega, nu1, nu2, coarsest
+        self.transfer, self.coarse = transfer, coarse
+        L = tree.max_level
+        self.L = L
+        self.eps = fem.coarse_eps(tree, leaf_eps)
+        self.ops: dict[int, LevelOps] = {}
+        for lv in range(L, coarsest - 1, -1):
+            level = tree.levels[lv]
+            A_full = fem.assemble(tree, lv, self.eps[lv])
+            st_r = fem.stencils(tree, lv, A_full)
+            if lv == L or coarse == "redisc":
+                A = fem.restrict_to_dofs(A_full, level.dof)
+                st = st_r
+                a_hat = None if lv == L else np.zeros_like(st_r)
+            else:
+                fine = self.ops[lv + 1]
+                A = galerkin.galerkin(fine.A, fine.P)
+                st = galerkin.full_coarse_stencils(tree, lv, A, st_r)
+                a_hat = galerkin.a_delta(st, st_r, level.dof)
+            diag = np.asarray(A.diagonal()).copy()
+            diag[~level.dof] = 1.0
+            ops = LevelOps(A=A, st=st, st_redisc=st_r, diag=diag, dof=level.dof, a_hat=a_hat)
+            self.ops[lv] = ops
+            if lv > coarsest:
+                ops.P = boxmg.prolongation(tree, lv, st, kind=transfer)
+                ops.p_hat = galerkin.p_delta(tree, lv, ops.P)
+        c = self.ops[coarsest]
+        idx = np.nonzero(c.dof)[0]
+        self._coarse_idx = idx
+        self._coarse_dense = c.A[idx][:, idx].toarray()
+
+    # --- single steps -----------------------------------------------------
+    def smooth(self, lv: int, u: np.ndarray, b: np.ndarray, nu: int) -> np.ndarray:
+        """nu omega-damped Jacobi sweeps (Alg. 1 smoothing update)."""
+        o = self.ops[lv]
+        u = u.copy()
+        for _ in range(nu):
+            r = b - o.A @ u
+            u = u + np.where(o.dof, self.omega * r / o.diag, 0.0)
+        return u
+
+    def residual(self, lv: int, u: np.ndarray, b: np.ndarray) -> np.ndarray:
+        o = self.ops[lv]
+        return np.where(o.dof, b - o.A @ u, 0.0)
+
+    def restrict(self, lv: int, r: np.ndarray) -> np.ndarray:
+        """b_{l-1} = R r_l with R = P^T."""
+        return self.ops[lv].P.T @ r
+
+    def prolong(self, lv: int, e: np.ndarray) -> np.ndarray:
+        """P e_{l-1} on level l."""
+        return self.ops[lv].P @ e
+
+    def coarse_solve(self, b: np.ndarray) -> np.ndarray:
+        u = np.zeros_like(b)
+        u[self._coarse_idx] = np.linalg.solve(self._coarse_dense, b[self._coarse_idx])
+        return u
+
+    # --- cycles -----------------------------------------------------------
+    def vcycle(self, u: np.ndarray, b: np.ndarray, lv: int | None = None) -> np.ndarray:
+        lv = self.L if lv is None else lv
+        if lv == self.coarsest:
+            return self.coarse_solve(b)
+        u = self.smooth(lv, u, b, self.nu1)
+        r = self.residual(lv, u, b)
+        bc = self.restrict(lv, r)
+        ec = self.vcycle(np.zeros_like(bc), bc, lv - 1)
+        u = u + np.where(self.ops[lv].dof, self.prolong(lv, ec), 0.0)
+        return self.smooth(lv, u, b, self.nu2)
+
+    def solve(self, b: np.ndarray, rel_tol: float = 1e-10, max_cycles: int = 100):
+        """V-cycles from u = 0 until ||r||_2 / ||r_0||_2 <= rel_tol; returns (u, history)."""
+        u = np.zeros_like(b)
+        r0 = np.linalg.norm(self.residual(self.L, u, b))
+        hist = [r0]
+        for _ in range(max_cycles):
+            if hist[-1] <= rel_tol * r0:
+                break
+            u = self.vcycle(u, b)
+            hist.append(np.linalg.norm(self.residual(self.L, u, b)))
+        return u, np.array(hist)
+
+    def direct(self, b: np.ndarray) -> np.ndarray:
+        """Exact discrete solution of the finest level (sparse direct solve)."""
+        o = self.ops[self.L]
+        idx = np.nonzero(o.dof)[0]
+        u = np.zeros_like(b)
+        u[idx] = spla.spsolve(o.A[idx][:, idx].tocsc(), b[idx])
+        return u
