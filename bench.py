@@ -1,0 +1,427 @@
+#!/usr/bin/env python
+"""Benchmark of the hybrid multigrid hot path on one GB300 (or N replicas).
+
+Workload (default): 2D -div(eps grad u) = f on the unit square, uniform k = 3
+spacetree of level 6 (729 x 729 cells, 529,984 DoFs), eps piecewise constant on a
+seeded 9 x 9 checkerboard with values {1, 1e-4}, f ~ U[-1, 1] per vertex, BoxMG
+prolongation / restriction with Galerkin coarse operators stored as FP64
+hierarchical deltas, damped Jacobi V(2,2) (omega 0.6), FP64 throughout, solved to
+a 1e-10 relative residual drop.
+
+A step = mg_setup (coarse coefficients, BoxMG, Galerkin R A P, deltas, coarsest
+Cholesky) + mg_solve, inputs resident in HBM.  Metric: DoF/s to the 1e-10 drop
+(DoFs x solves / time).  The mixed-precision form (FP64 refinement around FP32
+V-cycles reading BF16 deltas) is measured on the same workload and reported
+beside it.  L2 (126 MB) is flushed by writing a 512 MB buffer before every timed
+step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+# the CPU oracle legs run on one core; set before numpy loads its BLAS
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synthetic as syn  # noqa: E402
+
+WORKLOADS = {
+    "checker2d-l6": dict(dim=2, L=6, eps="checker", eps_seed=0, load_seed=1, transfer="boxmg",
+                         coarse="galerkin", tol=1e-10, max_cycles=3000,
+                         desc="2D level 6 (729^2 cells, 529,984 DoFs), 9x9 seeded checkerboard {1,1e-4}, "
+                              "BoxMG + Galerkin, V(2,2) omega 0.6, to 1e-10"),
+    "sin2d-l4": dict(dim=2, L=4, eps="const", eps_seed=0, load_seed=None, transfer="dlinear",
+                     coarse="redisc", tol=1e-8, max_cycles=200,
+                     desc="2D level 4 (81^2 cells, 6,400 DoFs), sin benchmark, geometric V(2,2), to 1e-8"),
+}
+
+FP64_PEAK_TFLOPS = 1.25  # nominal dense FP64 of a GB300 (2 FMA / clock / SM at ~2.07 GHz)
+FLOPS_PER_DOF_SWEEP_2D = 35  # FP64 flops per DoF of the finest 2D in-situ Jacobi sweep (division counted once)
+BYTES_PER_DOF_SWEEP_FP64 = 32  # u, b, eps read + u' written, 8 B each
+BYTES_PER_DOF_SWEEP_FP32 = 16
+
+
+def inputs(w):
+    L, d = w["L"], w["dim"]
+    if w["eps"] == "checker":
+        eps = syn.checkerboard_eps(L, d, seed=w["eps_seed"])
+    else:
+        eps = syn.constant_eps(L, d)
+    bf = syn.uniform_load(L, d, w["load_seed"]) if w["load_seed"] is not None else syn.sin_load(L, d)
+    return eps, bf
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            j = json.load(f)
+        return float(j.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            self.proc.wait(timeout=10)
+            self.f.close()
+
+    def summary(self):
+        if not self.proc or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def kernel_count(L, c, nu1, nu2, transfer, coarse, precision, cycles, outer, chunk):
+    """Kernels of ours launched by one mg_setup + mg_solve (memsets / copies excluded)."""
+    levels = L - c
+    per_cycle = levels * (nu1 + nu2 + 3) + 1  # sweeps, residual, restrict, prolong per level; coarse solve
+    setup = (levels + 1) + levels + levels * ((transfer == "boxmg") + (coarse == "galerkin")) + (levels + 1) + 2
+    if precision == "fp64":
+        return setup + 2 + cycles * (per_cycle + 2)
+    setup += (levels + 1) + levels * ((transfer == "boxmg") + (coarse == "galerkin"))
+    inner_chunks = max(1, math.ceil(cycles / max(chunk, 1)))
+    return setup + 2 + outer * 4 + cycles * per_cycle + inner_chunks * 2
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_ours(args):
+    import torch
+
+    import paper_1607_00648_gb300 as mg
+
+    world, rank, local = dist_setup()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_mod
+
+        dist = dist_mod
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    w = WORKLOADS[args.workload]
+    L, d = w["L"], w["dim"]
+    eps, bf = inputs(w)
+    grid = mg.Grid(d, L)
+    n_dofs = grid.info(L).n_dofs
+    eps_cat = grid.cells_to_concat({L: eps})
+    b = grid.to_slots(L, bf)
+    eps_dev = torch.from_numpy(eps_cat).to(dev)
+    b_dev = torch.from_numpy(b).to(dev)
+    u_dev = torch.zeros_like(b_dev)
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if dist:
+            dist.barrier()
+
+    def timed(H, K, W, prec):
+        res = None
+        for _ in range(W):
+            H.setup(eps_dev)
+            res = H.solve(u_dev, b_dev, rel_tol=w["tol"], max_cycles=w["max_cycles"])
+        total_ms, launches, stats = 0.0, 0, []
+        for _ in range(K):
+            flush.zero_()
+            barrier()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            H.setup(eps_dev)
+            res = H.solve(u_dev, b_dev, rel_tol=w["tol"], max_cycles=w["max_cycles"])
+            e1.record(stream)
+            torch.cuda.synchronize()
+            barrier()
+            total_ms += e0.elapsed_time(e1)
+            stats.append(res)
+            o = H.options
+            launches += kernel_count(L, o.coarsest_level, o.nu1, o.nu2, w["transfer"], w["coarse"], prec,
+                                     res["cycles"], res["outer_steps"], o.inner_cycles)
+        if dist:
+            t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            total_ms = float(t.item())
+        return total_ms, launches, stats
+
+    H64 = mg.Hierarchy(grid, transfer=w["transfer"], coarse=w["coarse"], precision="fp64")
+    Hmx = mg.Hierarchy(grid, transfer=w["transfer"], coarse=w["coarse"], precision="mixed_bf16")
+    with Clocks(torch.cuda.current_device()) as clk:
+        t64, launches64, st64 = timed(H64, args.steps, args.warmup, "fp64")
+        tmx, launchesmx, stmx = timed(Hmx, args.steps, args.warmup, "mixed")
+    clocks = clk.summary()
+    value = n_dofs * args.steps * world / (t64 / 1e3)
+    value_mx = n_dofs * args.steps * world / (tmx / 1e3)
+
+    # dominant kernel: finest-level FP64 in-situ Jacobi sweep (two sweeps per call, no copy)
+    H64.setup(eps_dev)
+    uu = torch.zeros_like(b_dev)
+    reps = 50
+    for _ in range(5):
+        H64.smooth(L, uu, b_dev, 2)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        H64.smooth(L, uu, b_dev, 2)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    sweep_s = e0.elapsed_time(e1) / 1e3 / (2 * reps)
+    Hmx.setup(eps_dev)
+    hbm_peak, peak_src = peaks()
+    flops = FLOPS_PER_DOF_SWEEP_2D * n_dofs
+    roofline = {"bound": "alu", "kernel": "k_sweep<2,double,0,Jacobi> (finest FP64 Jacobi sweep)",
+                "achieved": flops / sweep_s / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": flops / sweep_s / 1e12 / FP64_PEAK_TFLOPS,
+                "peak_source": "nominal FP64 of the recipe (no measured FP64 peak)",
+                "flops_per_dof": FLOPS_PER_DOF_SWEEP_2D, "launch_us": sweep_s * 1e6,
+                "hbm_equivalent": {"achieved": BYTES_PER_DOF_SWEEP_FP64 * n_dofs / sweep_s / 1e9,
+                                   "peak": hbm_peak, "unit": "GB/s",
+                                   "frac": BYTES_PER_DOF_SWEEP_FP64 * n_dofs / sweep_s / 1e9 / hbm_peak,
+                                   "peak_source": peak_src},
+                "traffic": None}
+
+    # end to end through the public API with host buffers
+    eps_h = torch.from_numpy(eps_cat).pin_memory()
+    b_h = torch.from_numpy(b).pin_memory()
+    u_h = torch.empty_like(b_h).pin_memory()
+    e2e_ms = 0.0
+    for i in range(args.warmup + args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        eps_dev.copy_(eps_h, non_blocking=True)
+        b_dev.copy_(b_h, non_blocking=True)
+        H64.setup(eps_dev)
+        H64.solve(u_dev, b_dev, rel_tol=w["tol"], max_cycles=w["max_cycles"])
+        u_h.copy_(u_dev, non_blocking=True)
+        torch.cuda.synchronize()
+        if i >= args.warmup:
+            e2e_ms += (time.perf_counter() - t0) * 1e3
+    if dist:
+        t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e = {"value": n_dofs * args.steps * world / (e2e_ms / 1e3), "unit": "DoF/s",
+           "h2d_bytes_per_step": int(eps_h.numel() * 8 + b_h.numel() * 8),
+           "d2h_bytes_per_step": int(u_h.numel() * 8)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(w, st64[-1]["cycles"])
+
+    if rank == 0:
+        out = {
+            "metric": "DoF/s to 1e-10 residual drop (FP64; mixed beside it)",
+            "value": value, "unit": "DoF/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t64 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "description": w["desc"], "dofs": n_dofs,
+                       "cycles_per_solve": st64[-1]["cycles"], "parallelism": f"replicas{world}",
+                       "l2": "flushed (512 MB write) before every timed step", "setup_included": True},
+            "mixed": {"value": value_mx, "unit": "DoF/s", "dtype": "f32 cycles + f64 refinement, bf16 deltas",
+                      "ms_per_step": tmx / args.steps, "inner_cycles": stmx[-1]["cycles"],
+                      "outer_steps": stmx[-1]["outer_steps"], "rel_residual": stmx[-1]["rel_residual"],
+                      "speedup_vs_fp64": value_mx / value},
+            "roofline": roofline, "e2e": e2e, "clocks": clocks,
+            "gpu_launches": launches64 + launchesmx,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(out))
+    if dist:
+        dist.destroy_process_group()
+
+
+def run_sweeps(args):
+    """Finest-level in-situ Jacobi sweeps alone on a 2D checkerboard grid of level
+    args.sweep_level (level 8: 6561^2 cells, 43M DoFs, vectors far larger than L2):
+    per-launch time of the FP64 and the FP32 sweep kernels and their roofline."""
+    import torch
+
+    import paper_1607_00648_gb300 as mg
+
+    torch.cuda.set_device(0)
+    L, d = args.sweep_level, 2
+    eps = syn.checkerboard_eps(L, d, seed=0)
+    grid = mg.Grid(d, L)
+    n_dofs = grid.info(L).n_dofs
+    eps_dev = torch.from_numpy(grid.cells_to_concat({L: eps})).cuda()
+    b64 = torch.from_numpy(grid.to_slots(L, syn.uniform_load(L, d, 1))).cuda()
+    H = mg.Hierarchy(grid, precision="mixed_bf16")
+    H.setup(eps_dev)
+    u64 = torch.zeros_like(b64)
+    b32 = b64.float()
+    u32 = torch.zeros_like(b32)
+    hbm, src = peaks()
+    out = {"workload": f"sweep2d-l{L}", "dofs": n_dofs}
+    for name, fn, u, bb, bpd in (("fp64", H.smooth, u64, b64, BYTES_PER_DOF_SWEEP_FP64),
+                                 ("fp32", H.smooth_f32, u32, b32, BYTES_PER_DOF_SWEEP_FP32)):
+        for _ in range(3):
+            fn(L, u, bb, 2)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = args.steps
+        e0.record()
+        for _ in range(reps):
+            fn(L, u, bb, 2)
+        e1.record()
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1e3 / (2 * reps)
+        out[name] = {"launch_us": t * 1e6, "GB/s": bpd * n_dofs / t / 1e9, "hbm_frac": bpd * n_dofs / t / 1e9 / hbm,
+                     "peak_source": src, "Gdof/s": n_dofs / t / 1e9}
+    print(json.dumps(out))
+
+
+def cpu_baseline(w, gpu_cycles, sample_cycles=15):
+    """The oracle as it stands on one host core: setup + a bounded number of V-cycles of
+    the full workload, extrapolated to the cycle count of the solve."""
+    from oracle import multigrid
+    from oracle import spacetree as stt
+
+    L, d = w["L"], w["dim"]
+    eps, bf = inputs(w)
+    t0 = time.perf_counter()
+    tree = stt.Spacetree(d, L)
+    O = multigrid.Hierarchy(tree, {L: eps}, transfer=w["transfer"], coarse=w["coarse"])
+    t_setup = time.perf_counter() - t0
+    b = tree.vertices_to_slots(L, bf)
+    u = np.zeros_like(b)
+    t0 = time.perf_counter()
+    for _ in range(sample_cycles):
+        u = O.vcycle(u, b)
+        np.linalg.norm(O.residual(L, u, b))
+    t_cycle = (time.perf_counter() - t0) / sample_cycles
+    n_dofs = int(tree.levels[L].dof.sum())
+    t_solve = t_setup + gpu_cycles * t_cycle
+    return {"value": n_dofs / t_solve, "unit": "DoF/s", "cores": 1, "kind": "oracle",
+            "sample": f"oracle setup + {sample_cycles} V(2,2) cycles of the full workload "
+                      f"({t_setup:.2f} s + {sample_cycles} x {t_cycle * 1e3:.1f} ms), extrapolated to "
+                      f"{gpu_cycles} cycles", "setup_s": t_setup, "cycle_s": t_cycle}
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    from oracle import multigrid
+    from oracle import spacetree as stt
+
+    w = WORKLOADS[args.workload]
+    L, d = w["L"], w["dim"]
+    eps, bf = inputs(w)
+    tree = stt.Spacetree(d, L)
+    b = tree.vertices_to_slots(L, bf)
+    n_dofs = int(tree.levels[L].dof.sum())
+    # cycles to the tolerance, once (untimed): the iteration is deterministic
+    O = multigrid.Hierarchy(tree, {L: eps}, transfer=w["transfer"], coarse=w["coarse"])
+    _, hist = O.solve(b, w["tol"], w["max_cycles"])
+    cycles = len(hist) - 1
+    sample = 5
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        O = multigrid.Hierarchy(tree, {L: eps}, transfer=w["transfer"], coarse=w["coarse"])
+        ts = time.perf_counter() - t0
+        u = np.zeros_like(b)
+        t1 = time.perf_counter()
+        for _ in range(sample):
+            u = O.vcycle(u, b)
+            np.linalg.norm(O.residual(L, u, b))
+        tc = (time.perf_counter() - t1) / sample
+        if i >= args.warmup:
+            times.append(ts + cycles * tc)
+    t = sum(times)
+    value = n_dofs * len(times) / t
+    out = {"impl": "reference", "metric": "DoF/s to 1e-10 residual drop (FP64; mixed beside it)",
+           "value": value, "unit": "DoF/s", "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": t / len(times) * 1e3, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": args.workload, "description": w["desc"], "dofs": n_dofs,
+                      "cycles_per_solve": cycles},
+           "cpu_baseline": {"value": value, "unit": "DoF/s", "cores": 1, "kind": "oracle",
+                            "sample": f"per step: oracle setup + {sample} V(2,2) cycles, extrapolated to "
+                                      f"{cycles} cycles"},
+           "e2e": {"value": value, "unit": "DoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="checker2d-l6", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline leg")
+    ap.add_argument("--sweep-level", type=int, default=0,
+                    help="time only the finest-level FP64 / FP32 sweeps on a 2D grid of this level")
+    args = ap.parse_args()
+    if args.sweep_level:
+        run_sweeps(args)
+    elif args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,257 @@
+/*
+ * mg.h -- C ABI of the GB300 quasi-matrix-free hybrid multigrid library (libmg.so).
+ *
+ * Implements the hot path of Weinzierl & Weinzierl, "Quasi-matrix-free hybrid
+ * multigrid on dynamically adaptive Cartesian grids" (arXiv:1607.00648): in-situ
+ * application of d-linear FEM stencils (9 points in 2D, 27 in 3D) in the damped
+ * Jacobi smoother, the residual, BoxMG prolongation / restriction and the
+ * Galerkin coarse-operator computation, every stored operator rebuilt on the fly
+ * as the rediscretised stencil plus a stored hierarchical delta (Sect. 5).
+ *
+ * Problem (eq. "pde" with v = 0):  -div(eps grad u) = f on (0,1)^d, u = 0 on the
+ * boundary, d in {2,3}, discretised on a k = 3 spacetree (Sect. 3).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Level layout.  Level l of the spacetree is stored as bricks: the level-l
+ *   descendants of one level-(l-m) cell, m = min(l,3) in 2D and min(l,2) in 3D,
+ *   so a brick has B = 3^m cells per axis.  Bricks follow the Peano curve of
+ *   their root cells (Sect. 3 / App. A: depth-first order = Peano curve);
+ *   inside a brick, vertex slots are lexicographic (x fastest) and padded to
+ *   slots_per_brick = roundup(B^d, 32).  Slot k of brick b holds the vertex at
+ *   brick_origin + lex(k).  A cell uses the slot of its lower-left vertex.
+ * Vectors.  A level vector (u, b, r, eps) is a device array of n_slots entries
+ *   in that order.  Only degree-of-freedom slots (EXISTS, not BOUNDARY, not
+ *   HANGING) carry unknowns; every call writes 0 to the other slots of its
+ *   outputs and requires 0 in the boundary slots of its inputs.
+ * Ownership.  The caller owns every pointer it passes (device pointers unless
+ *   the name says host); the library owns grid / hierarchy handles and all
+ *   internal device storage, released by the destroy calls (which accept NULL).
+ * Streams.  All device work is enqueued on the given cudaStream_t (passed as
+ *   void*, NULL = legacy default stream).  Only calls that return host values
+ *   (norm2_host, mg_solve) synchronise that stream.
+ * Errors.  Every call returns mg_status; no C++ exception crosses the ABI.  On
+ *   failure outputs are unspecified, handles stay valid, and mg_last_error()
+ *   returns a thread-local message.
+ */
+#ifndef MG_H
+#define MG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum mg_status {
+  MG_OK = 0,
+  MG_ERR_INVALID_ARG = 1,
+  MG_ERR_OOM = 2,
+  MG_ERR_CUDA = 3,
+  MG_ERR_NOT_CONVERGED = 4,
+  MG_ERR_DIVERGED = 5,
+  MG_ERR_NONFINITE = 6,
+  MG_ERR_INDEFINITE_COARSE = 7,
+  MG_ERR_TIMEOUT = 8,
+  MG_ERR_BUDGET = 9,
+  MG_ERR_UNSUPPORTED = 10
+} mg_status;
+
+/* Vertex flags (Sect. 3): a vertex is hanging if it has fewer than 2^d adjacent
+ * cells on its level, refined if all its adjacent cells are refined, else
+ * unrefined.  Boundary vertices carry the Dirichlet value 0. */
+#define MG_V_EXISTS 1u
+#define MG_V_BOUNDARY 2u
+#define MG_V_HANGING 4u
+#define MG_V_REFINED 8u
+/* Cell flags. */
+#define MG_C_EXISTS 1u
+#define MG_C_REFINED 2u
+
+typedef struct mg_grid mg_grid;
+typedef struct mg_hier mg_hier;
+
+typedef struct mg_level_info {
+  int32_t level;
+  int32_t dim;
+  int32_t brick_edge;      /* B, cells (= owned vertices) per brick axis */
+  int32_t slots_per_brick; /* roundup(B^d, 32) */
+  int64_t n_bricks;
+  int64_t n_slots;         /* n_bricks * slots_per_brick */
+  int64_t n_dofs;          /* EXISTS && !BOUNDARY && !HANGING */
+  int64_t n_cells;         /* existing cells of the level */
+  int64_t n_hanging;
+  int64_t slot_offset;     /* offset of this level in level-concatenated cell arrays */
+  double h;                /* mesh width 3^-level */
+} mg_level_info;
+
+/* ---------------------------------------------------------------- A1 grid */
+
+/* Build a k = 3 spacetree and flatten it into level arrays (Sect. 3, App. A).
+ * dim in {2,3}; 1 <= max_level <= 8 (2D) or 6 (3D).
+ * refine_masks: host array of max_level pointers (or NULL).  refine_masks[l]
+ *   (or NULL = refine every existing cell) is a byte mask over the complete
+ *   level l, lexicographic with x fastest, (3^l)^d entries; an existing level-l
+ *   cell is refined iff its byte is non-zero.  Host memory, read during the call.
+ * out: receives the grid handle (host object; destroy with mg_destroy_grid).
+ * Errors: MG_ERR_INVALID_ARG for bad dim / level / NULL out, MG_ERR_OOM. */
+mg_status mg_create_grid(int dim, int max_level, const uint8_t* const* refine_masks, mg_grid** out);
+
+/* Sizes of one level (0 <= level <= max_level).  info: host struct. */
+mg_status mg_grid_info(const mg_grid* grid, int level, mg_level_info* info);
+
+/* Host copies of the level tables (each pointer nullable; host memory, sizes in
+ * units of the element type):
+ *  coords        n_slots*d     global integer vertex coordinates (-1 on padding slots)
+ *  vflags        n_slots       MG_V_* bits
+ *  cflags        n_slots       MG_C_* bits of the cell owning the slot
+ *  nbr           n_slots*3^d   slot of vertex x+o, o in {-1,0,1}^d lexicographic (x
+ *                              fastest), -1 outside the domain or without a slot
+ *  cell_vertices n_slots*2^d   slots of the 2^d corners x+e, e in {0,1}^d lex, -1 if none
+ *  hang_idx      n_slots*2^d   HANGING slots: level-(l-1) slots of the corners of the
+ *                              coarse cell floor(x/3) with a non-zero d-linear weight
+ *                              (Sect. 3, rule 2), -1 elsewhere
+ *  hang_w        n_slots*2^d   the weights prod_i (r_i/3 or (3-r_i)/3), r = x mod 3; 0 where idx = -1
+ *  parent        n_slots       level-(l-1) slot at the same position (x = 0 mod 3), else -1
+ *                              (the injection I of Sect. 3, rule 1)
+ *  child         n_slots       level-(l+1) slot at position 3x, else -1
+ *  brick_roots   n_bricks*d    root-cell coordinates on level l-m, in Peano order
+ *  brick_nbr     n_bricks*3^d  brick index at root offset o, -1 if none */
+mg_status mg_grid_tables(const mg_grid* grid, int level, int32_t* coords, uint8_t* vflags, uint8_t* cflags,
+                         int32_t* nbr, int32_t* cell_vertices, int32_t* hang_idx, double* hang_w,
+                         int32_t* parent, int32_t* child, int32_t* brick_roots, int32_t* brick_nbr);
+
+void mg_destroy_grid(mg_grid* grid);
+
+/* ---------------------------------------------------------------- options */
+
+typedef enum mg_transfer { MG_TRANSFER_DLINEAR = 0, MG_TRANSFER_BOXMG = 1 } mg_transfer;
+typedef enum mg_coarse_op { MG_COARSE_REDISC = 0, MG_COARSE_GALERKIN = 1 } mg_coarse_op;
+typedef enum mg_precision {
+  MG_PREC_FP64 = 0,       /* everything in FP64, deltas stored in FP64 */
+  MG_PREC_MIXED_BF16 = 1, /* FP64 iterative refinement around FP32 V-cycles, deltas BF16 + FP32 scale */
+  MG_PREC_MIXED_FP16 = 2  /* same with FP16 codes */
+} mg_precision;
+
+typedef struct mg_options {
+  int32_t transfer;       /* mg_transfer (Sect. 4.4: BoxMG, or d-linear) */
+  int32_t coarse;         /* mg_coarse_op (Sect. 4.3: Galerkin R A P, or rediscretisation) */
+  int32_t precision;      /* mg_precision */
+  int32_t nu1, nu2;       /* pre / post smoothing steps of V(nu1, nu2) (Sect. 4.1) */
+  double omega;           /* Jacobi damping (Alg. 1 smoothing update) */
+  int32_t coarsest_level; /* level solved directly (FP64 Cholesky), 1 <= c < max_level */
+  int32_t inner_cycles;   /* mixed: FP32 V-cycles per refinement step */
+  int32_t use_graphs;     /* capture cycles in CUDA graphs */
+  int32_t reserved;
+} mg_options;
+
+void mg_default_options(mg_options* opt); /* BoxMG, Galerkin, FP64, V(2,2), omega 0.6, coarsest 1 */
+
+/* ---------------------------------------------------------------- hierarchy */
+
+/* Allocate the device-resident hierarchy of a grid (operators, deltas, work
+ * vectors) on the current device.  Allocation happens here only.
+ * Errors: MG_ERR_INVALID_ARG, MG_ERR_OOM, MG_ERR_UNSUPPORTED (adaptive grids with
+ * options this build does not handle). */
+mg_status mg_hier_create(const mg_grid* grid, const mg_options* opt, mg_hier** out);
+
+/* Setup (A8-A11): from leaf-cell coefficients eps (device, level-concatenated cell
+ * slots, n = sum of n_slots over levels 0..L, read at existing unrefined cells),
+ * compute coarse coefficients (mean of the 3^d children), BoxMG P per coarse
+ * vertex (App. C: one C(s) p = f solve per patch corner), Galerkin A_{l-1} =
+ * R A_l P with R = P^T (Sect. 4.3), the hierarchical deltas A_hat, P_hat
+ * (Sect. 5), their BF16/FP16 codes for the mixed path, and the FP64 Cholesky
+ * factor of the coarsest operator.  Enqueued on stream.
+ * Errors: MG_ERR_INDEFINITE_COARSE if a coarse stencil has a non-positive
+ * diagonal or the coarsest Cholesky fails (Sect. 4.3 definiteness check). */
+mg_status mg_setup(mg_hier* h, const double* eps, void* stream);
+
+/* ---------------------------------------------------------------- A3-A7 steps (FP64) */
+
+/* nu damped Jacobi sweeps u <- u + omega diag(A)^-1 (b - A u) on level (Alg. 1),
+ * in place on u (device, n_slots); b device, n_slots. */
+mg_status mg_smooth(mg_hier* h, int level, double* u, const double* b, int nu, void* stream);
+
+/* r = b - A u on level (device vectors).  norm2_host (nullable): receives
+ * sum over DoFs of r^2, computed by a fixed-order reduction; non-NULL
+ * synchronises the stream. */
+mg_status mg_residual(mg_hier* h, int level, const double* u, const double* b, double* r,
+                      double* norm2_host, void* stream);
+
+/* b_coarse = R r_fine, R = P^T (Sect. 4.4), from fine_level to fine_level-1. */
+mg_status mg_restrict(mg_hier* h, int fine_level, const double* r_fine, double* b_coarse, void* stream);
+
+/* u_fine += P e_coarse (Alg. 1 coarse-grid correction), fine_level-1 -> fine_level. */
+mg_status mg_prolong(mg_hier* h, int fine_level, const double* e_coarse, double* u_fine, void* stream);
+
+/* u on HANGING slots of level <- d-linear interpolant of level-1 (Sect. 3, rule 2). */
+mg_status mg_interpolate_hanging(mg_hier* h, int level, const double* u_coarse, double* u_fine, void* stream);
+
+/* FP32 counterparts on a mixed-precision hierarchy (the inner solver of the mixed
+ * path): same operations in FP32 arithmetic, coarse-level deltas decoded from
+ * their BF16/FP16 codes times the per-vertex FP32 scale, coefficients rounded to
+ * FP32.  u, b, r: device float vectors of n_slots.  MG_ERR_INVALID_ARG on an FP64
+ * hierarchy. */
+mg_status mg_smooth_f32(mg_hier* h, int level, float* u, const float* b, int nu, void* stream);
+mg_status mg_residual_f32(mg_hier* h, int level, const float* u, const float* b, float* r, double* norm2_host,
+                          void* stream);
+mg_status mg_vcycle_f32(mg_hier* h, float* u, const float* b, void* stream);
+
+/* ---------------------------------------------------------------- A12 cycles */
+
+/* One V(nu1, nu2) cycle on the finest level (correction scheme; on uniform
+ * grids with Galerkin coarse operators this is the FAS/HTMG cycle of Sect. 3 /
+ * Alg. 1).  u, b device finest-level vectors; u updated in place. FP64. */
+mg_status mg_vcycle(mg_hier* h, double* u, const double* b, void* stream);
+
+typedef struct mg_solve_stats {
+  int32_t cycles;          /* V-cycles run (mixed: FP32 inner cycles) */
+  int32_t outer_steps;     /* mixed: FP64 refinement steps; FP64: = cycles */
+  double rel_residual;     /* final ||r||_2 / ||r_0||_2 (FP64 residual) */
+  double r0_norm;          /* ||b - A u_0||_2 */
+  double solve_ms;         /* wall time of the call */
+  double* history;         /* host, nullable: per-check relative residuals */
+  int32_t history_capacity;
+  int32_t history_len;
+} mg_solve_stats;
+
+/* Solve A u = b from u = 0 on the finest level until ||r||/||r0|| <= rel_tol
+ * (Euclidean over DoFs) or max_cycles.  FP64: V-cycles.  Mixed: FP64 residual and
+ * update (iterative refinement) around inner_cycles FP32 V-cycles that read the
+ * BF16/FP16 deltas.  u, b device; stats host, nullable.  Synchronises stream.
+ * Returns MG_ERR_NOT_CONVERGED / MG_ERR_DIVERGED / MG_ERR_NONFINITE with u holding
+ * the last iterate. */
+mg_status mg_solve(mg_hier* h, double* u, const double* b, double rel_tol, int max_cycles,
+                   mg_solve_stats* stats, void* stream);
+
+/* ---------------------------------------------------------------- inspection (parity tests) */
+
+/* Reconstructed FP64 operator stencils of a level, A_redisc + A_hat
+ * (device, n_slots*3^d, offset-major: st[k*n_slots + slot]). */
+mg_status mg_get_stencils(mg_hier* h, int level, double* st, void* stream);
+
+/* FP64 deltas stored for a coarse level (device, nullable, offset-major):
+ * a_hat n_slots*3^d (Galerkin), p_hat n_slots*5^d (BoxMG P of level -> level+1,
+ * offsets in [-2,2]^d lexicographic). */
+mg_status mg_get_deltas(mg_hier* h, int level, double* a_hat, double* p_hat, void* stream);
+
+/* Mixed-path codes and scales of a coarse level (device, nullable, offset-major). */
+mg_status mg_get_codes(mg_hier* h, int level, uint16_t* a_codes, float* a_scale, uint16_t* p_codes,
+                       float* p_scale, void* stream);
+
+/* Standalone delta encoder (A10): for n rows of k FP64 entries (device, row-major
+ * delta[i*k + j]) write scale[i] = fl32(max_j |delta|) and codes = RNE to
+ * fmt (1 = BF16, 2 = FP16) of delta / scale formed in FP64 (device outputs). */
+mg_status mg_encode_deltas(int64_t n, int k, const double* delta, int fmt, uint16_t* codes, float* scale,
+                           void* stream);
+
+void mg_destroy_hier(mg_hier* h);
+
+const char* mg_last_error(void);
+const char* mg_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MG_H */

@@ -1,0 +1,167 @@
+// Device-side level descriptors, stencil rebuild and delta decoding shared by the
+// libmg CUDA translation units.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "../../include/mg.h"
+
+namespace mg {
+
+constexpr int kBlock = 256;  // threads per CTA of the brick kernels
+
+// Everything a kernel needs to address one level (passed by value).
+struct LevelDesc {
+  int dim, level, n, B, S, nb_axis;
+  int64_t n_bricks, n_slots;
+  double h;
+  const int32_t* brick_nbr;    // n_bricks * 3^d
+  const int32_t* brick_roots;  // n_bricks * d
+  const int32_t* brick_rank;   // nb_axis^d
+  const uint8_t* vflags;       // n_slots
+};
+
+__host__ __device__ constexpr int cpow(int b, int e) { return e == 0 ? 1 : b * cpow(b, e - 1); }
+
+// FEM element matrix of -div(eps grad u) for d-linear elements on a unit cube, by
+// Hamming distance of the two corners (Sect. 4): 2D 2/3, -1/6, -1/3; 3D 1/3, 0,
+// -1/12, -1/12 (times h in 3D, applied by the caller).
+__host__ __device__ constexpr double elem_k(int dim, int ham) {
+  return dim == 2 ? (ham == 0 ? 2.0 / 3.0 : ham == 1 ? -1.0 / 6.0 : -1.0 / 3.0)
+                  : (ham == 0 ? 1.0 / 3.0 : ham == 1 ? 0.0 : -1.0 / 12.0);
+}
+
+// d-linear interpolation weight (coarsening by three) at fine offset o in [-2,2]
+__host__ __device__ constexpr double wlin1(int o) { return o == 0 ? 1.0 : (o == 1 || o == -1) ? 2.0 / 3.0 : 1.0 / 3.0; }
+
+__device__ __forceinline__ bool is_dof(uint8_t f) {
+  return (f & MG_V_EXISTS) && !(f & (MG_V_BOUNDARY | MG_V_HANGING));
+}
+
+template <int DIM>
+__device__ __forceinline__ int brick_vol(int B) {
+  return DIM == 2 ? B * B : B * B * B;
+}
+
+// slot of integer position x on level L, -1 outside [0,n)^d or without a brick
+template <int DIM>
+__device__ __forceinline__ int64_t slot_of(const LevelDesc& L, const int* x) {
+  int64_t ri = 0, li = 0;
+#pragma unroll
+  for (int i = DIM - 1; i >= 0; --i) {
+    if (x[i] < 0 || x[i] >= L.n) return -1;
+    ri = ri * L.nb_axis + x[i] / L.B;
+    li = li * L.B + x[i] % L.B;
+  }
+  const int32_t rank = L.brick_rank[ri];
+  return rank < 0 ? -1 : static_cast<int64_t>(rank) * L.S + li;
+}
+
+// global coordinates of a slot; false on padding slots
+template <int DIM>
+__device__ __forceinline__ bool coords_of(const LevelDesc& L, int64_t slot, int* x) {
+  const int64_t b = slot / L.S;
+  int k = static_cast<int>(slot - b * L.S);
+  if (k >= brick_vol<DIM>(L.B)) return false;
+#pragma unroll
+  for (int i = 0; i < DIM; ++i) {
+    x[i] = L.brick_roots[b * DIM + i] * L.B + k % L.B;
+    k /= L.B;
+  }
+  return true;
+}
+
+// index of plane k of a per-vertex multi-entry array (brick-major planes)
+__device__ __forceinline__ int64_t plane_index(const LevelDesc& L, int64_t slot, int k, int K) {
+  const int64_t b = slot / L.S;
+  return (b * K + k) * L.S + (slot - b * L.S);
+}
+
+// ---- delta storage ---------------------------------------------------------
+// DMODE 0: none, 1: FP64 values, 2: BF16 codes x FP32 scale, 3: FP16 codes x FP32 scale
+__device__ __forceinline__ float bf16_bits_to_float(uint16_t q) {
+  return __uint_as_float(static_cast<uint32_t>(q) << 16);
+}
+__device__ __forceinline__ float fp16_bits_to_float(uint16_t q) {
+  __half_raw hr;
+  hr.x = q;
+  return __half2float(__half(hr));
+}
+
+template <int DMODE, typename T>
+__device__ __forceinline__ T load_delta(const void* p, const float* scale, int64_t idx, int64_t slot) {
+  if constexpr (DMODE == 1) {
+    return static_cast<T>(static_cast<const double*>(p)[idx]);
+  } else if constexpr (DMODE == 2) {
+    return static_cast<T>(bf16_bits_to_float(static_cast<const uint16_t*>(p)[idx]) * scale[slot]);
+  } else if constexpr (DMODE == 3) {
+    return static_cast<T>(fp16_bits_to_float(static_cast<const uint16_t*>(p)[idx]) * scale[slot]);
+  } else {
+    return T(0);
+  }
+}
+
+// P(V, o) = P_dlin(o) + P_hat_V(o) in FP64 (PMODE 0: d-linear only, 1: FP64 delta planes)
+template <int DIM, int PMODE>
+__device__ __forceinline__ double p_entry_d(const LevelDesc& Lc, const double* phat, int64_t cs, const int* o) {
+  double w = 1.0;
+  int k = 0, m = 1;
+#pragma unroll
+  for (int i = 0; i < DIM; ++i) {
+    w *= wlin1(o[i]);
+    k += (o[i] + 2) * m;
+    m *= 5;
+  }
+  if constexpr (PMODE == 1) w += phat[plane_index(Lc, cs, k, cpow(5, DIM))];
+  return w;
+}
+
+// ---- full stencil at an arbitrary vertex (setup kernels) -------------------
+// st[k], k over offsets {-1,0,1}^d lexicographic (x fastest): rediscretised from
+// the adjacent existing cells' eps (cell slot = lower-left vertex slot), plus the
+// stored FP64 delta when ahat != nullptr.
+template <int DIM>
+__device__ void full_stencil(const LevelDesc& L, const double* eps, const double* ahat, const int* x,
+                             int64_t slot, double* st) {
+  constexpr int N3 = cpow(3, DIM);
+  double ec[1 << DIM];
+#pragma unroll
+  for (int e = 0; e < (1 << DIM); ++e) {
+    int c[DIM];
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) c[i] = x[i] - ((e >> i) & 1);
+    const int64_t cs = slot_of<DIM>(L, c);
+    ec[e] = cs >= 0 ? eps[cs] : 0.0;
+  }
+  const double scale = DIM == 3 ? L.h : 1.0;
+#pragma unroll
+  for (int k = 0; k < N3; ++k) {
+    int o[DIM];
+    int ham = 0;
+    int kk = k;
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) {
+      o[i] = kk % 3 - 1;
+      kk /= 3;
+      ham += o[i] != 0;
+    }
+    double es = 0.0;
+#pragma unroll
+    for (int e = 0; e < (1 << DIM); ++e) {
+      bool ok = true;
+#pragma unroll
+      for (int i = 0; i < DIM; ++i) {
+        const int t = ((e >> i) & 1) + o[i];
+        ok = ok && t >= 0 && t <= 1;
+      }
+      if (ok) es += ec[e];
+    }
+    st[k] = elem_k(DIM, ham) * es * scale;
+    if (ahat && slot >= 0) st[k] += ahat[plane_index(L, slot, k, N3)];
+  }
+}
+
+}  // namespace mg

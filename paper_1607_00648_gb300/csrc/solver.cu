@@ -1,0 +1,1175 @@
+// Hierarchy, setup sequence, V-cycle and solve drivers, and the C-ABI entry points
+// of libmg (everything except the grid builder).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <type_traits>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+#include "kernels.cuh"
+#include "setup.cuh"
+
+namespace mg {
+
+// ----------------------------------------------------------------------------- small kernels
+
+__global__ void k_leaf_eps(LevelDesc L, const uint8_t* cflags, const double* eps_in, double* eps) {
+  const int64_t s = blockIdx.x * static_cast<int64_t>(kBlock) + threadIdx.x;
+  if (s >= L.n_slots) return;
+  const uint8_t f = cflags[s];
+  eps[s] = ((f & MG_C_EXISTS) && !(f & MG_C_REFINED)) ? eps_in[s] : 0.0;
+}
+
+__global__ void __launch_bounds__(kBlock) k_reduce_partials(const double* partial, int64_t n, double* out) {
+  double v = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += kBlock) v += partial[i];
+  __shared__ double warp_sums[kBlock / 32];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+  if ((threadIdx.x & 31) == 0) warp_sums[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < kBlock / 32; ++w) s += warp_sums[w];
+    out[0] = s;
+  }
+}
+
+__global__ void k_to_f32(int64_t n, const double* in, float* out) {
+  const int64_t i = blockIdx.x * static_cast<int64_t>(kBlock) + threadIdx.x;
+  if (i < n) out[i] = static_cast<float>(in[i]);
+}
+
+// b32 = fl32(r64 / sigma), sigma = sqrt(norm2 / n_dofs) (keeps the FP32 correction O(1))
+__global__ void k_scale_to_f32(int64_t n, const double* r, const double* norm2, double inv_count, float* out,
+                               double* sigma_out) {
+  const int64_t i = blockIdx.x * static_cast<int64_t>(kBlock) + threadIdx.x;
+  const double sigma = sqrt(norm2[0] * inv_count);
+  const double inv = sigma > 0.0 ? 1.0 / sigma : 0.0;
+  if (i == 0) sigma_out[0] = sigma;
+  if (i < n) out[i] = static_cast<float>(r[i] * inv);
+}
+
+// u64 += sigma * e32 (iterative-refinement update; e32 is zero off the DoFs)
+__global__ void k_update_f64(int64_t n, double* u, const float* e, const double* sigma) {
+  const int64_t i = blockIdx.x * static_cast<int64_t>(kBlock) + threadIdx.x;
+  if (i < n) u[i] = fma(sigma[0], static_cast<double>(e[i]), u[i]);
+}
+
+// Round an FP64 value to the nearest (ties to even) BF16 (FMT 1) or FP16 (FMT 2)
+// value, from the IEEE 754 definition of the target format: the quantum is
+// 2^(max(E, Emin) - fraction bits) for the leading-bit exponent E.
+template <int FMT>
+__device__ uint16_t round_to_16(double t) {
+  constexpr int frac = FMT == 1 ? 7 : 10;
+  constexpr int emin = FMT == 1 ? -126 : -14;
+  constexpr int bias = FMT == 1 ? 127 : 15;
+  const uint16_t sign = t < 0.0 ? 0x8000u : 0u;
+  const double a = fabs(t);
+  if (a == 0.0) return sign;
+  int e;
+  frexp(a, &e);
+  int E = e - 1;
+  if (E < emin) E = emin;
+  const double m = rint(ldexp(a, frac - E));  // integer mantissa incl. leading bit, ties to even
+  long long mi = static_cast<long long>(m);
+  if (mi >= (1LL << (frac + 1))) {  // rounding carried into the next binade
+    mi >>= 1;
+    ++E;
+  }
+  if (mi < (1LL << frac)) return sign | static_cast<uint16_t>(mi);  // subnormal (E == emin)
+  return sign | static_cast<uint16_t>(((E + bias) << frac) | (mi - (1LL << frac)));
+}
+
+// per row: scale = fl32(max |delta|), codes = round_to_16(delta / scale)
+template <int FMT>
+__global__ void k_encode_rows(int64_t n, int K, const double* delta, uint16_t* codes, float* scale) {
+  const int64_t i = blockIdx.x * static_cast<int64_t>(kBlock) + threadIdx.x;
+  if (i >= n) return;
+  double m = 0.0;
+  for (int k = 0; k < K; ++k) m = fmax(m, fabs(delta[i * K + k]));
+  const float s = __double2float_rn(m);
+  scale[i] = s;
+  const double sd = static_cast<double>(s);
+  for (int k = 0; k < K; ++k) codes[i * K + k] = sd > 0.0 ? round_to_16<FMT>(delta[i * K + k] / sd) : 0;
+}
+
+// same on brick-major planes of a level
+template <int FMT>
+__global__ void k_encode_planes(LevelDesc L, int K, const double* delta, uint16_t* codes, float* scale) {
+  const int64_t s = blockIdx.x * static_cast<int64_t>(kBlock) + threadIdx.x;
+  if (s >= L.n_slots) return;
+  double m = 0.0;
+  for (int k = 0; k < K; ++k) m = fmax(m, fabs(delta[plane_index(L, s, k, K)]));
+  const float sc = __double2float_rn(m);
+  scale[s] = sc;
+  const double sd = static_cast<double>(sc);
+  for (int k = 0; k < K; ++k) {
+    const int64_t idx = plane_index(L, s, k, K);
+    codes[idx] = sd > 0.0 ? round_to_16<FMT>(delta[idx] / sd) : 0;
+  }
+}
+
+// reconstructed stencils (offset-major export) and the diagonal audit (Sect. 4.3)
+template <int DIM>
+__global__ void k_export_stencils(LevelDesc L, const double* eps, const double* ahat, double* out, int* status) {
+  constexpr int N3 = cpow(3, DIM);
+  const int64_t s = blockIdx.x * static_cast<int64_t>(kBlock) + threadIdx.x;
+  if (s >= L.n_slots) return;
+  int x[DIM];
+  double st[N3];
+  if (!coords_of<DIM>(L, s, x)) {
+    if (out)
+      for (int k = 0; k < N3; ++k) out[k * L.n_slots + s] = 0.0;
+    return;
+  }
+  full_stencil<DIM>(L, eps, ahat, x, s, st);
+  if (out)
+    for (int k = 0; k < N3; ++k) out[k * L.n_slots + s] = st[k];
+  if (status && is_dof(L.vflags[s]) && !(st[N3 / 2] > 0.0)) atomicExch(status, 2);
+}
+
+// dense coarsest operator over its DoFs
+template <int DIM>
+__global__ void k_coarse_assemble(LevelDesc L, const double* eps, const double* ahat, const int32_t* c_slots,
+                                  const int32_t* c_map, int n, double* M) {
+  constexpr int N3 = cpow(3, DIM);
+  const int i = blockIdx.x * kBlock + threadIdx.x;
+  if (i >= n) return;
+  const int64_t s = c_slots[i];
+  int x[DIM];
+  coords_of<DIM>(L, s, x);
+  double st[N3];
+  full_stencil<DIM>(L, eps, ahat, x, s, st);
+  for (int j = 0; j < n; ++j) M[static_cast<int64_t>(i) * n + j] = 0.0;
+  for (int k = 0; k < N3; ++k) {
+    int y[DIM], kk = k;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+      y[a] = x[a] + kk % 3 - 1;
+      kk /= 3;
+    }
+    const int64_t t = slot_of<DIM>(L, y);
+    if (t < 0) continue;
+    const int j = c_map[t];
+    if (j >= 0) M[static_cast<int64_t>(i) * n + j] = st[k];
+  }
+}
+
+// in-place lower Cholesky factor of the SPD coarsest operator (one CTA); status 3 on failure
+__global__ void __launch_bounds__(kBlock) k_cholesky(double* M, int n, int* status) {
+  __shared__ int fail;
+  if (threadIdx.x == 0) fail = 0;
+  __syncthreads();
+  for (int k = 0; k < n; ++k) {
+    if (threadIdx.x == 0) {
+      const double d = M[static_cast<int64_t>(k) * n + k];
+      if (!(d > 0.0)) {
+        fail = 1;
+      } else {
+        M[static_cast<int64_t>(k) * n + k] = sqrt(d);
+      }
+    }
+    __syncthreads();
+    if (fail) break;
+    const double dk = M[static_cast<int64_t>(k) * n + k];
+    for (int i = k + 1 + threadIdx.x; i < n; i += kBlock) M[static_cast<int64_t>(i) * n + k] /= dk;
+    __syncthreads();
+    const int m = n - k - 1;
+    for (int t = threadIdx.x; t < m * m; t += kBlock) {
+      const int i = k + 1 + t / m, j = k + 1 + t % m;
+      if (j <= i) M[static_cast<int64_t>(i) * n + j] -= M[static_cast<int64_t>(i) * n + k] * M[static_cast<int64_t>(j) * n + k];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && fail) atomicExch(status, 3);
+}
+
+// u(coarsest DoFs) = A^-1 b by the Cholesky factor, in FP64 for both precisions
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_coarse_solve(const double* Lm, int n, const int32_t* c_slots, const T* b,
+                                                           T* u) {
+  extern __shared__ double y[];
+  for (int i = threadIdx.x; i < n; i += kBlock) y[i] = static_cast<double>(b[c_slots[i]]);
+  __syncthreads();
+  for (int k = 0; k < n; ++k) {  // L y = b
+    if (threadIdx.x == 0) y[k] /= Lm[static_cast<int64_t>(k) * n + k];
+    __syncthreads();
+    for (int i = k + 1 + threadIdx.x; i < n; i += kBlock) y[i] -= Lm[static_cast<int64_t>(i) * n + k] * y[k];
+    __syncthreads();
+  }
+  for (int k = n - 1; k >= 0; --k) {  // L^T x = y
+    if (threadIdx.x == 0) y[k] /= Lm[static_cast<int64_t>(k) * n + k];
+    __syncthreads();
+    for (int i = threadIdx.x; i < k; i += kBlock) y[i] -= Lm[static_cast<int64_t>(k) * n + i] * y[k];
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < n; i += kBlock) u[c_slots[i]] = static_cast<T>(y[i]);
+}
+
+// ----------------------------------------------------------------------------- hierarchy
+
+struct DevLevel {
+  LevelDesc d{};
+  int32_t* brick_nbr = nullptr;
+  int32_t* brick_roots = nullptr;
+  int32_t* brick_rank = nullptr;
+  uint8_t* vflags = nullptr;
+  uint8_t* cflags = nullptr;
+  int32_t* hang_idx = nullptr;
+  double* hang_w = nullptr;
+  double* eps = nullptr;
+  float* eps32 = nullptr;
+  double* ahat = nullptr;
+  uint16_t* a16 = nullptr;
+  float* ascale = nullptr;
+  double* phat = nullptr;
+  uint16_t* p16 = nullptr;
+  float* pscale = nullptr;
+  double *u = nullptr, *b = nullptr, *r = nullptr, *t = nullptr;
+  float *u32 = nullptr, *b32 = nullptr, *r32 = nullptr, *t32 = nullptr;
+  double* partial = nullptr;
+  int64_t n_dofs = 0;
+};
+
+struct Graph {
+  cudaGraphExec_t exec = nullptr;
+  const void* key0 = nullptr;
+  const void* key1 = nullptr;
+  void reset() {
+    if (exec) cudaGraphExecDestroy(exec);
+    exec = nullptr;
+    key0 = key1 = nullptr;
+  }
+};
+
+struct Hier {
+  const Grid* g = nullptr;
+  mg_options opt{};
+  int L = 0, c = 1, dim = 2;
+  bool galerkin = false, boxmg = false, mixed = false;
+  int fmt = 1;  // 1 bf16, 2 fp16
+  std::vector<DevLevel> lv;
+  std::vector<void*> allocs;
+  int n_c = 0;
+  int32_t* c_slots = nullptr;
+  int32_t* c_map = nullptr;
+  double* c_mat = nullptr;
+  int* d_status = nullptr;
+  double* d_scal = nullptr;  // [0] norm2 fp64, [1] norm2 fp32 inner, [2] sigma
+  double* h_pin = nullptr;   // pinned mirror of d_scal
+  cudaStream_t own = nullptr;
+  bool ready = false;
+  Graph g_cycle64, g_outer, g_inner;
+};
+
+#define MG_TRY_CUDA(call)                                                         \
+  do {                                                                            \
+    cudaError_t e_ = (call);                                                      \
+    if (e_ != cudaSuccess) {                                                      \
+      set_error(std::string(#call) + " failed: " + cudaGetErrorString(e_));       \
+      return MG_ERR_CUDA;                                                         \
+    }                                                                             \
+  } while (0)
+
+#define MG_CHECK(expr)               \
+  do {                               \
+    mg_status st_ = (expr);          \
+    if (st_ != MG_OK) return st_;    \
+  } while (0)
+
+static mg_status last_launch(const char* what) {
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_error(std::string(what) + ": " + cudaGetErrorString(e));
+    return MG_ERR_CUDA;
+  }
+  return MG_OK;
+}
+
+template <typename T>
+static mg_status dalloc(Hier& H, T** p, size_t n) {
+  *p = nullptr;
+  if (n == 0) return MG_OK;
+  void* q = nullptr;
+  const cudaError_t e = cudaMalloc(&q, n * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    set_error(std::string("cudaMalloc of ") + std::to_string(n * sizeof(T)) + " bytes: " + cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? MG_ERR_OOM : MG_ERR_CUDA;
+  }
+  H.allocs.push_back(q);
+  MG_TRY_CUDA(cudaMemset(q, 0, n * sizeof(T)));
+  *p = static_cast<T*>(q);
+  return MG_OK;
+}
+
+template <typename T>
+static mg_status upload(Hier& H, T** p, const std::vector<T>& v) {
+  MG_CHECK(dalloc(H, p, v.size()));
+  if (!v.empty()) MG_TRY_CUDA(cudaMemcpy(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return MG_OK;
+}
+
+static void free_hier(Hier* H) {
+  if (!H) return;
+  H->g_cycle64.reset();
+  H->g_outer.reset();
+  H->g_inner.reset();
+  for (void* p : H->allocs) cudaFree(p);
+  if (H->h_pin) cudaFreeHost(H->h_pin);
+  if (H->own) cudaStreamDestroy(H->own);
+  delete H;
+}
+
+static inline unsigned nblk(int64_t n) { return static_cast<unsigned>((n + kBlock - 1) / kBlock); }
+
+static mg_status create(const Grid* g, const mg_options& o, Hier** out) {
+  Hier* H = new (std::nothrow) Hier();
+  if (!H) {
+    set_error("mg_hier_create: out of host memory");
+    return MG_ERR_OOM;
+  }
+  H->g = g;
+  H->opt = o;
+  H->L = g->L;
+  H->c = o.coarsest_level;
+  H->dim = g->dim;
+  H->galerkin = o.coarse == MG_COARSE_GALERKIN;
+  H->boxmg = o.transfer == MG_TRANSFER_BOXMG;
+  H->mixed = o.precision != MG_PREC_FP64;
+  H->fmt = o.precision == MG_PREC_MIXED_FP16 ? 2 : 1;
+  auto fail = [&](mg_status s) {
+    free_hier(H);
+    return s;
+  };
+  const int d = g->dim;
+  const int n3 = ipow(3, d), n5 = ipow(5, d);
+  H->lv.resize(H->L + 1);
+  mg_status st;
+  for (int l = H->c; l <= H->L; ++l) {
+    const HostLevel& hl = g->levels[l];
+    DevLevel& D = H->lv[l];
+    if ((st = upload(*H, &D.brick_nbr, hl.brick_nbr)) != MG_OK) return fail(st);
+    if ((st = upload(*H, &D.brick_roots, hl.brick_roots)) != MG_OK) return fail(st);
+    if ((st = upload(*H, &D.brick_rank, hl.brick_rank)) != MG_OK) return fail(st);
+    if ((st = upload(*H, &D.vflags, hl.vflags)) != MG_OK) return fail(st);
+    if ((st = upload(*H, &D.cflags, hl.cflags)) != MG_OK) return fail(st);
+    if (l > 0) {
+      if ((st = upload(*H, &D.hang_idx, hl.hang_idx)) != MG_OK) return fail(st);
+      if ((st = upload(*H, &D.hang_w, hl.hang_w)) != MG_OK) return fail(st);
+    }
+    const size_t ns = static_cast<size_t>(hl.n_slots);
+    D.n_dofs = hl.n_dofs;
+    D.d = LevelDesc{d, l, hl.n, hl.B, hl.S, hl.nb_axis, hl.n_bricks, hl.n_slots, hl.h,
+                    D.brick_nbr, D.brick_roots, D.brick_rank, D.vflags};
+    if ((st = dalloc(*H, &D.eps, ns)) != MG_OK) return fail(st);
+    if ((st = dalloc(*H, &D.r, ns)) != MG_OK) return fail(st);
+    if ((st = dalloc(*H, &D.t, ns)) != MG_OK) return fail(st);
+    if ((st = dalloc(*H, &D.partial, static_cast<size_t>(hl.n_bricks))) != MG_OK) return fail(st);
+    if (l < H->L) {
+      if ((st = dalloc(*H, &D.u, ns)) != MG_OK) return fail(st);
+      if ((st = dalloc(*H, &D.b, ns)) != MG_OK) return fail(st);
+      if (H->galerkin && (st = dalloc(*H, &D.ahat, ns * n3)) != MG_OK) return fail(st);
+      if (H->boxmg && (st = dalloc(*H, &D.phat, ns * n5)) != MG_OK) return fail(st);
+    }
+    if (H->mixed) {
+      if ((st = dalloc(*H, &D.eps32, ns)) != MG_OK) return fail(st);
+      if ((st = dalloc(*H, &D.u32, ns)) != MG_OK) return fail(st);
+      if ((st = dalloc(*H, &D.b32, ns)) != MG_OK) return fail(st);
+      if ((st = dalloc(*H, &D.r32, ns)) != MG_OK) return fail(st);
+      if ((st = dalloc(*H, &D.t32, ns)) != MG_OK) return fail(st);
+      if (l < H->L) {
+        if (H->galerkin) {
+          if ((st = dalloc(*H, &D.a16, ns * n3)) != MG_OK) return fail(st);
+          if ((st = dalloc(*H, &D.ascale, ns)) != MG_OK) return fail(st);
+        }
+        if (H->boxmg) {
+          if ((st = dalloc(*H, &D.p16, ns * n5)) != MG_OK) return fail(st);
+          if ((st = dalloc(*H, &D.pscale, ns)) != MG_OK) return fail(st);
+        }
+      }
+    }
+  }
+  // coarsest dense system
+  const HostLevel& hc = g->levels[H->c];
+  std::vector<int32_t> slots, map(hc.n_slots, -1);
+  for (int64_t s = 0; s < hc.n_slots; ++s) {
+    const uint8_t f = hc.vflags[s];
+    if ((f & MG_V_EXISTS) && !(f & (MG_V_BOUNDARY | MG_V_HANGING))) {
+      map[s] = static_cast<int32_t>(slots.size());
+      slots.push_back(static_cast<int32_t>(s));
+    }
+  }
+  H->n_c = static_cast<int>(slots.size());
+  if (H->n_c == 0 || H->n_c > 4096) {
+    set_error("mg_hier_create: coarsest level has " + std::to_string(H->n_c) + " DoFs (need 1..4096)");
+    return fail(MG_ERR_INVALID_ARG);
+  }
+  if ((st = upload(*H, &H->c_slots, slots)) != MG_OK) return fail(st);
+  if ((st = upload(*H, &H->c_map, map)) != MG_OK) return fail(st);
+  if ((st = dalloc(*H, &H->c_mat, static_cast<size_t>(H->n_c) * H->n_c)) != MG_OK) return fail(st);
+  if ((st = dalloc(*H, &H->d_status, 1)) != MG_OK) return fail(st);
+  if ((st = dalloc(*H, &H->d_scal, 16)) != MG_OK) return fail(st);
+  if (cudaMallocHost(&H->h_pin, 16 * sizeof(double)) != cudaSuccess) {
+    set_error("mg_hier_create: cudaMallocHost failed");
+    return fail(MG_ERR_OOM);
+  }
+  if (cudaStreamCreate(&H->own) != cudaSuccess) {
+    set_error("mg_hier_create: cudaStreamCreate failed");
+    return fail(MG_ERR_CUDA);
+  }
+  *out = H;
+  return MG_OK;
+}
+
+// ----------------------------------------------------------------------------- kernel dispatch
+
+template <int DIM, typename T>
+static void sweep_dim(const DevLevel& D, int op, int amode, const T* u, const T* b, T* out, const T* eps,
+                      const void* ahat, const float* ascale, T omega, double* partial, cudaStream_t s) {
+  SweepArgs<T> a{D.d, u, b, out, eps, ahat, ascale, omega, partial};
+  const int Bu = D.d.B + 2, Be = D.d.B + 1;
+  const size_t smem = (DIM == 2 ? (Bu * Bu + Be * Be) : (Bu * Bu * Bu + Be * Be * Be)) * sizeof(T);
+  const unsigned grid = static_cast<unsigned>(D.d.n_bricks);
+#define MG_SW(AM, OP) k_sweep<DIM, T, AM, OP><<<grid, kBlock, smem, s>>>(a)
+  if constexpr (std::is_same<T, double>::value) {
+    if (op == kJacobi) {
+      if (amode == 1) MG_SW(1, kJacobi); else MG_SW(0, kJacobi);
+    } else {
+      if (amode == 1) MG_SW(1, kResidual); else MG_SW(0, kResidual);
+    }
+  } else {
+    if (op == kJacobi) {
+      if (amode == 2) MG_SW(2, kJacobi); else if (amode == 3) MG_SW(3, kJacobi); else MG_SW(0, kJacobi);
+    } else {
+      if (amode == 2) MG_SW(2, kResidual); else if (amode == 3) MG_SW(3, kResidual); else MG_SW(0, kResidual);
+    }
+  }
+#undef MG_SW
+}
+
+template <typename T>
+static void sweep(const Hier& H, int l, int op, const T* u, const T* b, T* out, double* partial, cudaStream_t s) {
+  const DevLevel& D = H.lv[l];
+  const bool coarse = l < H.L && H.galerkin;
+  int amode = 0;
+  const void* ahat = nullptr;
+  const float* ascale = nullptr;
+  const T* eps;
+  if constexpr (std::is_same<T, double>::value) {
+    eps = D.eps;
+    if (coarse) {
+      amode = 1;
+      ahat = D.ahat;
+    }
+  } else {
+    eps = D.eps32;
+    if (coarse) {
+      amode = H.fmt == 1 ? 2 : 3;
+      ahat = D.a16;
+      ascale = D.ascale;
+    }
+  }
+  const T omega = static_cast<T>(H.opt.omega);
+  if (H.dim == 2)
+    sweep_dim<2, T>(D, op, amode, u, b, out, eps, ahat, ascale, omega, partial, s);
+  else
+    sweep_dim<3, T>(D, op, amode, u, b, out, eps, ahat, ascale, omega, partial, s);
+}
+
+template <typename T>
+static void transfer(const Hier& H, int fine, bool restrict_op, const T* in, T* out, cudaStream_t s) {
+  const DevLevel& F = H.lv[fine];
+  const DevLevel& C = H.lv[fine - 1];
+  int pmode = 0;
+  const void* ph = nullptr;
+  const float* ps = nullptr;
+  if (H.boxmg) {
+    if constexpr (std::is_same<T, double>::value) {
+      pmode = 1;
+      ph = C.phat;
+    } else {
+      pmode = H.fmt == 1 ? 2 : 3;
+      ph = C.p16;
+      ps = C.pscale;
+    }
+  }
+#define MG_TR(DIM, PM)                                                                           \
+  do {                                                                                           \
+    if (restrict_op)                                                                             \
+      k_restrict<DIM, T, PM><<<nblk(C.d.n_slots), kBlock, 0, s>>>(C.d, F.d, in, out, ph, ps);   \
+    else                                                                                         \
+      k_prolong<DIM, T, PM><<<nblk(F.d.n_slots), kBlock, 0, s>>>(C.d, F.d, in, out, ph, ps);    \
+  } while (0)
+  if (H.dim == 2) {
+    if (pmode == 0) MG_TR(2, 0); else if (pmode == 1) MG_TR(2, 1); else if (pmode == 2) MG_TR(2, 2); else MG_TR(2, 3);
+  } else {
+    if (pmode == 0) MG_TR(3, 0); else if (pmode == 1) MG_TR(3, 1); else if (pmode == 2) MG_TR(3, 2); else MG_TR(3, 3);
+  }
+#undef MG_TR
+}
+
+static void reduce(const DevLevel& D, double* out, cudaStream_t s) {
+  k_reduce_partials<<<1, kBlock, 0, s>>>(D.partial, D.d.n_bricks, out);
+}
+
+template <typename T>
+static void coarse_solve(const Hier& H, const T* b, T* u, cudaStream_t s) {
+  k_coarse_solve<T><<<1, kBlock, H.n_c * sizeof(double), s>>>(H.c_mat, H.n_c, H.c_slots, b, u);
+}
+
+// nu damped Jacobi sweeps, ping-pong through tmp, result in u
+template <typename T>
+static void smooth(const Hier& H, int l, T* u, const T* b, T* tmp, int nu, cudaStream_t s) {
+  T* src = u;
+  T* dst = tmp;
+  for (int k = 0; k < nu; ++k) {
+    sweep<T>(H, l, kJacobi, src, b, dst, nullptr, s);
+    T* t = src;
+    src = dst;
+    dst = t;
+  }
+  if (src != u) cudaMemcpyAsync(u, src, H.lv[l].d.n_slots * sizeof(T), cudaMemcpyDeviceToDevice, s);
+}
+
+template <typename T>
+static T* lvec(Hier& H, int l, int which) {  // 0 u, 1 b, 2 r, 3 t
+  DevLevel& D = H.lv[l];
+  if constexpr (std::is_same<T, double>::value) {
+    return which == 0 ? D.u : which == 1 ? D.b : which == 2 ? D.r : D.t;
+  } else {
+    return which == 0 ? D.u32 : which == 1 ? D.b32 : which == 2 ? D.r32 : D.t32;
+  }
+}
+
+// V(nu1, nu2) cycle on level l (correction scheme; Alg. 1 semantics, Sect. 3 FAS reduced)
+template <typename T>
+static void vcycle(Hier& H, int l, T* u, const T* b, cudaStream_t s) {
+  if (l == H.c) {
+    coarse_solve<T>(H, b, u, s);
+    return;
+  }
+  T* tmp = lvec<T>(H, l, 3);
+  T* r = lvec<T>(H, l, 2);
+  T* uc = lvec<T>(H, l - 1, 0);
+  T* bc = lvec<T>(H, l - 1, 1);
+  smooth<T>(H, l, u, b, tmp, H.opt.nu1, s);
+  sweep<T>(H, l, kResidual, u, b, r, nullptr, s);
+  transfer<T>(H, l, true, r, bc, s);
+  cudaMemsetAsync(uc, 0, H.lv[l - 1].d.n_slots * sizeof(T), s);
+  vcycle<T>(H, l - 1, uc, bc, s);
+  transfer<T>(H, l, false, uc, u, s);
+  smooth<T>(H, l, u, b, tmp, H.opt.nu2, s);
+}
+
+// finest residual r = b - A u with its squared norm into d_scal[slot]
+template <typename T>
+static void residual_norm(Hier& H, const T* u, const T* b, T* r, int slot, cudaStream_t s) {
+  DevLevel& F = H.lv[H.L];
+  sweep<T>(H, H.L, kResidual, u, b, r, F.partial, s);
+  reduce(F, H.d_scal + slot, s);
+}
+
+static mg_status run_setup(Hier& H, const double* eps_in, cudaStream_t s) {
+  const Grid& g = *H.g;
+  const int d = H.dim;
+  for (int l = H.c; l <= H.L; ++l) {
+    DevLevel& D = H.lv[l];
+    k_leaf_eps<<<nblk(D.d.n_slots), kBlock, 0, s>>>(D.d, D.cflags, eps_in + g.levels[l].slot_offset, D.eps);
+  }
+  for (int l = H.L - 1; l >= H.c; --l) {
+    DevLevel& C = H.lv[l];
+    DevLevel& F = H.lv[l + 1];
+    if (d == 2)
+      k_mean_eps<2><<<nblk(C.d.n_slots), kBlock, 0, s>>>(C.d, F.d, C.cflags, F.eps, C.eps);
+    else
+      k_mean_eps<3><<<nblk(C.d.n_slots), kBlock, 0, s>>>(C.d, F.d, C.cflags, F.eps, C.eps);
+  }
+  MG_CHECK(last_launch("setup: coefficients"));
+  MG_TRY_CUDA(cudaMemsetAsync(H.d_status, 0, sizeof(int), s));
+  for (int l = H.L; l > H.c; --l) {
+    DevLevel& F = H.lv[l];
+    DevLevel& C = H.lv[l - 1];
+    const double* ahat_f = (l < H.L && H.galerkin) ? F.ahat : nullptr;
+    const unsigned gb = static_cast<unsigned>((C.d.n_slots + 127) / 128);
+    if (H.boxmg) {
+      if (d == 2)
+        k_boxmg<2><<<gb, 128, 0, s>>>(C.d, F.d, F.eps, ahat_f, C.phat, H.d_status);
+      else
+        k_boxmg<3><<<gb, 128, 0, s>>>(C.d, F.d, F.eps, ahat_f, C.phat, H.d_status);
+    }
+    if (H.galerkin) {
+      if (d == 2) {
+        if (H.boxmg)
+          k_rap<2, 1><<<gb, 128, 0, s>>>(C.d, F.d, F.eps, ahat_f, C.eps, C.phat, C.ahat);
+        else
+          k_rap<2, 0><<<gb, 128, 0, s>>>(C.d, F.d, F.eps, ahat_f, C.eps, C.phat, C.ahat);
+      } else {
+        if (H.boxmg)
+          k_rap<3, 1><<<gb, 128, 0, s>>>(C.d, F.d, F.eps, ahat_f, C.eps, C.phat, C.ahat);
+        else
+          k_rap<3, 0><<<gb, 128, 0, s>>>(C.d, F.d, F.eps, ahat_f, C.eps, C.phat, C.ahat);
+      }
+    }
+    MG_CHECK(last_launch("setup: BoxMG / Galerkin"));
+  }
+  // diagonal audit of every level (Sect. 4.3 definiteness check) and coarsest factor
+  for (int l = H.c; l <= H.L; ++l) {
+    DevLevel& D = H.lv[l];
+    const double* ah = (l < H.L && H.galerkin) ? D.ahat : nullptr;
+    if (d == 2)
+      k_export_stencils<2><<<nblk(D.d.n_slots), kBlock, 0, s>>>(D.d, D.eps, ah, nullptr, H.d_status);
+    else
+      k_export_stencils<3><<<nblk(D.d.n_slots), kBlock, 0, s>>>(D.d, D.eps, ah, nullptr, H.d_status);
+  }
+  {
+    DevLevel& C = H.lv[H.c];
+    const double* ah = (H.c < H.L && H.galerkin) ? C.ahat : nullptr;
+    if (d == 2)
+      k_coarse_assemble<2><<<nblk(H.n_c), kBlock, 0, s>>>(C.d, C.eps, ah, H.c_slots, H.c_map, H.n_c, H.c_mat);
+    else
+      k_coarse_assemble<3><<<nblk(H.n_c), kBlock, 0, s>>>(C.d, C.eps, ah, H.c_slots, H.c_map, H.n_c, H.c_mat);
+    k_cholesky<<<1, kBlock, 0, s>>>(H.c_mat, H.n_c, H.d_status);
+  }
+  MG_CHECK(last_launch("setup: coarse factor"));
+  if (H.mixed) {
+    const int n3 = ipow(3, d), n5 = ipow(5, d);
+    for (int l = H.c; l <= H.L; ++l) {
+      DevLevel& D = H.lv[l];
+      k_to_f32<<<nblk(D.d.n_slots), kBlock, 0, s>>>(D.d.n_slots, D.eps, D.eps32);
+      if (l < H.L) {
+        if (H.galerkin) {
+          if (H.fmt == 1)
+            k_encode_planes<1><<<nblk(D.d.n_slots), kBlock, 0, s>>>(D.d, n3, D.ahat, D.a16, D.ascale);
+          else
+            k_encode_planes<2><<<nblk(D.d.n_slots), kBlock, 0, s>>>(D.d, n3, D.ahat, D.a16, D.ascale);
+        }
+        if (H.boxmg) {
+          if (H.fmt == 1)
+            k_encode_planes<1><<<nblk(D.d.n_slots), kBlock, 0, s>>>(D.d, n5, D.phat, D.p16, D.pscale);
+          else
+            k_encode_planes<2><<<nblk(D.d.n_slots), kBlock, 0, s>>>(D.d, n5, D.phat, D.p16, D.pscale);
+        }
+      }
+    }
+    MG_CHECK(last_launch("setup: encode"));
+  }
+  int status = 0;
+  MG_TRY_CUDA(cudaMemcpyAsync(&status, H.d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  MG_TRY_CUDA(cudaStreamSynchronize(s));
+  if (status == 1) {
+    set_error("mg_setup: a BoxMG patch system is singular");
+    return MG_ERR_INDEFINITE_COARSE;
+  }
+  if (status == 2) {
+    set_error("mg_setup: a level operator has a non-positive diagonal (Sect. 4.3 definiteness check)");
+    return MG_ERR_INDEFINITE_COARSE;
+  }
+  if (status == 3) {
+    set_error("mg_setup: the coarsest operator is not positive definite");
+    return MG_ERR_INDEFINITE_COARSE;
+  }
+  H.ready = true;
+  return MG_OK;
+}
+
+static cudaStream_t pick(Hier& H, void* stream) {
+  return stream ? static_cast<cudaStream_t>(stream) : H.own;
+}
+
+// capture fn() on stream s into g (re-captured when the key pointers change)
+template <typename F>
+static mg_status graph_launch(Hier& H, Graph& g, const void* k0, const void* k1, cudaStream_t s, F fn) {
+  if (!H.opt.use_graphs) {
+    fn(s);
+    return last_launch("cycle");
+  }
+  if (!g.exec || g.key0 != k0 || g.key1 != k1) {
+    g.reset();
+    cudaGraph_t graph = nullptr;
+    MG_TRY_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    fn(s);
+    const cudaError_t e = cudaStreamEndCapture(s, &graph);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      set_error(std::string("graph capture: ") + cudaGetErrorString(e));
+      return MG_ERR_CUDA;
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&g.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) {
+      g.exec = nullptr;
+      set_error(std::string("graph instantiate: ") + cudaGetErrorString(ei));
+      return MG_ERR_CUDA;
+    }
+    g.key0 = k0;
+    g.key1 = k1;
+  }
+  MG_TRY_CUDA(cudaGraphLaunch(g.exec, s));
+  return MG_OK;
+}
+
+static mg_status solve_fp64(Hier& H, double* u, const double* b, double tol, int max_cycles, mg_solve_stats* st,
+                            cudaStream_t s) {
+  DevLevel& F = H.lv[H.L];
+  MG_TRY_CUDA(cudaMemsetAsync(u, 0, F.d.n_slots * sizeof(double), s));
+  residual_norm<double>(H, u, b, F.r, 0, s);
+  MG_TRY_CUDA(cudaMemcpyAsync(H.h_pin, H.d_scal, sizeof(double), cudaMemcpyDeviceToHost, s));
+  MG_TRY_CUDA(cudaStreamSynchronize(s));
+  const double r0 = std::sqrt(H.h_pin[0]);
+  if (st) {
+    st->r0_norm = r0;
+    st->history_len = 0;
+  }
+  if (!std::isfinite(r0)) {
+    set_error("mg_solve: non-finite initial residual");
+    return MG_ERR_NONFINITE;
+  }
+  double rel = r0 > 0 ? 1.0 : 0.0;
+  int cycles = 0;
+  while (rel > tol && cycles < max_cycles) {
+    MG_CHECK(graph_launch(H, H.g_cycle64, u, b, s, [&](cudaStream_t ss) {
+      vcycle<double>(H, H.L, u, b, ss);
+      residual_norm<double>(H, u, b, F.r, 0, ss);
+      cudaMemcpyAsync(H.h_pin, H.d_scal, sizeof(double), cudaMemcpyDeviceToHost, ss);
+    }));
+    MG_TRY_CUDA(cudaStreamSynchronize(s));
+    ++cycles;
+    rel = std::sqrt(H.h_pin[0]) / r0;
+    if (st && st->history && st->history_len < st->history_capacity) st->history[st->history_len++] = rel;
+    if (!std::isfinite(rel)) {
+      set_error("mg_solve: non-finite residual");
+      if (st) st->cycles = cycles;
+      return MG_ERR_NONFINITE;
+    }
+    if (rel > 1e6) {
+      set_error("mg_solve: residual grew by more than 1e6 (diverged)");
+      if (st) st->cycles = cycles;
+      return MG_ERR_DIVERGED;
+    }
+  }
+  if (st) {
+    st->cycles = cycles;
+    st->outer_steps = cycles;
+    st->rel_residual = rel;
+  }
+  if (rel > tol) {
+    set_error("mg_solve: not converged within max_cycles");
+    return MG_ERR_NOT_CONVERGED;
+  }
+  return MG_OK;
+}
+
+// FP64 iterative refinement around FP32 V-cycles (Sect. 5 deltas decoded from 16 bits)
+static mg_status solve_mixed(Hier& H, double* u, const double* b, double tol, int max_cycles, mg_solve_stats* st,
+                             cudaStream_t s) {
+  DevLevel& F = H.lv[H.L];
+  const int64_t n = F.d.n_slots;
+  const double inv_count = F.n_dofs > 0 ? 1.0 / static_cast<double>(F.n_dofs) : 0.0;
+  MG_TRY_CUDA(cudaMemsetAsync(u, 0, n * sizeof(double), s));
+  MG_TRY_CUDA(cudaMemsetAsync(F.u32, 0, n * sizeof(float), s));
+  MG_TRY_CUDA(cudaMemsetAsync(H.d_scal + 2, 0, sizeof(double), s));
+  residual_norm<double>(H, u, b, F.r, 0, s);
+  MG_TRY_CUDA(cudaMemcpyAsync(H.h_pin, H.d_scal, sizeof(double), cudaMemcpyDeviceToHost, s));
+  MG_TRY_CUDA(cudaStreamSynchronize(s));
+  const double r0 = std::sqrt(H.h_pin[0]);
+  if (st) {
+    st->r0_norm = r0;
+    st->history_len = 0;
+  }
+  if (!std::isfinite(r0)) {
+    set_error("mg_solve: non-finite initial residual");
+    return MG_ERR_NONFINITE;
+  }
+  double rel = r0 > 0 ? 1.0 : 0.0;
+  int cycles = 0, outer = 0;
+  const int chunk = H.opt.inner_cycles > 0 ? H.opt.inner_cycles : 8;
+  bool first = true;
+  while (rel > tol && cycles < max_cycles) {
+    // outer step: u += sigma e (skipped the first time), r = b - A u in FP64, b32 = r / sigma
+    MG_CHECK(graph_launch(H, H.g_outer, u, b, s, [&](cudaStream_t ss) {
+      k_update_f64<<<nblk(n), kBlock, 0, ss>>>(n, u, F.u32, H.d_scal + 2);
+      residual_norm<double>(H, u, b, F.r, 0, ss);
+      k_scale_to_f32<<<nblk(n), kBlock, 0, ss>>>(n, F.r, H.d_scal, inv_count, F.b32, H.d_scal + 2);
+      cudaMemsetAsync(F.u32, 0, n * sizeof(float), ss);
+      cudaMemcpyAsync(H.h_pin, H.d_scal, sizeof(double), cudaMemcpyDeviceToHost, ss);
+    }));
+    MG_TRY_CUDA(cudaStreamSynchronize(s));
+    ++outer;
+    rel = std::sqrt(H.h_pin[0]) / r0;
+    if (!first && st && st->history && st->history_len < st->history_capacity) st->history[st->history_len++] = rel;
+    first = false;
+    if (!std::isfinite(rel)) {
+      set_error("mg_solve: non-finite residual");
+      return MG_ERR_NONFINITE;
+    }
+    if (rel > 1e6) {
+      set_error("mg_solve: residual grew by more than 1e6 (diverged)");
+      return MG_ERR_DIVERGED;
+    }
+    if (rel <= tol) break;
+    // inner FP32 cycles until the correction equation is solved to what this step needs
+    const double target = std::max(1e-5, 0.3 * tol / rel);
+    double prev = 1.0;
+    while (cycles < max_cycles) {
+      MG_CHECK(graph_launch(H, H.g_inner, nullptr, nullptr, s, [&](cudaStream_t ss) {
+        for (int k = 0; k < chunk; ++k) vcycle<float>(H, H.L, F.u32, F.b32, ss);
+        residual_norm<float>(H, F.u32, F.b32, F.r32, 1, ss);
+        cudaMemcpyAsync(H.h_pin + 1, H.d_scal + 1, sizeof(double), cudaMemcpyDeviceToHost, ss);
+      }));
+      MG_TRY_CUDA(cudaStreamSynchronize(s));
+      cycles += chunk;
+      const double inner = std::sqrt(H.h_pin[1] * inv_count);  // ||b32|| = sqrt(n_dofs)
+      if (!std::isfinite(inner)) {
+        set_error("mg_solve: non-finite FP32 inner residual");
+        return MG_ERR_NONFINITE;
+      }
+      if (inner <= target || inner > 0.9 * prev) break;
+      prev = inner;
+    }
+  }
+  if (st) {
+    st->cycles = cycles;
+    st->outer_steps = outer;
+    st->rel_residual = rel;
+  }
+  if (rel > tol) {
+    set_error("mg_solve: not converged within max_cycles");
+    return MG_ERR_NOT_CONVERGED;
+  }
+  return MG_OK;
+}
+
+}  // namespace mg
+
+using namespace mg;
+
+// ----------------------------------------------------------------------------- C ABI
+
+static Hier* H_(mg_hier* h) { return reinterpret_cast<Hier*>(h); }
+
+static mg_status check_level(Hier* H, int level, bool need_ready) {
+  if (!H) {
+    set_error("NULL hierarchy");
+    return MG_ERR_INVALID_ARG;
+  }
+  if (level < H->c || level > H->L) {
+    set_error("level outside [coarsest, max_level]");
+    return MG_ERR_INVALID_ARG;
+  }
+  if (need_ready && !H->ready) {
+    set_error("hierarchy not set up (call mg_setup)");
+    return MG_ERR_INVALID_ARG;
+  }
+  return MG_OK;
+}
+
+extern "C" {
+
+void mg_default_options(mg_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->transfer = MG_TRANSFER_BOXMG;
+  o->coarse = MG_COARSE_GALERKIN;
+  o->precision = MG_PREC_FP64;
+  o->nu1 = 2;
+  o->nu2 = 2;
+  o->omega = 0.6;
+  o->coarsest_level = 1;
+  o->inner_cycles = 8;
+  o->use_graphs = 1;
+}
+
+mg_status mg_hier_create(const mg_grid* grid, const mg_options* opt, mg_hier** out) {
+  if (!grid || !out) {
+    set_error("mg_hier_create: NULL argument");
+    return MG_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  mg_options o;
+  if (opt)
+    o = *opt;
+  else
+    mg_default_options(&o);
+  const Grid* g = reinterpret_cast<const Grid*>(grid);
+  if (o.coarsest_level < 1 || o.coarsest_level >= g->L || o.nu1 < 0 || o.nu2 < 0 || !(o.omega > 0.0) ||
+      o.transfer < 0 || o.transfer > 1 || o.coarse < 0 || o.coarse > 1 || o.precision < 0 || o.precision > 2) {
+    set_error("mg_hier_create: invalid options");
+    return MG_ERR_INVALID_ARG;
+  }
+  if (!g->uniform) {
+    set_error("mg_hier_create: adaptive grids are not supported by this hierarchy yet");
+    return MG_ERR_UNSUPPORTED;
+  }
+  try {
+    Hier* H = nullptr;
+    const mg_status st = create(g, o, &H);
+    if (st != MG_OK) return st;
+    *out = reinterpret_cast<mg_hier*>(H);
+  } catch (const std::bad_alloc&) {
+    set_error("mg_hier_create: out of host memory");
+    return MG_ERR_OOM;
+  }
+  return MG_OK;
+}
+
+mg_status mg_setup(mg_hier* h, const double* eps, void* stream) {
+  Hier* H = H_(h);
+  if (!H || !eps) {
+    set_error("mg_setup: NULL argument");
+    return MG_ERR_INVALID_ARG;
+  }
+  H->ready = false;
+  return run_setup(*H, eps, pick(*H, stream));
+}
+
+mg_status mg_smooth(mg_hier* h, int level, double* u, const double* b, int nu, void* stream) {
+  Hier* H = H_(h);
+  MG_CHECK(check_level(H, level, true));
+  if (!u || !b || nu < 0) {
+    set_error("mg_smooth: invalid argument");
+    return MG_ERR_INVALID_ARG;
+  }
+  smooth<double>(*H, level, u, b, H->lv[level].t, nu, pick(*H, stream));
+  return last_launch("mg_smooth");
+}
+
+mg_status mg_residual(mg_hier* h, int level, const double* u, const double* b, double* r, double* norm2_host,
+                      void* stream) {
+  Hier* H = H_(h);
+  MG_CHECK(check_level(H, level, true));
+  if (!u || !b || !r) {
+    set_error("mg_residual: NULL vector");
+    return MG_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = pick(*H, stream);
+  DevLevel& D = H->lv[level];
+  sweep<double>(*H, level, kResidual, u, b, r, D.partial, s);
+  if (norm2_host) {
+    reduce(D, H->d_scal + 3, s);
+    MG_TRY_CUDA(cudaMemcpyAsync(H->h_pin + 3, H->d_scal + 3, sizeof(double), cudaMemcpyDeviceToHost, s));
+    MG_TRY_CUDA(cudaStreamSynchronize(s));
+    *norm2_host = H->h_pin[3];
+  }
+  return last_launch("mg_residual");
+}
+
+static mg_status check_mixed(Hier* H, const char* what) {
+  if (!H->mixed) {
+    set_error(std::string(what) + ": needs a mixed-precision hierarchy");
+    return MG_ERR_INVALID_ARG;
+  }
+  return MG_OK;
+}
+
+mg_status mg_smooth_f32(mg_hier* h, int level, float* u, const float* b, int nu, void* stream) {
+  Hier* H = H_(h);
+  MG_CHECK(check_level(H, level, true));
+  MG_CHECK(check_mixed(H, "mg_smooth_f32"));
+  if (!u || !b || nu < 0) {
+    set_error("mg_smooth_f32: invalid argument");
+    return MG_ERR_INVALID_ARG;
+  }
+  smooth<float>(*H, level, u, b, H->lv[level].t32, nu, pick(*H, stream));
+  return last_launch("mg_smooth_f32");
+}
+
+mg_status mg_residual_f32(mg_hier* h, int level, const float* u, const float* b, float* r, double* norm2_host,
+                          void* stream) {
+  Hier* H = H_(h);
+  MG_CHECK(check_level(H, level, true));
+  MG_CHECK(check_mixed(H, "mg_residual_f32"));
+  if (!u || !b || !r) {
+    set_error("mg_residual_f32: NULL vector");
+    return MG_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = pick(*H, stream);
+  DevLevel& D = H->lv[level];
+  sweep<float>(*H, level, kResidual, u, b, r, D.partial, s);
+  if (norm2_host) {
+    reduce(D, H->d_scal + 3, s);
+    MG_TRY_CUDA(cudaMemcpyAsync(H->h_pin + 3, H->d_scal + 3, sizeof(double), cudaMemcpyDeviceToHost, s));
+    MG_TRY_CUDA(cudaStreamSynchronize(s));
+    *norm2_host = H->h_pin[3];
+  }
+  return last_launch("mg_residual_f32");
+}
+
+mg_status mg_vcycle_f32(mg_hier* h, float* u, const float* b, void* stream) {
+  Hier* H = H_(h);
+  MG_CHECK(check_level(H, H ? H->L : 0, true));
+  MG_CHECK(check_mixed(H, "mg_vcycle_f32"));
+  if (!u || !b) {
+    set_error("mg_vcycle_f32: NULL vector");
+    return MG_ERR_INVALID_ARG;
+  }
+  vcycle<float>(*H, H->L, u, b, pick(*H, stream));
+  return last_launch("mg_vcycle_f32");
+}
+
+mg_status mg_restrict(mg_hier* h, int fine_level, const double* r_fine, double* b_coarse, void* stream) {
+  Hier* H = H_(h);
+  MG_CHECK(check_level(H, fine_level, true));
+  if (fine_level == H->c || !r_fine || !b_coarse) {
+    set_error("mg_restrict: invalid argument");
+    return MG_ERR_INVALID_ARG;
+  }
+  transfer<double>(*H, fine_level, true, r_fine, b_coarse, pick(*H, stream));
+  return last_launch("mg_restrict");
+}
+
+mg_status mg_prolong(mg_hier* h, int fine_level, const double* e_coarse, double* u_fine, void* stream) {
+  Hier* H = H_(h);
+  MG_CHECK(check_level(H, fine_level, true));
+  if (fine_level == H->c || !e_coarse || !u_fine) {
+    set_error("mg_prolong: invalid argument");
+    return MG_ERR_INVALID_ARG;
+  }
+  transfer<double>(*H, fine_level, false, e_coarse, u_fine, pick(*H, stream));
+  return last_launch("mg_prolong");
+}
+
+mg_status mg_interpolate_hanging(mg_hier* h, int level, const double* u_coarse, double* u_fine, void* stream) {
+  Hier* H = H_(h);
+  MG_CHECK(check_level(H, level, false));
+  if (level == H->c || !u_coarse || !u_fine) {
+    set_error("mg_interpolate_hanging: invalid argument");
+    return MG_ERR_INVALID_ARG;
+  }
+  DevLevel& F = H->lv[level];
+  cudaStream_t s = pick(*H, stream);
+  if (H->dim == 2)
+    k_hanging<2, double><<<nblk(F.d.n_slots), kBlock, 0, s>>>(F.d, F.hang_idx, F.hang_w, u_coarse, u_fine);
+  else
+    k_hanging<3, double><<<nblk(F.d.n_slots), kBlock, 0, s>>>(F.d, F.hang_idx, F.hang_w, u_coarse, u_fine);
+  return last_launch("mg_interpolate_hanging");
+}
+
+mg_status mg_vcycle(mg_hier* h, double* u, const double* b, void* stream) {
+  Hier* H = H_(h);
+  MG_CHECK(check_level(H, H ? H->L : 0, true));
+  if (!u || !b) {
+    set_error("mg_vcycle: NULL vector");
+    return MG_ERR_INVALID_ARG;
+  }
+  vcycle<double>(*H, H->L, u, b, pick(*H, stream));
+  return last_launch("mg_vcycle");
+}
+
+mg_status mg_solve(mg_hier* h, double* u, const double* b, double rel_tol, int max_cycles, mg_solve_stats* stats,
+                   void* stream) {
+  Hier* H = H_(h);
+  MG_CHECK(check_level(H, H ? H->L : 0, true));
+  if (!u || !b || max_cycles < 0 || !(rel_tol >= 0.0)) {
+    set_error("mg_solve: invalid argument");
+    return MG_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = pick(*H, stream);
+  const auto t0 = std::chrono::steady_clock::now();
+  const mg_status st = H->mixed ? solve_mixed(*H, u, b, rel_tol, max_cycles, stats, s)
+                                : solve_fp64(*H, u, b, rel_tol, max_cycles, stats, s);
+  if (stats)
+    stats->solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  return st;
+}
+
+mg_status mg_get_stencils(mg_hier* h, int level, double* st, void* stream) {
+  Hier* H = H_(h);
+  MG_CHECK(check_level(H, level, true));
+  if (!st) {
+    set_error("mg_get_stencils: NULL output");
+    return MG_ERR_INVALID_ARG;
+  }
+  DevLevel& D = H->lv[level];
+  const double* ah = (level < H->L && H->galerkin) ? D.ahat : nullptr;
+  cudaStream_t s = pick(*H, stream);
+  if (H->dim == 2)
+    k_export_stencils<2><<<nblk(D.d.n_slots), kBlock, 0, s>>>(D.d, D.eps, ah, st, nullptr);
+  else
+    k_export_stencils<3><<<nblk(D.d.n_slots), kBlock, 0, s>>>(D.d, D.eps, ah, st, nullptr);
+  return last_launch("mg_get_stencils");
+}
+
+// brick-major planes -> offset-major export
+__global__ void k_planes_to_offset_major(mg::LevelDesc L, int K, const double* in, double* out) {
+  const int64_t s = blockIdx.x * static_cast<int64_t>(mg::kBlock) + threadIdx.x;
+  if (s >= L.n_slots) return;
+  for (int k = 0; k < K; ++k) out[k * L.n_slots + s] = in[mg::plane_index(L, s, k, K)];
+}
+__global__ void k_planes16_to_offset_major(mg::LevelDesc L, int K, const uint16_t* in, uint16_t* out) {
+  const int64_t s = blockIdx.x * static_cast<int64_t>(mg::kBlock) + threadIdx.x;
+  if (s >= L.n_slots) return;
+  for (int k = 0; k < K; ++k) out[k * L.n_slots + s] = in[mg::plane_index(L, s, k, K)];
+}
+
+mg_status mg_get_deltas(mg_hier* h, int level, double* a_hat, double* p_hat, void* stream) {
+  Hier* H = H_(h);
+  MG_CHECK(check_level(H, level, true));
+  if (level >= H->L) {
+    set_error("mg_get_deltas: the finest level stores no deltas");
+    return MG_ERR_INVALID_ARG;
+  }
+  DevLevel& D = H->lv[level];
+  cudaStream_t s = pick(*H, stream);
+  if (a_hat) {
+    if (!D.ahat) {
+      set_error("mg_get_deltas: no Galerkin deltas (coarse = redisc)");
+      return MG_ERR_INVALID_ARG;
+    }
+    k_planes_to_offset_major<<<nblk(D.d.n_slots), kBlock, 0, s>>>(D.d, ipow(3, H->dim), D.ahat, a_hat);
+  }
+  if (p_hat) {
+    if (!D.phat) {
+      set_error("mg_get_deltas: no BoxMG deltas (transfer = dlinear)");
+      return MG_ERR_INVALID_ARG;
+    }
+    k_planes_to_offset_major<<<nblk(D.d.n_slots), kBlock, 0, s>>>(D.d, ipow(5, H->dim), D.phat, p_hat);
+  }
+  return last_launch("mg_get_deltas");
+}
+
+mg_status mg_get_codes(mg_hier* h, int level, uint16_t* a_codes, float* a_scale, uint16_t* p_codes, float* p_scale,
+                       void* stream) {
+  Hier* H = H_(h);
+  MG_CHECK(check_level(H, level, true));
+  if (!H->mixed || level >= H->L) {
+    set_error("mg_get_codes: no codes (FP64 hierarchy or finest level)");
+    return MG_ERR_INVALID_ARG;
+  }
+  DevLevel& D = H->lv[level];
+  cudaStream_t s = pick(*H, stream);
+  const size_t ns = static_cast<size_t>(D.d.n_slots);
+  if (a_codes && D.a16)
+    k_planes16_to_offset_major<<<nblk(D.d.n_slots), kBlock, 0, s>>>(D.d, ipow(3, H->dim), D.a16, a_codes);
+  if (a_scale && D.ascale) MG_TRY_CUDA(cudaMemcpyAsync(a_scale, D.ascale, ns * sizeof(float), cudaMemcpyDeviceToDevice, s));
+  if (p_codes && D.p16)
+    k_planes16_to_offset_major<<<nblk(D.d.n_slots), kBlock, 0, s>>>(D.d, ipow(5, H->dim), D.p16, p_codes);
+  if (p_scale && D.pscale) MG_TRY_CUDA(cudaMemcpyAsync(p_scale, D.pscale, ns * sizeof(float), cudaMemcpyDeviceToDevice, s));
+  return last_launch("mg_get_codes");
+}
+
+mg_status mg_encode_deltas(int64_t n, int k, const double* delta, int fmt, uint16_t* codes, float* scale,
+                           void* stream) {
+  if (n < 0 || k <= 0 || (n > 0 && (!delta || !codes || !scale)) || (fmt != 1 && fmt != 2)) {
+    set_error("mg_encode_deltas: invalid argument");
+    return MG_ERR_INVALID_ARG;
+  }
+  if (n == 0) return MG_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (fmt == 1)
+    k_encode_rows<1><<<nblk(n), kBlock, 0, s>>>(n, k, delta, codes, scale);
+  else
+    k_encode_rows<2><<<nblk(n), kBlock, 0, s>>>(n, k, delta, codes, scale);
+  return last_launch("mg_encode_deltas");
+}
+
+void mg_destroy_hier(mg_hier* h) { free_hier(H_(h)); }
+
+}  // extern "C"

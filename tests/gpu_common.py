@@ -1,0 +1,131 @@
+"""Shared fixtures of the GPU parity tests: build a case on both sides from the same seeded inputs."""
+from __future__ import annotations
+
+import os
+
+import numpy as np
+
+from oracle import multigrid
+from oracle import spacetree as stt
+import synthetic as syn
+
+
+def lib():
+    import paper_1607_00648_gb300 as mg
+    from paper_1607_00648_gb300 import build
+
+    if not os.path.exists(mg._lib.LIB_PATH):
+        build.build()
+    mg.load()
+    return mg
+
+
+def eps_field(kind: str, L: int, dim: int, seed: int = 0) -> np.ndarray:
+    if kind == "const":
+        return syn.constant_eps(L, dim)
+    if kind == "checker":
+        return syn.checkerboard_eps(L, dim, seed=seed, tiles=9 if L >= 2 else 3)
+    if kind == "checker3":
+        return syn.checkerboard_eps(L, dim, seed=seed, tiles=3)
+    if kind == "sphere":
+        return syn.sphere_eps(L, dim)
+    if kind == "grf":
+        return syn.lognormal_grf_eps(L, dim, sigma=2.0, seed=1000 + seed)
+    raise ValueError(kind)
+
+
+class Case:
+    """One problem on the CPU oracle and on the GPU library, same slot numbering."""
+
+    def __init__(self, dim, L, eps_kind="checker", transfer="boxmg", coarse="galerkin", precision="fp64",
+                 seed=0, omega=0.6, nu1=2, nu2=2, load="uniform", oracle=True):
+        import torch
+
+        self.mg = lib()
+        self.torch = torch
+        self.dim, self.L = dim, L
+        self.eps = eps_field(eps_kind, L, dim, seed)
+        self.grid = self.mg.Grid(dim, L)
+        self.H = self.mg.Hierarchy(self.grid, transfer=transfer, coarse=coarse, precision=precision,
+                                   omega=omega, nu1=nu1, nu2=nu2)
+        eps_cat = self.grid.cells_to_concat({L: self.eps})
+        self.eps_dev = torch.from_numpy(eps_cat).cuda()
+        self.H.setup(self.eps_dev)
+        torch.cuda.synchronize()
+        self.tree = stt.Spacetree(dim, L) if oracle else None
+        self.O = (multigrid.Hierarchy(self.tree, {L: self.eps}, transfer=transfer, coarse=coarse, omega=omega,
+                                      nu1=nu1, nu2=nu2) if oracle else None)
+        if load == "sin":
+            bf = syn.sin_load(L, dim)
+        else:
+            bf = syn.uniform_load(L, dim, seed + 1)
+        self.b = self.grid.to_slots(L, bf)
+        self.b_dev = torch.from_numpy(self.b).cuda()
+
+    def n(self, level):
+        return self.grid.info(level).n_slots
+
+    def dof(self, level):
+        return self.grid.dof_mask(level)
+
+    def dev(self, a):
+        return self.torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+    def host(self, t):
+        self.torch.cuda.synchronize()
+        return t.cpu().numpy()
+
+    def abs_scale(self, level):
+        """Per-entry magnitude scale of the floating-point sums behind a level's stencils.
+
+        S_L = |A_L| on the finest level and S_{l-1} = |P|^T S_l |P| below (Galerkin):
+        the forward error of a sum is bounded by (number of terms) * u * sum |terms|
+        (Higham), so two correct FP64 evaluations of an entry differ by at most a small
+        multiple of u * S.  Returned in the 3^d stencil view (slot x offset).
+        """
+        from oracle import fem
+
+        if not hasattr(self, "_S"):
+            S = {self.L: abs(self.O.ops[self.L].A)}
+            for lv in range(self.L - 1, 0, -1):
+                if self.O.coarse == "galerkin":
+                    P = abs(self.O.ops[lv + 1].P)
+                    S[lv] = (P.T @ S[lv + 1] @ P).tocsr()
+                else:
+                    S[lv] = abs(self.O.ops[lv].A)
+            self._S = S
+        st = np.maximum(fem.stencils(self.tree, level, self._S[level]), np.abs(self.O.ops[level].st))
+        # floor: 1e-4 of the row's scale (the oracle's quadrature leaves ~1e-17 where the
+        # element matrix has exact zeros, e.g. 3D face neighbours)
+        return np.maximum(st, 1e-4 * st.max(axis=1, keepdims=True))
+
+    def amplification(self):
+        """Largest cancellation factor sum|terms| / |sum| of a coarse Galerkin diagonal."""
+        if not hasattr(self, "_amp"):
+            amp = 1.0
+            for lv in range(1, self.L):
+                S = self.abs_scale(lv)
+                dof = self.dof(lv)
+                c = 3**self.dim // 2
+                amp = max(amp, float((S[dof, c] / np.abs(self.O.ops[lv].st[dof, c])).max()))
+            self._amp = amp
+        return self._amp
+
+    def random_vec(self, level, seed):
+        rng = np.random.default_rng(seed)
+        v = rng.standard_normal(self.n(level))
+        v[~self.dof(level)] = 0.0
+        return v
+
+
+def rel_inf(a, b):
+    """max |a - b| / max |b| (infinity-norm relative error)."""
+    den = np.abs(b).max()
+    return np.abs(a - b).max() / (den if den > 0 else 1.0)
+
+
+def rowwise_rel(a, b):
+    """max over rows of max |a - b| / max |b| within the row."""
+    den = np.abs(b).max(axis=1)
+    den = np.where(den > 0, den, 1.0)
+    return (np.abs(a - b).max(axis=1) / den).max()

@@ -1,0 +1,252 @@
+"""GPU parity of the CUDA hot path (through the C ABI) against the CPU oracle.
+
+FP64 results must match the oracle within 1e-12 relative (infinity norm over the
+compared vector); integer / code outputs bit for bit.  Galerkin coarse stencils
+are sums whose terms can cancel (on the 1:1e-4 checkerboard the level-1
+diagonal is 5.8e7 times smaller than the sum of the magnitudes of its terms), so
+their tolerance is 1e-12 times the magnitude scale |P|^T|A||P| of each entry, and
+V-cycle / solve outputs get 1e-12 times the largest such cancellation factor
+(1 on well-conditioned cases, which therefore stay at plain 1e-12).  Cases
+span several bricks (2D level 4: 9 bricks of 27^2 cells; 3D level 3: 27 bricks of
+9^3 cells) and the padded tail of every brick.
+"""
+import numpy as np
+import pytest
+
+from oracle import codec
+from tests.gpu_common import Case, lib, rel_inf, rowwise_rel
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-12
+
+CASES = [
+    (2, 4, "checker", "boxmg", "galerkin"),
+    (2, 4, "grf", "boxmg", "galerkin"),
+    (3, 3, "sphere", "boxmg", "galerkin"),
+    (2, 4, "const", "dlinear", "redisc"),
+    (3, 3, "grf", "dlinear", "galerkin"),
+]
+
+
+@pytest.fixture(scope="module", params=CASES, ids=lambda c: "-".join(map(str, c)))
+def case(request):
+    dim, L, eps, tr, co = request.param
+    return Case(dim, L, eps, tr, co)
+
+
+def test_stencils_match(case):
+    K = 3**case.dim
+    for lv in range(1, case.L + 1):
+        n = case.n(lv)
+        out = case.torch.empty(K * n, dtype=case.torch.float64, device="cuda")
+        case.H.get_stencils(lv, out)
+        st = case.host(out).reshape(K, n).T
+        dof = case.dof(lv)
+        # entries pointing past the upper boundary (no slot) multiply the Dirichlet value only
+        has = case.grid.tables(lv)["nbr"] >= 0
+        scale = case.abs_scale(lv)
+        err = (np.abs(st - case.O.ops[lv].st) * has)[dof] / np.maximum(scale[dof], 1e-300)
+        assert err.max() < TOL, (lv, err.max())
+
+
+def test_deltas_match(case):
+    if case.O.coarse != "galerkin" and case.O.transfer != "boxmg":
+        pytest.skip("no deltas stored")
+    for lv in range(1, case.L):
+        n = case.n(lv)
+        dof = case.dof(lv)
+        if case.O.coarse == "galerkin":
+            a = case.torch.empty(3**case.dim * n, dtype=case.torch.float64, device="cuda")
+            case.H.get_deltas(lv, a_hat=a)
+            ah = case.host(a).reshape(-1, n).T
+            scale = case.abs_scale(lv)
+            assert (np.abs(ah - case.O.ops[lv].a_hat)[dof] / np.maximum(scale[dof], 1e-300)).max() < TOL
+        if case.O.transfer == "boxmg":
+            p = case.torch.empty(5**case.dim * n, dtype=case.torch.float64, device="cuda")
+            case.H.get_deltas(lv, p_hat=p)
+            ph = case.host(p).reshape(-1, n).T
+            assert np.abs(ph - case.O.ops[lv + 1].p_hat)[dof].max() < TOL
+
+
+@pytest.mark.parametrize("nu", [1, 2, 3])
+def test_smoother_matches(case, nu):
+    for lv in (case.L, case.L - 1):
+        u = case.random_vec(lv, 10 + lv)
+        b = case.random_vec(lv, 20 + lv) if lv < case.L else case.b
+        ud = case.dev(u)
+        case.H.smooth(lv, ud, case.dev(b), nu)
+        ref = case.O.smooth(lv, u, b, nu)
+        assert rel_inf(case.host(ud), ref) < TOL
+
+
+def test_residual_and_norm_match(case):
+    for lv in (case.L, case.L - 1):
+        u = case.random_vec(lv, 30 + lv)
+        b = case.random_vec(lv, 40 + lv)
+        r = case.torch.zeros(case.n(lv), dtype=case.torch.float64, device="cuda")
+        n2 = case.H.residual(lv, case.dev(u), case.dev(b), r, want_norm=True)
+        ref = case.O.residual(lv, u, b)
+        assert rel_inf(case.host(r), ref) < TOL
+        assert abs(n2 - float(ref @ ref)) <= 1e-12 * float(ref @ ref)
+
+
+def test_transfers_match(case):
+    L = case.L
+    r = case.random_vec(L, 50)
+    bc = case.torch.zeros(case.n(L - 1), dtype=case.torch.float64, device="cuda")
+    case.H.restrict(L, case.dev(r), bc)
+    assert rel_inf(case.host(bc), case.O.restrict(L, r)) < TOL
+    e = case.random_vec(L - 1, 60)
+    u = case.random_vec(L, 70)
+    ud = case.dev(u)
+    case.H.prolong(L, case.dev(e), ud)
+    ref = u + np.where(case.dof(L), case.O.prolong(L, e), 0.0)
+    assert rel_inf(case.host(ud), ref) < TOL
+
+
+def test_vcycle_matches(case):
+    u = case.random_vec(case.L, 80)
+    ud = case.dev(u)
+    case.H.vcycle(ud, case.b_dev)
+    ref = case.O.vcycle(u, case.b)
+    assert rel_inf(case.host(ud), ref) < TOL * case.amplification()
+
+
+def test_solve_matches_oracle(case):
+    u = case.torch.zeros(case.n(case.L), dtype=case.torch.float64, device="cuda")
+    res = case.H.solve(u, case.b_dev, rel_tol=1e-10, max_cycles=400)
+    ref, hist = case.O.solve(case.b, 1e-10, 400)
+    assert res["cycles"] == len(hist) - 1
+    assert rel_inf(case.host(u), ref) < 10 * TOL * case.amplification()
+    assert res["rel_residual"] <= 1e-10
+    assert np.allclose(res["history"], hist[1:] / hist[0], rtol=10 * TOL * case.amplification(),
+                       atol=1e-13)  # b - A u cancels: ~1e-16 ||b|| absolute rounding in each residual
+
+
+@pytest.mark.parametrize("dim,L,eps", [(2, 4, "checker"), (3, 3, "sphere")])
+def test_fp32_finest_sweep_within_fp32_rounding(dim, L, eps):
+    # finest level: no deltas, so the FP32 sweep differs from the FP64 oracle by FP32
+    # rounding only; bound: 64 u32 * (|u| + omega |D^-1| (|b| + |A| |u|)) per vertex
+    c = Case(dim, L, eps, precision="mixed_bf16")
+    torch = c.torch
+    u = c.random_vec(L, 5)
+    ud = torch.from_numpy(u.astype(np.float32)).cuda()
+    bd = c.b_dev.float()
+    c.H.smooth_f32(L, ud, bd, 1)
+    u32 = u.astype(np.float32).astype(np.float64)
+    b32 = c.b.astype(np.float32).astype(np.float64)
+    ref = c.O.smooth(L, u32, b32, 1)
+    o = c.O.ops[L]
+    bound = np.abs(u32) + c.O.omega * (np.abs(b32) + abs(o.A) @ np.abs(u32)) / o.diag
+    err = np.abs(c.host(ud).astype(np.float64) - ref)
+    assert np.all(err <= 64 * 2.0**-24 * bound + 1e-30)
+
+
+def test_encoder_matches_oracle_bit_exact():
+    mg = lib()
+    import torch
+
+    rng = np.random.default_rng(8)
+    d = rng.standard_normal((4099, 27)) * np.exp(rng.uniform(-40, 5, (4099, 1)))
+    d[5] = 0.0
+    d[6, 3] = -1e-300
+    dd = torch.from_numpy(d).cuda()
+    for fmt, name in ((1, "bf16"), (2, "fp16")):
+        codes = torch.empty(d.shape, dtype=torch.int16, device="cuda")
+        scale = torch.empty(d.shape[0], dtype=torch.float32, device="cuda")
+        mg.encode_deltas(dd, codes, scale, fmt)
+        torch.cuda.synchronize()
+        qo, so = codec.encode(d, name)
+        assert np.array_equal(codes.cpu().numpy().view(np.uint16), qo)
+        assert np.array_equal(scale.cpu().numpy().view(np.uint32), so.view(np.uint32))
+
+
+def test_mixed_codes_are_the_encoding_of_the_fp64_deltas():
+    for fmt, prec in (("bf16", "mixed_bf16"), ("fp16", "mixed_fp16")):
+        c = Case(2, 4, "checker", precision=prec, oracle=False)
+        torch = c.torch
+        for lv in range(1, 4):
+            n = c.n(lv)
+            a = torch.empty(9 * n, dtype=torch.float64, device="cuda")
+            p = torch.empty(25 * n, dtype=torch.float64, device="cuda")
+            c.H.get_deltas(lv, a_hat=a, p_hat=p)
+            ac = torch.empty(9 * n, dtype=torch.int16, device="cuda")
+            pc = torch.empty(25 * n, dtype=torch.int16, device="cuda")
+            asc = torch.empty(n, dtype=torch.float32, device="cuda")
+            psc = torch.empty(n, dtype=torch.float32, device="cuda")
+            c.H.get_codes(lv, ac, asc, pc, psc)
+            for dlt, cod, sc, K in ((a, ac, asc, 9), (p, pc, psc, 25)):
+                q, s = codec.encode(c.host(dlt).reshape(K, n).T, fmt)
+                assert np.array_equal(c.host(cod).view(np.uint16).reshape(K, n).T, q)
+                assert np.array_equal(c.host(sc).view(np.uint32), s.view(np.uint32))
+
+
+@pytest.mark.parametrize("prec", ["mixed_bf16", "mixed_fp16"])
+@pytest.mark.parametrize("dim,L,eps", [(2, 4, "checker"), (3, 3, "sphere"), (2, 5, "grf")])
+def test_mixed_solve_reaches_fp64_solution(dim, L, eps, prec):
+    c = Case(dim, L, eps, precision=prec)
+    u = c.torch.zeros(c.n(L), dtype=c.torch.float64, device="cuda")
+    res = c.H.solve(u, c.b_dev, rel_tol=1e-10, max_cycles=2000)
+    assert res["rel_residual"] <= 1e-10
+    # FP64 residual of the returned iterate, by the oracle's operator
+    ug = c.host(u)
+    r = c.O.residual(L, ug, c.b)
+    assert np.linalg.norm(r) <= 1.0001e-10 * np.linalg.norm(c.b)
+    # stated per-result error of the mixed path: within 1e-8 (infinity-norm relative)
+    # of the exact discrete solution, next to an FP64 residual drop of 1e-10
+    ud = c.O.direct(c.b)
+    assert rel_inf(ug, ud) <= 1e-8
+
+
+def test_full_size_config2_sampled_parity():
+    # 2D level 6 (729^2 cells, 529,984 DoFs), seeded 9x9 checkerboard {1, 1e-4},
+    # BoxMG + Galerkin FP64: compare one Jacobi sweep, one V-cycle and the setup
+    c = Case(2, 6, "checker")
+    L = 6
+    u = c.random_vec(L, 99)
+    ud = c.dev(u)
+    c.H.smooth(L, ud, c.b_dev, 2)
+    assert rel_inf(c.host(ud), c.O.smooth(L, u, c.b, 2)) < TOL
+    ud = c.dev(u)
+    c.H.vcycle(ud, c.b_dev)
+    assert rel_inf(c.host(ud), c.O.vcycle(u, c.b)) < TOL * c.amplification()
+    for lv in (5, 4, 1):
+        n = c.n(lv)
+        out = c.torch.empty(9 * n, dtype=c.torch.float64, device="cuda")
+        c.H.get_stencils(lv, out)
+        st = c.host(out).reshape(9, n).T
+        dof = c.dof(lv)
+        has = c.grid.tables(lv)["nbr"] >= 0
+        err = (np.abs(st - c.O.ops[lv].st) * has)[dof] / np.maximum(c.abs_scale(lv)[dof], 1e-300)
+        assert err.max() < TOL
+
+
+def test_edge_cases():
+    mg = lib()
+    import torch
+
+    # smallest hierarchy: level 2 over the coarsest level 1
+    c = Case(2, 2, "checker3")
+    u = torch.zeros(c.n(2), dtype=torch.float64, device="cuda")
+    res = c.H.solve(u, c.b_dev, rel_tol=1e-12, max_cycles=200)
+    assert rel_inf(c.host(u), c.O.direct(c.b)) < 1e-10
+    # zero right-hand side: converged at once with u = 0
+    z = torch.zeros_like(c.b_dev)
+    res = c.H.solve(u, z, rel_tol=1e-10, max_cycles=10)
+    assert res["cycles"] == 0 and float(u.abs().max()) == 0.0
+    # nu = 0 smoothing is the identity
+    v = c.dev(c.random_vec(2, 3))
+    v0 = v.clone()
+    c.H.smooth(2, v, c.b_dev, 0)
+    assert torch.equal(v, v0)
+    # non-finite data is reported, not propagated silently
+    bn = c.b_dev.clone()
+    bn[int(np.nonzero(c.dof(2))[0][0])] = float("nan")
+    res = c.H.solve(u, bn, rel_tol=1e-10, max_cycles=10, raise_on_fail=False)
+    assert res["status"] == 6
+    # invalid arguments
+    with pytest.raises(mg.MgError):
+        c.H.smooth(7, v, c.b_dev, 1)
+    with pytest.raises(mg.MgError):
+        mg.Hierarchy(c.grid, coarsest_level=2)

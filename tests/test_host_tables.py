@@ -1,0 +1,98 @@
+"""Host-side parity of the C-ABI library with the oracle (no GPU needed).
+
+The grid builder (mg_create_grid / mg_grid_tables) is plain host C++; its level
+tables must equal the oracle's independently computed ones bit for bit.
+"""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import spacetree as stt
+import synthetic as syn
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="session")
+def mg():
+    import paper_1607_00648_gb300 as mgpkg
+    from paper_1607_00648_gb300 import build
+
+    if not os.path.exists(mgpkg._lib.LIB_PATH):
+        build.build()
+    mgpkg.load()
+    return mgpkg
+
+
+def test_library_exports_every_declared_symbol(mg):
+    header = open(os.path.join(ROOT, "include", "mg.h")).read()
+    declared = set(re.findall(r"^\s*(?:mg_status|void|const char\*)\s+(mg_\w+)\s*\(", header, re.M))
+    assert len(declared) >= 20
+    lib = ctypes.CDLL(mg._lib.LIB_PATH)
+    for name in sorted(declared):
+        assert hasattr(lib, name), name
+    assert declared <= set(mg._lib.symbols())
+
+
+def _compare_level(g, tree, level):
+    t = g.tables(level)
+    lv = tree.levels[level]
+    inf = g.info(level)
+    assert inf.n_slots == lv.n_slots and inf.n_bricks == lv.n_bricks
+    assert inf.brick_edge == lv.B and inf.slots_per_brick == lv.S
+    assert inf.n_dofs == int(lv.dof.sum())
+    assert np.array_equal(t["coords"], lv.coords)
+    assert np.array_equal(t["vflags"], lv.vflags)
+    assert np.array_equal(t["cflags"], lv.cflags)
+    assert np.array_equal(t["nbr"], lv.nbr)
+    assert np.array_equal(t["cell_vertices"], lv.cell_vertices)
+    assert np.array_equal(t["brick_roots"], lv.brick_roots)
+    assert np.array_equal(t["brick_nbr"], lv.brick_nbr)
+    assert np.array_equal(t["parent"], tree.parent_map(level))
+    assert np.array_equal(t["child"], tree.child_map(level))
+    hi, hw = tree.hanging_map(level)
+    assert np.array_equal(t["hang_idx"], hi)
+    assert np.array_equal(t["hang_w"].view(np.uint64), hw.view(np.uint64))
+
+
+@pytest.mark.parametrize("dim,L", [(2, 3), (2, 4), (3, 2), (3, 3)])
+def test_uniform_tables_bit_exact(mg, dim, L):
+    g = mg.Grid(dim, L)
+    tree = stt.Spacetree(dim, L)
+    for level in range(L + 1):
+        _compare_level(g, tree, level)
+
+
+def test_adaptive_tables_bit_exact_2d(mg):
+    m1 = np.zeros((3, 3), bool)
+    m1[1, 1] = m1[2, 1] = m1[0, 0] = True
+    m2 = np.zeros((9, 9), bool)
+    m2[4, 4] = m2[3, 4] = m2[0, 1] = True
+    masks = {1: m1, 2: m2}
+    g = mg.Grid(2, 3, masks)
+    tree = stt.Spacetree(2, 3, masks)
+    for level in range(4):
+        _compare_level(g, tree, level)
+
+
+def test_adaptive_tables_bit_exact_3d_shell(mg):
+    # the sphere-shell refinement of the adaptive 3D workload, one level lower
+    masks = {2: syn.sphere_shell_mask(2, 3)}
+    g = mg.Grid(3, 3, masks)
+    tree = stt.Spacetree(3, 3, masks)
+    assert tree.levels[3].vflags.astype(bool).any()
+    for level in range(4):
+        _compare_level(g, tree, level)
+
+
+def test_invalid_arguments_are_rejected(mg):
+    with pytest.raises(mg.MgError):
+        mg.Grid(4, 2)
+    with pytest.raises(mg.MgError):
+        mg.Grid(2, 0)
+    g = mg.Grid(2, 2)
+    with pytest.raises(mg.MgError):
+        g.info(5)
