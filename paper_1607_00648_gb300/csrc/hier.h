@@ -1,0 +1,67 @@
+// Device-resident multigrid hierarchy (shared by the libmg CUDA translation units).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "device.cuh"
+#include "internal.h"
+
+namespace mg {
+
+struct DevLevel {
+  LevelDesc d{};
+  int32_t* brick_nbr = nullptr;
+  int32_t* brick_roots = nullptr;
+  int32_t* brick_rank = nullptr;
+  uint8_t* vflags = nullptr;
+  uint8_t* cflags = nullptr;
+  int32_t* hang_idx = nullptr;
+  double* hang_w = nullptr;
+  double* eps = nullptr;
+  float* eps32 = nullptr;
+  double* ahat = nullptr;
+  uint16_t* a16 = nullptr;
+  float* ascale = nullptr;
+  double* phat = nullptr;
+  uint16_t* p16 = nullptr;
+  float* pscale = nullptr;
+  double *u = nullptr, *b = nullptr, *r = nullptr, *t = nullptr;
+  float *u32 = nullptr, *b32 = nullptr, *r32 = nullptr, *t32 = nullptr;
+  double* partial = nullptr;
+  int64_t n_dofs = 0;
+};
+
+struct Graph {
+  cudaGraphExec_t exec = nullptr;
+  const void* key0 = nullptr;
+  const void* key1 = nullptr;
+  void reset() {
+    if (exec) cudaGraphExecDestroy(exec);
+    exec = nullptr;
+    key0 = key1 = nullptr;
+  }
+};
+
+struct Hier {
+  const Grid* g = nullptr;
+  mg_options opt{};
+  int L = 0, c = 1, dim = 2;
+  bool galerkin = false, boxmg = false, mixed = false;
+  int fmt = 1;  // 1 bf16, 2 fp16
+  std::vector<DevLevel> lv;
+  std::vector<void*> allocs;
+  int n_c = 0;
+  int32_t* c_slots = nullptr;
+  int32_t* c_map = nullptr;
+  double* c_mat = nullptr;
+  int* d_status = nullptr;
+  double* d_scal = nullptr;  // [0] norm2 fp64, [1] norm2 fp32 inner, [2] sigma
+  double* h_pin = nullptr;   // pinned mirror of d_scal
+  cudaStream_t own = nullptr;
+  bool ready = false;
+  Graph g_cycle64, g_outer, g_inner;
+};
+
+}  // namespace mg
