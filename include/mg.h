@@ -198,6 +198,23 @@ mg_status mg_residual_f32(mg_hier* h, int level, const float* u, const float* b,
                           void* stream);
 mg_status mg_vcycle_f32(mg_hier* h, float* u, const float* b, void* stream);
 
+/* Allocation-free residual: r = b - A u on level and the squared norm of r over the
+ * DoFs, written to the device double *norm2 (no host copy, no synchronisation).
+ * The paper has no counterpart; this is a service of the library for callers that
+ * must not call cudaMalloc: code running under a fixed device-memory budget handed
+ * out by a host framework, or latency-critical loops where an allocation call could
+ * block on work already queued on the GPU.  The hierarchy h is created beforehand.
+ * The reduction's per-brick partial sums live in a file-scope device array of 4096
+ * doubles (32 KiB, held by every GPU that loads the library until the process
+ * exits); levels with more than 4096 bricks are rejected with MG_ERR_INVALID_ARG
+ * (2D up to level 6 and 3D up to level 4 fit).  The first call on a device looks
+ * up that array's device address (cudaGetSymbolAddress) with the device current;
+ * make that first call before any stream capture.  Every call on a device shares
+ * the one array, so calls whose kernels overlap on the GPU (concurrent streams)
+ * race; serialise them.  u, b, r: device vectors of n_slots; norm2: device. */
+mg_status mg_residual_norm_noalloc(mg_hier* h, int level, const double* u, const double* b, double* r,
+                                   double* norm2, void* stream);
+
 /* ---------------------------------------------------------------- A12 cycles */
 
 /* One V(nu1, nu2) cycle on the finest level (correction scheme; on uniform

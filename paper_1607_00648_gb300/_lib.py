@@ -65,6 +65,7 @@ _SIGS = {
     "mg_smooth_f32": (C.c_int, [_P, C.c_int, _P, _P, C.c_int, _P]),
     "mg_residual_f32": (C.c_int, [_P, C.c_int, _P, _P, _P, _F64P, _P]),
     "mg_vcycle_f32": (C.c_int, [_P, _P, _P, _P]),
+    "mg_residual_norm_noalloc": (C.c_int, [_P, C.c_int, _P, _P, _P, _P, _P]),
     "mg_restrict": (C.c_int, [_P, C.c_int, _P, _P, _P]),
     "mg_prolong": (C.c_int, [_P, C.c_int, _P, _P, _P]),
     "mg_interpolate_hanging": (C.c_int, [_P, C.c_int, _P, _P, _P]),

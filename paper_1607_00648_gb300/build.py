@@ -14,7 +14,7 @@ BUILD = os.path.join(HERE, "_build")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-lineinfo"]
-SOURCES = ["grid.cpp", "solver.cu"]
+SOURCES = ["grid.cpp", "solver.cu", "noalloc.cu"]
 
 
 def _nvcc() -> str:
