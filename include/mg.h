@@ -142,8 +142,10 @@ typedef struct mg_options {
   double omega;           /* Jacobi damping (Alg. 1 smoothing update) */
   int32_t coarsest_level; /* level solved directly (FP64 Cholesky), 1 <= c < max_level */
   int32_t inner_cycles;   /* mixed: FP32 V-cycles per refinement step */
-  int32_t use_graphs;     /* capture cycles in CUDA graphs */
-  int32_t reserved;
+  int32_t use_graphs;     /* host-stepped solve: capture cycles in CUDA graphs */
+  int32_t persistent;     /* 1: whole solve in one cooperative persistent launch;
+                             0: host-stepped, CUDA-graph-captured cycles (default: on GB300 a
+                             dependent graph kernel costs ~0.6 us, a grid-wide barrier ~1.2 us) */
 } mg_options;
 
 void mg_default_options(mg_options* opt); /* BoxMG, Galerkin, FP64, V(2,2), omega 0.6, coarsest 1 */

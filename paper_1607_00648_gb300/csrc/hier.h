@@ -10,6 +10,8 @@
 
 namespace mg {
 
+constexpr int kHistCap = 4096;
+
 struct DevLevel {
   LevelDesc d{};
   int32_t* brick_nbr = nullptr;
@@ -30,6 +32,7 @@ struct DevLevel {
   double *u = nullptr, *b = nullptr, *r = nullptr, *t = nullptr;
   float *u32 = nullptr, *b32 = nullptr, *r32 = nullptr, *t32 = nullptr;
   double* partial = nullptr;
+  unsigned* counter = nullptr;
   int64_t n_dofs = 0;
 };
 
@@ -59,6 +62,10 @@ struct Hier {
   int* d_status = nullptr;
   double* d_scal = nullptr;  // [0] norm2 fp64, [1] norm2 fp32 inner, [2] sigma
   double* h_pin = nullptr;   // pinned mirror of d_scal
+  double* d_hist = nullptr;  // persistent solve: history, outputs, parameter block
+  int* d_pint = nullptr;
+  double* d_pdbl = nullptr;
+  void* d_psolve = nullptr;
   cudaStream_t own = nullptr;
   bool ready = false;
   Graph g_cycle64, g_outer, g_inner;

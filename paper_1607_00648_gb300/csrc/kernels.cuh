@@ -1,13 +1,15 @@
 // Hot-path kernels: in-situ stencil sweeps (A2-A4), restriction (A5), prolongation
 // (A6), hanging interpolation (A7) and reductions, templated on dimension,
-// arithmetic type and delta storage.
+// arithmetic type, delta storage and the (compile-time) brick edge.
 #pragma once
+
+#include <type_traits>
 
 #include "device.cuh"
 
 namespace mg {
 
-enum SweepOp { kJacobi = 0, kResidual = 1 };
+enum SweepOp { kJacobi = 0, kResidual = 1, kJacobiNorm = 2 };  // kJacobiNorm: Jacobi + sum of r^2
 
 template <typename T>
 struct SweepArgs {
@@ -19,157 +21,266 @@ struct SweepArgs {
   const void* ahat;     // A_hat planes (3^d per vertex) or nullptr
   const float* ascale;  // per-vertex scale of 16-bit codes
   T omega;
-  double* partial;      // per-CTA partial sum of r^2 (residual op), nullable
+  double* partial;      // per-CTA partial sums of r^2 (residual op), nullable
+  unsigned* counter;    // completion counter for the fused final sum, nullable
+  double* norm2;        // fused final sum of r^2 (written by the last CTA), nullable
+  int R;                // slab thickness along the last axis (divides B)
 };
 
-// Deterministic CTA reduction of one double per thread into partial[blockIdx.x].
-__device__ __forceinline__ void block_reduce_store(double v, double* partial) {
+// Deterministic CTA reduction of one double per thread; thread 0 returns the sum.
+__device__ __forceinline__ double block_sum(double v) {
   __shared__ double warp_sums[kBlock / 32];
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (lane == 0) warp_sums[warp] = v;
   __syncthreads();
+  double s = 0.0;
   if (threadIdx.x == 0) {
-    double s = 0.0;
-#pragma unroll
-    for (int w = 0; w < kBlock / 32; ++w) s += warp_sums[w];
-    partial[blockIdx.x] = s;
+    const int nw = (blockDim.x + 31) >> 5;
+    for (int w = 0; w < nw; ++w) s += warp_sums[w];
+  }
+  return s;
+}
+
+// Stores this CTA's partial sum; the last CTA to finish (counter ticket) adds all
+// partials in index order, so the result does not depend on scheduling.
+__device__ __forceinline__ void store_partial_and_finish(double v, double* partial, unsigned* counter,
+                                                         double* norm2) {
+  const unsigned nblocks = gridDim.x * gridDim.y;
+  const unsigned bid = blockIdx.x * gridDim.y + blockIdx.y;
+  const double s = block_sum(v);
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+    partial[bid] = s;
+    last = false;
+    if (counter) {
+      __threadfence();
+      last = atomicAdd(counter, 1u) == nblocks - 1;
+    }
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double t = 0.0;
+  for (unsigned i = threadIdx.x; i < nblocks; i += blockDim.x) t += static_cast<volatile double*>(partial)[i];
+  const double tot = block_sum(t);
+  if (threadIdx.x == 0) {
+    norm2[0] = tot;
+    *counter = 0u;  // ready for the next launch (graph replays included)
   }
 }
 
-// One CTA per brick.  The brick's vertex values with a one-vertex halo and the
-// coefficients of all cells touching the brick are staged in shared memory;
-// each DoF vertex then rebuilds its 3^d stencil from the 2^d adjacent cells
-// (element-wise split of Sect. 4, summed per Hamming class), adds the stored
-// delta A_hat on coarse levels (Sect. 5), and applies either the damped
-// Jacobi update (Alg. 1) or the residual b - A u.
-template <int DIM, typename T, int AMODE, int OP>
-__global__ void __launch_bounds__(kBlock) k_sweep(SweepArgs<T> a) {
-  constexpr int N3 = cpow(3, DIM);
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const LevelDesc& L = a.L;
-  const int B = L.B, Bu = B + 2, Be = B + 1;
-  const int nu_tile = DIM == 2 ? Bu * Bu : Bu * Bu * Bu;
-  const int ne_tile = DIM == 2 ? Be * Be : Be * Be * Be;
-  T* su = reinterpret_cast<T*>(smem_raw);
-  T* se = su + nu_tile;
-  const int64_t brick = blockIdx.x;
-  const int32_t* bn = L.brick_nbr + brick * N3;
+// 1/D by Newton-Raphson from an FP32 seed (x_{k+1} = x_k (2 - D x_k), quadratic
+// convergence: 2^-22 -> 2^-44 -> 2^-88, i.e. correctly rounded up to the last bit
+// or two), cheaper than an FP64 division on GB300's scarce FP64 units.
+__device__ __forceinline__ double recip_nr(double D) {
+  const double a = fabs(D);
+  if (!(a > 1e-30 && a < 1e30)) return 1.0 / D;
+  double y = static_cast<double>(__fdividef(1.0f, static_cast<float>(D)));
+  double e = fma(-D, y, 1.0);
+  y = fma(y, e, y);
+  e = fma(-D, y, 1.0);
+  return fma(y, e, y);
+}
+__device__ __forceinline__ float recip_nr(float D) { return 1.0f / D; }
 
-  // vertex values, local coordinates -1 .. B
-  for (int t = threadIdx.x; t < nu_tile; t += kBlock) {
-    int rem = t, nidx = 0, mul = 1, lm = 1;
-    int64_t li = 0;
+// One CTA per (brick, slab of R rows / planes along the last axis).  The slab's
+// vertex values with a one-vertex halo and the coefficients of all cells touching
+// it are staged in shared memory; each DoF vertex then rebuilds its 3^d stencil
+// from the 2^d adjacent cells (element-wise split of Sect. 4, summed per Hamming
+// class), adds the stored delta A_hat on coarse levels (Sect. 5), and applies
+// either the damped Jacobi update (Alg. 1) or the residual b - A u.
+template <int DIM, typename T, int AMODE, int OP, int B>
+__device__ __forceinline__ double sweep_item(const SweepArgs<T>& a, int64_t brick, int slab,
+                                             unsigned char* smem_raw) {
+  constexpr int N3 = cpow(3, DIM);
+  constexpr int Bu = B + 2, Be = B + 1;
+  constexpr int PLANE = DIM == 2 ? B : B * B;      // vertices per row / plane
+  constexpr int UPL = DIM == 2 ? Bu : Bu * Bu;     // tile entries per row / plane (u)
+  constexpr int EPL = DIM == 2 ? Be : Be * Be;     // (eps)
+  const LevelDesc& L = a.L;
+  const int R = a.R;
+  const int z0 = slab * R;
+  T* su = reinterpret_cast<T*>(smem_raw);
+  T* se = su + UPL * (R + 2);
+  const int64_t base = brick * L.S;
+  __syncthreads();  // the tile may still be read by a previous item of this CTA
+  const int32_t* bn = L.brick_nbr + brick * N3;
+  const int nt = blockDim.x;
+
+  // interior of the slab: contiguous slots of this brick (vertex values and the
+  // coefficients of the cells they own).  A whole brick starts on a 16-byte
+  // boundary (slots_per_brick is a multiple of 32), so it is read with 16-byte
+  // vector loads; slabs of a split brick use scalar loads.
+  const int nin = R * PLANE;
+  auto put = [&](int s, T uv, T ev) {
+    const int x = s % B;
+    const int y = DIM == 2 ? s / B : (s / B) % B;
+    const int zl = s / PLANE - z0;
+    const int tu = DIM == 2 ? (zl + 1) * Bu + (x + 1) : ((zl + 1) * Bu + (y + 1)) * Bu + (x + 1);
+    const int te = DIM == 2 ? (zl + 1) * Be + (x + 1) : ((zl + 1) * Be + (y + 1)) * Be + (x + 1);
+    su[tu] = uv;
+    se[te] = ev;
+  };
+  constexpr int VEC = 16 / sizeof(T);
+  using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+  const bool vec_ok = R == B && ((reinterpret_cast<uintptr_t>(a.u) | reinterpret_cast<uintptr_t>(a.eps)) & 15) == 0;
+  if (vec_ok) {
+    const V* up = reinterpret_cast<const V*>(a.u + base);
+    const V* ep = reinterpret_cast<const V*>(a.eps + base);
+    const int nvec = (nin + VEC - 1) / VEC;
+#pragma unroll 2
+    for (int j = threadIdx.x; j < nvec; j += nt) {
+      const V uv = __ldg(up + j);
+      const V ev = __ldg(ep + j);
+      const T* uu = reinterpret_cast<const T*>(&uv);
+      const T* ee = reinterpret_cast<const T*>(&ev);
 #pragma unroll
-    for (int i = 0; i < DIM; ++i) {
-      int l = rem % Bu - 1;
-      rem /= Bu;
-      const int o = l < 0 ? -1 : (l >= B ? 1 : 0);
-      l -= o * B;
-      nidx += (o + 1) * mul;
-      mul *= 3;
-      li += static_cast<int64_t>(l) * lm;
-      lm *= B;
+      for (int c = 0; c < VEC; ++c)
+        if (j * VEC + c < nin) put(j * VEC + c, uu[c], ee[c]);
     }
-    const int32_t nb = bn[nidx];
-    su[t] = nb >= 0 ? a.u[static_cast<int64_t>(nb) * L.S + li] : T(0);
+  } else {
+    for (int i = threadIdx.x; i < nin; i += nt) put(z0 * PLANE + i, a.u[base + z0 * PLANE + i], a.eps[base + z0 * PLANE + i]);
   }
-  // cell coefficients, local cell coordinates -1 .. B-1
-  for (int t = threadIdx.x; t < ne_tile; t += kBlock) {
-    int rem = t, nidx = 0, mul = 1, lm = 1;
-    int64_t li = 0;
-#pragma unroll
-    for (int i = 0; i < DIM; ++i) {
-      int l = rem % Be - 1;
-      rem /= Be;
-      const int o = l < 0 ? -1 : 0;
-      l -= o * B;
-      nidx += (o + 1) * mul;
-      mul *= 3;
-      li += static_cast<int64_t>(l) * lm;
-      lm *= B;
-    }
+  // halo vertices (tile positions outside the slab interior)
+  auto load_halo = [&](int t, int x, int y, int z) {
+    const int ox = x < 0 ? -1 : (x >= B ? 1 : 0);
+    const int oy = DIM == 2 ? 0 : (y < 0 ? -1 : (y >= B ? 1 : 0));
+    const int oz = z < 0 ? -1 : (z >= B ? 1 : 0);
+    const int nidx = DIM == 2 ? (ox + 1) + 3 * (oz + 1) : (ox + 1) + 3 * (oy + 1) + 9 * (oz + 1);
     const int32_t nb = bn[nidx];
+    const int lx = x - ox * B, ly = y - oy * B, lz = z - oz * B;
+    const int li = DIM == 2 ? lz * B + lx : (lz * B + ly) * B + lx;
+    su[t] = nb >= 0 ? a.u[static_cast<int64_t>(nb) * L.S + li] : T(0);
+  };
+  if constexpr (DIM == 2) {
+    // two halo rows of B + 2 and two halo columns of R
+    const int nh = 2 * Bu + 2 * R;
+    for (int i = threadIdx.x; i < nh; i += nt) {
+      int x, zl;
+      if (i < 2 * Bu) {
+        x = i % Bu - 1;
+        zl = i < Bu ? -1 : R;
+      } else {
+        const int j = i - 2 * Bu;
+        x = j < R ? -1 : B;
+        zl = j % R;
+      }
+      load_halo((zl + 1) * Bu + (x + 1), x, 0, zl + z0);
+    }
+  } else {
+    const int nu = UPL * (R + 2);
+    for (int t = threadIdx.x; t < nu; t += nt) {
+      const int x = t % Bu - 1;
+      const int y = (t / Bu) % Bu - 1;
+      const int z = t / UPL - 1 + z0;
+      if (x >= 0 && x < B && y >= 0 && y < B && z >= z0 && z < z0 + R) continue;
+      load_halo(t, x, y, z);
+    }
+  }
+  // halo cells: local cell coordinate -1 on some axis (x, y, or the slab's z0 - 1)
+  const int ne = EPL * (R + 1);
+  for (int t = threadIdx.x; t < ne; t += nt) {
+    const int x = t % Be - 1;
+    const int y = DIM == 2 ? 0 : (t / Be) % Be - 1;
+    const int z = t / EPL - 1 + z0;
+    if (x >= 0 && (DIM == 2 || y >= 0) && z >= z0) continue;
+    const int ox = x < 0 ? -1 : 0;
+    const int oy = DIM == 2 ? 0 : (y < 0 ? -1 : 0);
+    const int oz = z < 0 ? -1 : 0;
+    const int nidx = DIM == 2 ? (ox + 1) + 3 * (oz + 1) : (ox + 1) + 3 * (oy + 1) + 9 * (oz + 1);
+    const int32_t nb = bn[nidx];
+    const int lx = x - ox * B, ly = y - oy * B, lz = z - oz * B;
+    const int li = DIM == 2 ? lz * B + lx : (lz * B + ly) * B + lx;
     se[t] = nb >= 0 ? a.eps[static_cast<int64_t>(nb) * L.S + li] : T(0);
   }
   __syncthreads();
 
-  const int nloc = brick_vol<DIM>(B);
   const T hscale = DIM == 3 ? static_cast<T>(L.h) : T(1);
   double part = 0.0;
-  for (int s = threadIdx.x; s < nloc; s += kBlock) {
-    const int64_t slot = brick * L.S + s;
+  for (int i = threadIdx.x; i < nin; i += nt) {
+    const int s = z0 * PLANE + i;
+    const int64_t slot = base + s;
     T res = T(0);
     if (is_dof(L.vflags[slot])) {
-      int x[DIM];
-      int rem = s;
+      const int x = s % B;
+      const int y = DIM == 2 ? 0 : (s / B) % B;
+      const int zl = s / PLANE - z0;
+      const int cu = DIM == 2 ? (zl + 1) * Bu + (x + 1) : ((zl + 1) * Bu + (y + 1)) * Bu + (x + 1);
+      const int ce = DIM == 2 ? (zl + 1) * Be + (x + 1) : ((zl + 1) * Be + (y + 1)) * Be + (x + 1);
+      T Au, D;
+      if constexpr (DIM == 2) {
+        // explicit 2D form: cells sw, se, nw, ne; pair sums of the cells shared with
+        // each edge neighbour; corners see one cell
+        const T e_sw = se[ce - Be - 1], e_se = se[ce - Be], e_nw = se[ce - 1], e_ne = se[ce];
+        const T sW = e_sw + e_nw, sE = e_se + e_ne, sS = e_sw + e_se, sN = e_nw + e_ne;
+        const T sC = sW + sE;
+        const T* uc = su + cu;
+        T a1 = sW * uc[-1];
+        a1 = fma(sE, uc[1], a1);
+        a1 = fma(sS, uc[-Bu], a1);
+        a1 = fma(sN, uc[Bu], a1);
+        T a2 = e_sw * uc[-Bu - 1];
+        a2 = fma(e_se, uc[-Bu + 1], a2);
+        a2 = fma(e_nw, uc[Bu - 1], a2);
+        a2 = fma(e_ne, uc[Bu + 1], a2);
+        const T k0 = static_cast<T>(elem_k(2, 0)), k1 = static_cast<T>(elem_k(2, 1)), k2 = static_cast<T>(elem_k(2, 2));
+        D = k0 * sC;
+        Au = fma(D, uc[0], fma(k1, a1, k2 * a2));
+      } else {
+        T acc[DIM + 1];
 #pragma unroll
-      for (int i = 0; i < DIM; ++i) {
-        x[i] = rem % B;
-        rem /= B;
-      }
-      int cu = 0, ce = 0, su_mul = 1, se_mul = 1;
+        for (int c = 0; c <= DIM; ++c) acc[c] = T(0);
+        T es_centre = T(0);
 #pragma unroll
-      for (int i = 0; i < DIM; ++i) {
-        cu += (x[i] + 1) * su_mul;
-        ce += (x[i] + 1) * se_mul;
-        su_mul *= Bu;
-        se_mul *= Be;
-      }
-      // per Hamming-class accumulators: sum over offsets of (sum of eps of the
-      // cells shared by v and v+o) * u(v+o)
-      T acc[DIM + 1];
+        for (int k = 0; k < N3; ++k) {
+          int o[DIM];
+          int ham = 0, kk = k;
 #pragma unroll
-      for (int c = 0; c <= DIM; ++c) acc[c] = T(0);
-      T es_centre = T(0);
-#pragma unroll
-      for (int k = 0; k < N3; ++k) {
-        int o[DIM];
-        int ham = 0, kk = k;
-#pragma unroll
-        for (int i = 0; i < DIM; ++i) {
-          o[i] = kk % 3 - 1;
-          kk /= 3;
-          ham += o[i] != 0;
-        }
-        if (elem_k(DIM, ham) == 0.0) continue;
-        T es = T(0);
-#pragma unroll
-        for (int e = 0; e < (1 << DIM); ++e) {
-          bool ok = true;
-          int cidx = ce, m = 1;
-#pragma unroll
-          for (int i = 0; i < DIM; ++i) {
-            const int ei = (e >> i) & 1;
-            const int t = ei + o[i];
-            ok = ok && t >= 0 && t <= 1;
-            cidx -= ei * m;
-            m *= Be;
+          for (int q = 0; q < DIM; ++q) {
+            o[q] = kk % 3 - 1;
+            kk /= 3;
+            ham += o[q] != 0;
           }
-          if (ok) es += se[cidx];
-        }
-        int uidx = cu, m = 1;
+          if (elem_k(DIM, ham) == 0.0) continue;
+          T es = T(0);
 #pragma unroll
-        for (int i = 0; i < DIM; ++i) {
-          uidx += o[i] * m;
-          m *= Bu;
+          for (int e = 0; e < (1 << DIM); ++e) {
+            bool ok = true;
+            int cidx = ce, m = 1;
+#pragma unroll
+            for (int q = 0; q < DIM; ++q) {
+              const int eq = (e >> q) & 1;
+              const int tq = eq + o[q];
+              ok = ok && tq >= 0 && tq <= 1;
+              cidx -= eq * m;
+              m *= Be;
+            }
+            if (ok) es += se[cidx];
+          }
+          int uidx = cu, m = 1;
+#pragma unroll
+          for (int q = 0; q < DIM; ++q) {
+            uidx += o[q] * m;
+            m *= Bu;
+          }
+          acc[ham] = fma(es, su[uidx], acc[ham]);
+          if (ham == 0) es_centre = es;
         }
-        acc[ham] = fma(es, su[uidx], acc[ham]);
-        if (ham == 0) es_centre = es;
+        Au = T(0);
+#pragma unroll
+        for (int c = 0; c <= DIM; ++c)
+          if (elem_k(DIM, c) != 0.0) Au = fma(static_cast<T>(elem_k(DIM, c)), acc[c], Au);
+        Au *= hscale;
+        D = static_cast<T>(elem_k(DIM, 0)) * es_centre * hscale;
       }
-      T Au = T(0);
-#pragma unroll
-      for (int c = 0; c <= DIM; ++c)
-        if (elem_k(DIM, c) != 0.0) Au = fma(static_cast<T>(elem_k(DIM, c)), acc[c], Au);
-      Au *= hscale;
-      T D = static_cast<T>(elem_k(DIM, 0)) * es_centre * hscale;
       if constexpr (AMODE != 0) {
 #pragma unroll
         for (int k = 0; k < N3; ++k) {
           int uidx = cu, m = 1, kk = k;
 #pragma unroll
-          for (int i = 0; i < DIM; ++i) {
+          for (int q = 0; q < DIM; ++q) {
             uidx += (kk % 3 - 1) * m;
             kk /= 3;
             m *= Bu;
@@ -180,8 +291,9 @@ __global__ void __launch_bounds__(kBlock) k_sweep(SweepArgs<T> a) {
         }
       }
       const T r = a.b[slot] - Au;
-      if constexpr (OP == kJacobi) {
-        res = su[cu] + a.omega * r / D;
+      if constexpr (OP == kJacobi || OP == kJacobiNorm) {
+        res = fma(a.omega * r, recip_nr(D), su[cu]);
+        if constexpr (OP == kJacobiNorm) part += static_cast<double>(r) * static_cast<double>(r);
       } else {
         res = r;
         part += static_cast<double>(r) * static_cast<double>(r);
@@ -189,69 +301,96 @@ __global__ void __launch_bounds__(kBlock) k_sweep(SweepArgs<T> a) {
     }
     a.out[slot] = res;
   }
+  return part;
+}
+
+template <int DIM, typename T, int AMODE, int OP, int B>
+__global__ void __launch_bounds__(kBlock) k_sweep(SweepArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const double part = sweep_item<DIM, T, AMODE, OP, B>(a, blockIdx.x, blockIdx.y, smem_raw);
   if constexpr (OP == kResidual) {
-    if (a.partial) block_reduce_store(part, a.partial);
+    if (a.partial) store_partial_and_finish(part, a.partial, a.counter, a.norm2);
   }
 }
 
-// P(V, o) = P_dlin(o) + P_hat_V(o), o in [-2,2]^d lexicographic (5^d planes on the coarse level)
-template <int DIM, int PMODE, typename T>
-__device__ __forceinline__ T p_entry(const LevelDesc& Lc, const void* phat, const float* pscale, int64_t cs,
-                                     const int* o) {
-  constexpr int N5 = cpow(5, DIM);
-  double w = 1.0;
-  int k = 0, m = 1;
+// slot of integer position x on a level with compile-time brick edge B
+template <int DIM, int B>
+__device__ __forceinline__ int64_t slot_of_b(const LevelDesc& L, const int* x) {
+  int64_t ri = 0, li = 0;
+#pragma unroll
+  for (int i = DIM - 1; i >= 0; --i) {
+    if (x[i] < 0 || x[i] >= L.n) return -1;
+    ri = ri * L.nb_axis + x[i] / B;
+    li = li * B + x[i] % B;
+  }
+  const int32_t rank = L.brick_rank[ri];
+  return rank < 0 ? -1 : static_cast<int64_t>(rank) * L.S + li;
+}
+
+template <int DIM, int B>
+__device__ __forceinline__ bool coords_of_b(const LevelDesc& L, int64_t slot, int* x) {
+  constexpr int VOL = DIM == 2 ? B * B : B * B * B;
+  const int64_t b = slot / L.S;
+  int k = static_cast<int>(slot - b * L.S);
+  if (k >= VOL) return false;
 #pragma unroll
   for (int i = 0; i < DIM; ++i) {
-    w *= wlin1(o[i]);
-    k += (o[i] + 2) * m;
-    m *= 5;
+    x[i] = L.brick_roots[b * DIM + i] * B + k % B;
+    k /= B;
   }
-  T p = static_cast<T>(w);
-  if constexpr (PMODE != 0) p += load_delta<PMODE, T>(phat, pscale, plane_index(Lc, cs, k, N5), cs);
-  return p;
+  return true;
 }
 
 // b_c(V) = sum_o P(V,o) r_f(3V + o): restriction with R = P^T (Sect. 4.4).
-// One thread per coarse slot; zero on non-DoF coarse slots.
-template <int DIM, typename T, int PMODE>
-__global__ void __launch_bounds__(kBlock) k_restrict(LevelDesc Lc, LevelDesc Lf, const T* rf, T* bc,
-                                                       const void* phat, const float* pscale) {
-  const int64_t cs = blockIdx.x * static_cast<int64_t>(kBlock) + threadIdx.x;
-  if (cs >= Lc.n_slots) return;
+// One thread per coarse slot; zero on non-DoF coarse slots.  The 5^d loop is fully
+// unrolled so the d-linear weights are compile-time constants.
+template <int DIM, typename T, int PMODE, int BC, int BF>
+__device__ __forceinline__ void restrict_one(const LevelDesc& Lc, const LevelDesc& Lf, const T* rf, T* bc,
+                                             const void* phat, const float* pscale, int64_t cs) {
+  constexpr int N5 = cpow(5, DIM);
   int X[DIM];
-  if (!coords_of<DIM>(Lc, cs, X) || !is_dof(Lc.vflags[cs])) {
+  if (!coords_of_b<DIM, BC>(Lc, cs, X) || !is_dof(Lc.vflags[cs])) {
     bc[cs] = T(0);
     return;
   }
-  constexpr int N5 = cpow(5, DIM);
+  const int64_t cb = cs / Lc.S, cl = cs - cb * Lc.S;
   T acc = T(0);
-#pragma unroll 5
+#pragma unroll
   for (int k = 0; k < N5; ++k) {
     int o[DIM], y[DIM];
     int kk = k;
+    double w = 1.0;
 #pragma unroll
     for (int i = 0; i < DIM; ++i) {
       o[i] = kk % 5 - 2;
       kk /= 5;
       y[i] = 3 * X[i] + o[i];
+      w *= wlin1(o[i]);
     }
-    const int64_t fs = slot_of<DIM>(Lf, y);
+    const int64_t fs = slot_of_b<DIM, BF>(Lf, y);
     if (fs < 0) continue;
-    acc = fma(p_entry<DIM, PMODE, T>(Lc, phat, pscale, cs, o), rf[fs], acc);
+    T p = static_cast<T>(w);
+    if constexpr (PMODE != 0) p += load_delta<PMODE, T>(phat, pscale, (cb * N5 + k) * Lc.S + cl, cs);
+    acc = fma(p, rf[fs], acc);
   }
   bc[cs] = acc;
 }
 
+template <int DIM, typename T, int PMODE, int BC, int BF>
+__global__ void __launch_bounds__(kBlock) k_restrict(LevelDesc Lc, LevelDesc Lf, const T* rf, T* bc,
+                                                       const void* phat, const float* pscale) {
+  const int64_t cs = blockIdx.x * static_cast<int64_t>(kBlock) + threadIdx.x;
+  if (cs < Lc.n_slots) restrict_one<DIM, T, PMODE, BC, BF>(Lc, Lf, rf, bc, phat, pscale, cs);
+}
+
 // u_f(v) += sum over coarse parents V of P(V, v - 3V) e_c(V) (coarse-grid
 // correction of Alg. 1).  One thread per fine slot; non-DoF slots untouched.
-template <int DIM, typename T, int PMODE>
-__global__ void __launch_bounds__(kBlock) k_prolong(LevelDesc Lc, LevelDesc Lf, const T* ec, T* uf,
-                                                      const void* phat, const float* pscale) {
-  const int64_t fs = blockIdx.x * static_cast<int64_t>(kBlock) + threadIdx.x;
-  if (fs >= Lf.n_slots) return;
+template <int DIM, typename T, int PMODE, int BC, int BF>
+__device__ __forceinline__ void prolong_one(const LevelDesc& Lc, const LevelDesc& Lf, const T* ec, T* uf,
+                                            const void* phat, const float* pscale, int64_t fs) {
+  constexpr int N5 = cpow(5, DIM);
   int x[DIM];
-  if (!coords_of<DIM>(Lf, fs, x) || !is_dof(Lf.vflags[fs])) return;
+  if (!coords_of_b<DIM, BF>(Lf, fs, x) || !is_dof(Lf.vflags[fs])) return;
   int lo[DIM], cnt[DIM];
 #pragma unroll
   for (int i = 0; i < DIM; ++i) {
@@ -263,19 +402,36 @@ __global__ void __launch_bounds__(kBlock) k_prolong(LevelDesc Lc, LevelDesc Lf, 
   for (int e = 0; e < (1 << DIM); ++e) {
     int X[DIM], o[DIM];
     bool ok = true;
+    double w = 1.0;
+    int k = 0, m = 1;
 #pragma unroll
     for (int i = 0; i < DIM; ++i) {
       const int ei = (e >> i) & 1;
       if (ei >= cnt[i]) ok = false;
       X[i] = lo[i] + ei;
       o[i] = x[i] - 3 * X[i];
+      w *= wlin1(o[i]);
+      k += (o[i] + 2) * m;
+      m *= 5;
     }
     if (!ok) continue;
-    const int64_t cs = slot_of<DIM>(Lc, X);
+    const int64_t cs = slot_of_b<DIM, BC>(Lc, X);
     if (cs < 0 || !is_dof(Lc.vflags[cs])) continue;
-    acc = fma(p_entry<DIM, PMODE, T>(Lc, phat, pscale, cs, o), ec[cs], acc);
+    T p = static_cast<T>(w);
+    if constexpr (PMODE != 0) {
+      const int64_t cb = cs / Lc.S;
+      p += load_delta<PMODE, T>(phat, pscale, (cb * N5 + k) * Lc.S + (cs - cb * Lc.S), cs);
+    }
+    acc = fma(p, ec[cs], acc);
   }
   uf[fs] += acc;
+}
+
+template <int DIM, typename T, int PMODE, int BC, int BF>
+__global__ void __launch_bounds__(kBlock) k_prolong(LevelDesc Lc, LevelDesc Lf, const T* ec, T* uf,
+                                                      const void* phat, const float* pscale) {
+  const int64_t fs = blockIdx.x * static_cast<int64_t>(kBlock) + threadIdx.x;
+  if (fs < Lf.n_slots) prolong_one<DIM, T, PMODE, BC, BF>(Lc, Lf, ec, uf, phat, pscale, fs);
 }
 
 // u_f on HANGING slots = d-linear interpolant of the coarser level (Sect. 3, rule 2)
@@ -296,5 +452,21 @@ __global__ void __launch_bounds__(kBlock) k_hanging(LevelDesc Lf, const int32_t*
 
 // sum of partial[0..n) in a fixed order by one CTA -> *out
 __global__ void __launch_bounds__(kBlock) k_reduce_partials(const double* partial, int64_t n, double* out);
+
+// ---- host-side launchers (instantiated per dimension / type in k2d_*.cu, k3d_*.cu) ----
+
+// slab thickness: the largest divisor R of B giving at least `target` CTAs (or 1)
+inline int pick_slab(int B, int64_t n_bricks, int64_t target) {
+  int R = B;
+  while (R > 1 && n_bricks * (B / R) < target) R /= 3;
+  return R;
+}
+
+template <int DIM, typename T>
+void launch_sweep(SweepArgs<T> a, int op, int amode, cudaStream_t s);
+
+template <int DIM, typename T>
+void launch_transfer(const LevelDesc& Lc, const LevelDesc& Lf, bool restrict_op, int pmode, const T* in, T* out,
+                     const void* phat, const float* pscale, cudaStream_t s);
 
 }  // namespace mg

@@ -1,0 +1,77 @@
+// Host launchers of the hot-path kernels, instantiated per (dimension, type) in
+// k2d_f64.cu, k2d_f32.cu, k3d_f64.cu, k3d_f32.cu so they compile in parallel.
+#pragma once
+
+#include <type_traits>
+
+#include "kernels.cuh"
+
+namespace mg {
+
+template <int DIM, typename T, int B>
+static void sweep_b(SweepArgs<T> a, int op, int amode, cudaStream_t s) {
+  constexpr int PLANE = DIM == 2 ? B : B * B;
+  constexpr int UPL = DIM == 2 ? B + 2 : (B + 2) * (B + 2);
+  constexpr int EPL = DIM == 2 ? B + 1 : (B + 1) * (B + 1);
+  const int R = a.R;
+  const dim3 grid(static_cast<unsigned>(a.L.n_bricks), static_cast<unsigned>(B / R));
+  int threads = ((R * PLANE + 31) / 32) * 32;
+  if (threads > kBlock) threads = kBlock;
+  const size_t smem = (static_cast<size_t>(UPL) * (R + 2) + static_cast<size_t>(EPL) * (R + 1)) * sizeof(T);
+#define MG_SW(AM, OP) k_sweep<DIM, T, AM, OP, B><<<grid, threads, smem, s>>>(a)
+  if constexpr (std::is_same<T, double>::value) {
+    if (op == kJacobi) {
+      if (amode == 1) MG_SW(1, kJacobi); else MG_SW(0, kJacobi);
+    } else {
+      if (amode == 1) MG_SW(1, kResidual); else MG_SW(0, kResidual);
+    }
+  } else {
+    if (op == kJacobi) {
+      if (amode == 2) MG_SW(2, kJacobi); else if (amode == 3) MG_SW(3, kJacobi); else MG_SW(0, kJacobi);
+    } else {
+      if (amode == 2) MG_SW(2, kResidual); else if (amode == 3) MG_SW(3, kResidual); else MG_SW(0, kResidual);
+    }
+  }
+#undef MG_SW
+}
+
+template <int DIM, typename T, int BC, int BF>
+static void transfer_b(const LevelDesc& Lc, const LevelDesc& Lf, bool restrict_op, int pmode, const T* in, T* out,
+                       const void* ph, const float* ps, cudaStream_t s) {
+  const unsigned gc = static_cast<unsigned>((Lc.n_slots + kBlock - 1) / kBlock);
+  const unsigned gf = static_cast<unsigned>((Lf.n_slots + kBlock - 1) / kBlock);
+#define MG_TR(PM)                                                                          \
+  do {                                                                                     \
+    if (restrict_op)                                                                       \
+      k_restrict<DIM, T, PM, BC, BF><<<gc, kBlock, 0, s>>>(Lc, Lf, in, out, ph, ps);      \
+    else                                                                                   \
+      k_prolong<DIM, T, PM, BC, BF><<<gf, kBlock, 0, s>>>(Lc, Lf, in, out, ph, ps);       \
+  } while (0)
+  if constexpr (std::is_same<T, double>::value) {
+    if (pmode == 1) MG_TR(1); else MG_TR(0);
+  } else {
+    if (pmode == 2) MG_TR(2); else if (pmode == 3) MG_TR(3); else MG_TR(0);
+  }
+#undef MG_TR
+}
+
+}  // namespace mg
+
+#define MG_INSTANTIATE_LAUNCHERS(DIM, T)                                                                    \
+  namespace mg {                                                                                            \
+  template <>                                                                                               \
+  void launch_sweep<DIM, T>(SweepArgs<T> a, int op, int amode, cudaStream_t s) {                             \
+    switch (a.L.B) {                                                                                        \
+      case 3: sweep_b<DIM, T, 3>(a, op, amode, s); break;                                                   \
+      case 9: sweep_b<DIM, T, 9>(a, op, amode, s); break;                                                   \
+      default: MG_SWEEP_27(DIM, T) break;                                                                   \
+    }                                                                                                       \
+  }                                                                                                         \
+  template <>                                                                                               \
+  void launch_transfer<DIM, T>(const LevelDesc& Lc, const LevelDesc& Lf, bool r, int pmode, const T* in,     \
+                               T* out, const void* ph, const float* ps, cudaStream_t s) {                   \
+    if (Lc.B == 3 && Lf.B == 9) transfer_b<DIM, T, 3, 9>(Lc, Lf, r, pmode, in, out, ph, ps, s);              \
+    else if (Lc.B == 9 && Lf.B == 9) transfer_b<DIM, T, 9, 9>(Lc, Lf, r, pmode, in, out, ph, ps, s);         \
+    else MG_TRANSFER_27(DIM, T)                                                                             \
+  }                                                                                                         \
+  }

@@ -16,8 +16,9 @@
 namespace mg {
 namespace {
 
-// One partial sum per brick of the level: 4096 bricks (32 KiB) covers every level
-// up to 2D level 6 (729 bricks) and 3D level 4 (729 bricks).
+// One partial sum per CTA of the residual sweep (a brick, or a slab of a brick on
+// small levels): 4096 entries (32 KiB) cover every level up to 2D level 6 and 3D
+// level 4 (729 bricks each; smaller levels are split into at most 912 slabs).
 constexpr int64_t kMaxBricks = 4096;
 static __device__ __align__(256) double g_partials[kMaxBricks];
 
@@ -64,17 +65,26 @@ __global__ void __launch_bounds__(kBlock) k_sum_partials(const double* partial, 
   }
 }
 
-template <int DIM>
-void launch_residual(const DevLevel& D, bool coarse_delta, const double* u, const double* b, double* r,
-                     double* partial, cudaStream_t s) {
-  SweepArgs<double> a{D.d, u, b, r, D.eps, coarse_delta ? D.ahat : nullptr, nullptr, 0.0, partial};
-  const int Bu = D.d.B + 2, Be = D.d.B + 1;
-  const size_t smem = (DIM == 2 ? (Bu * Bu + Be * Be) : (Bu * Bu * Bu + Be * Be * Be)) * sizeof(double);
-  const unsigned grid = static_cast<unsigned>(D.d.n_bricks);
-  if (coarse_delta)
-    k_sweep<DIM, double, 1, kResidual><<<grid, kBlock, smem, s>>>(a);
+constexpr int64_t kSweepTargetCtas = 4 * 152;
+
+// launches the residual sweep with its per-CTA partial sums in `partial`; returns
+// the number of partial sums written
+int64_t launch_residual(const Hier& H, const DevLevel& D, bool coarse_delta, const double* u, const double* b,
+                        double* r, double* partial, cudaStream_t s) {
+  SweepArgs<double> a{};
+  a.L = D.d;
+  a.u = u;
+  a.b = b;
+  a.out = r;
+  a.eps = D.eps;
+  a.ahat = coarse_delta ? D.ahat : nullptr;
+  a.partial = partial;
+  a.R = pick_slab(D.d.B, D.d.n_bricks, kSweepTargetCtas);
+  if (H.dim == 2)
+    launch_sweep<2, double>(a, kResidual, coarse_delta ? 1 : 0, s);
   else
-    k_sweep<DIM, double, 0, kResidual><<<grid, kBlock, smem, s>>>(a);
+    launch_sweep<3, double>(a, kResidual, coarse_delta ? 1 : 0, s);
+  return D.d.n_bricks * (D.d.B / a.R);
 }
 
 }  // namespace
@@ -104,11 +114,12 @@ extern "C" mg_status mg_residual_norm_noalloc(mg_hier* h, int level, const doubl
   if (st != MG_OK) return st;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const bool coarse_delta = level < H->L && H->galerkin;
-  if (H->dim == 2)
-    launch_residual<2>(D, coarse_delta, u, b, r, partial, s);
-  else
-    launch_residual<3>(D, coarse_delta, u, b, r, partial, s);
-  k_sum_partials<<<1, kBlock, 0, s>>>(partial, D.d.n_bricks, norm2);
+  if (D.d.n_bricks * (D.d.B / pick_slab(D.d.B, D.d.n_bricks, kSweepTargetCtas)) > kMaxBricks) {
+    set_error("mg_residual_norm_noalloc: level needs more than 4096 partial sums; use mg_residual");
+    return MG_ERR_INVALID_ARG;
+  }
+  const int64_t nparts = launch_residual(*H, D, coarse_delta, u, b, r, partial, s);
+  k_sum_partials<<<1, kBlock, 0, s>>>(partial, nparts, norm2);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     set_error(std::string("mg_residual_norm_noalloc: launch failed: ") + cudaGetErrorString(e));

@@ -14,9 +14,15 @@
 #include "hier.h"
 #include "internal.h"
 #include "kernels.cuh"
+#include "persist.cuh"
 #include "setup.cuh"
 
 namespace mg {
+
+extern template cudaError_t persist_launch_fp64<2>(const PSolve<double>*, int, int, size_t, cudaStream_t, int*);
+extern template cudaError_t persist_launch_fp64<3>(const PSolve<double>*, int, int, size_t, cudaStream_t, int*);
+extern template cudaError_t persist_launch_mixed<2>(const PSolve<float>*, int, int, size_t, cudaStream_t, int*);
+extern template cudaError_t persist_launch_mixed<3>(const PSolve<float>*, int, int, size_t, cudaStream_t, int*);
 
 // ----------------------------------------------------------------------------- small kernels
 
@@ -214,6 +220,24 @@ __global__ void __launch_bounds__(kBlock) k_coarse_solve(const double* Lm, int n
   for (int i = threadIdx.x; i < n; i += kBlock) u[c_slots[i]] = static_cast<T>(y[i]);
 }
 
+// the same for at most 32 unknowns: one thread, no barriers
+template <typename T>
+__global__ void k_coarse_solve_small(const double* Lm, int n, const int32_t* c_slots, const T* b, T* u) {
+  if (threadIdx.x != 0) return;
+  double y[32];
+  for (int i = 0; i < n; ++i) {
+    double v = static_cast<double>(b[c_slots[i]]);
+    for (int j = 0; j < i; ++j) v -= Lm[i * n + j] * y[j];
+    y[i] = v / Lm[i * n + i];
+  }
+  for (int i = n - 1; i >= 0; --i) {
+    double v = y[i];
+    for (int j = i + 1; j < n; ++j) v -= Lm[j * n + i] * y[j];
+    y[i] = v / Lm[i * n + i];
+  }
+  for (int i = 0; i < n; ++i) u[c_slots[i]] = static_cast<T>(y[i]);
+}
+
 // ----------------------------------------------------------------------------- hierarchy
 
 #define MG_TRY_CUDA(call)                                                         \
@@ -319,7 +343,8 @@ static mg_status create(const Grid* g, const mg_options& o, Hier** out) {
     if ((st = dalloc(*H, &D.eps, ns)) != MG_OK) return fail(st);
     if ((st = dalloc(*H, &D.r, ns)) != MG_OK) return fail(st);
     if ((st = dalloc(*H, &D.t, ns)) != MG_OK) return fail(st);
-    if ((st = dalloc(*H, &D.partial, static_cast<size_t>(hl.n_bricks))) != MG_OK) return fail(st);
+    if ((st = dalloc(*H, &D.partial, static_cast<size_t>(hl.n_bricks) * hl.B)) != MG_OK) return fail(st);
+    if ((st = dalloc(*H, &D.counter, 1)) != MG_OK) return fail(st);
     if (l < H->L) {
       if ((st = dalloc(*H, &D.u, ns)) != MG_OK) return fail(st);
       if ((st = dalloc(*H, &D.b, ns)) != MG_OK) return fail(st);
@@ -364,6 +389,14 @@ static mg_status create(const Grid* g, const mg_options& o, Hier** out) {
   if ((st = dalloc(*H, &H->c_mat, static_cast<size_t>(H->n_c) * H->n_c)) != MG_OK) return fail(st);
   if ((st = dalloc(*H, &H->d_status, 1)) != MG_OK) return fail(st);
   if ((st = dalloc(*H, &H->d_scal, 16)) != MG_OK) return fail(st);
+  if ((st = dalloc(*H, &H->d_hist, kHistCap)) != MG_OK) return fail(st);
+  if ((st = dalloc(*H, &H->d_pint, 4)) != MG_OK) return fail(st);
+  if ((st = dalloc(*H, &H->d_pdbl, 4)) != MG_OK) return fail(st);
+  {
+    unsigned char* ps = nullptr;
+    if ((st = dalloc(*H, &ps, std::max(sizeof(PSolve<double>), sizeof(PSolve<float>)))) != MG_OK) return fail(st);
+    H->d_psolve = ps;
+  }
   if (cudaMallocHost(&H->h_pin, 16 * sizeof(double)) != cudaSuccess) {
     set_error("mg_hier_create: cudaMallocHost failed");
     return fail(MG_ERR_OOM);
@@ -378,57 +411,55 @@ static mg_status create(const Grid* g, const mg_options& o, Hier** out) {
 
 // ----------------------------------------------------------------------------- kernel dispatch
 
-template <int DIM, typename T>
-static void sweep_dim(const DevLevel& D, int op, int amode, const T* u, const T* b, T* out, const T* eps,
-                      const void* ahat, const float* ascale, T omega, double* partial, cudaStream_t s) {
-  SweepArgs<T> a{D.d, u, b, out, eps, ahat, ascale, omega, partial};
-  const int Bu = D.d.B + 2, Be = D.d.B + 1;
-  const size_t smem = (DIM == 2 ? (Bu * Bu + Be * Be) : (Bu * Bu * Bu + Be * Be * Be)) * sizeof(T);
-  const unsigned grid = static_cast<unsigned>(D.d.n_bricks);
-#define MG_SW(AM, OP) k_sweep<DIM, T, AM, OP><<<grid, kBlock, smem, s>>>(a)
+constexpr int64_t kSweepTargetCtas = 4 * 152;  // spread small levels over the SMs
+
+template <typename T>
+static SweepArgs<T> sweep_args(const Hier& H, int l, const T* u, const T* b, T* out, int* amode) {
+  const DevLevel& D = H.lv[l];
+  const bool coarse = l < H.L && H.galerkin;
+  SweepArgs<T> a{};
+  a.L = D.d;
+  a.u = u;
+  a.b = b;
+  a.out = out;
+  a.omega = static_cast<T>(H.opt.omega);
+  a.R = pick_slab(D.d.B, D.d.n_bricks, kSweepTargetCtas);
+  *amode = 0;
   if constexpr (std::is_same<T, double>::value) {
-    if (op == kJacobi) {
-      if (amode == 1) MG_SW(1, kJacobi); else MG_SW(0, kJacobi);
-    } else {
-      if (amode == 1) MG_SW(1, kResidual); else MG_SW(0, kResidual);
+    a.eps = D.eps;
+    if (coarse) {
+      *amode = 1;
+      a.ahat = D.ahat;
     }
   } else {
-    if (op == kJacobi) {
-      if (amode == 2) MG_SW(2, kJacobi); else if (amode == 3) MG_SW(3, kJacobi); else MG_SW(0, kJacobi);
-    } else {
-      if (amode == 2) MG_SW(2, kResidual); else if (amode == 3) MG_SW(3, kResidual); else MG_SW(0, kResidual);
+    a.eps = D.eps32;
+    if (coarse) {
+      *amode = H.fmt == 1 ? 2 : 3;
+      a.ahat = D.a16;
+      a.ascale = D.ascale;
     }
   }
-#undef MG_SW
+  return a;
 }
 
 template <typename T>
-static void sweep(const Hier& H, int l, int op, const T* u, const T* b, T* out, double* partial, cudaStream_t s) {
-  const DevLevel& D = H.lv[l];
-  const bool coarse = l < H.L && H.galerkin;
-  int amode = 0;
-  const void* ahat = nullptr;
-  const float* ascale = nullptr;
-  const T* eps;
-  if constexpr (std::is_same<T, double>::value) {
-    eps = D.eps;
-    if (coarse) {
-      amode = 1;
-      ahat = D.ahat;
-    }
-  } else {
-    eps = D.eps32;
-    if (coarse) {
-      amode = H.fmt == 1 ? 2 : 3;
-      ahat = D.a16;
-      ascale = D.ascale;
-    }
-  }
-  const T omega = static_cast<T>(H.opt.omega);
+static void launch(const Hier& H, SweepArgs<T> a, int op, int amode, cudaStream_t s) {
   if (H.dim == 2)
-    sweep_dim<2, T>(D, op, amode, u, b, out, eps, ahat, ascale, omega, partial, s);
+    launch_sweep<2, T>(a, op, amode, s);
   else
-    sweep_dim<3, T>(D, op, amode, u, b, out, eps, ahat, ascale, omega, partial, s);
+    launch_sweep<3, T>(a, op, amode, s);
+}
+
+template <typename T>
+static void sweep(const Hier& H, int l, int op, const T* u, const T* b, T* out, double* norm2, cudaStream_t s) {
+  int amode = 0;
+  SweepArgs<T> a = sweep_args<T>(H, l, u, b, out, &amode);
+  if (norm2) {
+    a.partial = H.lv[l].partial;
+    a.counter = H.lv[l].counter;
+    a.norm2 = norm2;
+  }
+  launch<T>(H, a, op, amode, s);
 }
 
 template <typename T>
@@ -448,28 +479,18 @@ static void transfer(const Hier& H, int fine, bool restrict_op, const T* in, T* 
       ps = C.pscale;
     }
   }
-#define MG_TR(DIM, PM)                                                                           \
-  do {                                                                                           \
-    if (restrict_op)                                                                             \
-      k_restrict<DIM, T, PM><<<nblk(C.d.n_slots), kBlock, 0, s>>>(C.d, F.d, in, out, ph, ps);   \
-    else                                                                                         \
-      k_prolong<DIM, T, PM><<<nblk(F.d.n_slots), kBlock, 0, s>>>(C.d, F.d, in, out, ph, ps);    \
-  } while (0)
-  if (H.dim == 2) {
-    if (pmode == 0) MG_TR(2, 0); else if (pmode == 1) MG_TR(2, 1); else if (pmode == 2) MG_TR(2, 2); else MG_TR(2, 3);
-  } else {
-    if (pmode == 0) MG_TR(3, 0); else if (pmode == 1) MG_TR(3, 1); else if (pmode == 2) MG_TR(3, 2); else MG_TR(3, 3);
-  }
-#undef MG_TR
-}
-
-static void reduce(const DevLevel& D, double* out, cudaStream_t s) {
-  k_reduce_partials<<<1, kBlock, 0, s>>>(D.partial, D.d.n_bricks, out);
+  if (H.dim == 2)
+    launch_transfer<2, T>(C.d, F.d, restrict_op, pmode, in, out, ph, ps, s);
+  else
+    launch_transfer<3, T>(C.d, F.d, restrict_op, pmode, in, out, ph, ps, s);
 }
 
 template <typename T>
 static void coarse_solve(const Hier& H, const T* b, T* u, cudaStream_t s) {
-  k_coarse_solve<T><<<1, kBlock, H.n_c * sizeof(double), s>>>(H.c_mat, H.n_c, H.c_slots, b, u);
+  if (H.n_c <= 32)
+    k_coarse_solve_small<T><<<1, 32, 0, s>>>(H.c_mat, H.n_c, H.c_slots, b, u);
+  else
+    k_coarse_solve<T><<<1, kBlock, H.n_c * sizeof(double), s>>>(H.c_mat, H.n_c, H.c_slots, b, u);
 }
 
 // nu damped Jacobi sweeps, ping-pong through tmp, result in u
@@ -519,9 +540,7 @@ static void vcycle(Hier& H, int l, T* u, const T* b, cudaStream_t s) {
 // finest residual r = b - A u with its squared norm into d_scal[slot]
 template <typename T>
 static void residual_norm(Hier& H, const T* u, const T* b, T* r, int slot, cudaStream_t s) {
-  DevLevel& F = H.lv[H.L];
-  sweep<T>(H, H.L, kResidual, u, b, r, F.partial, s);
-  reduce(F, H.d_scal + slot, s);
+  sweep<T>(H, H.L, kResidual, u, b, r, H.d_scal + slot, s);
 }
 
 static mg_status run_setup(Hier& H, const double* eps_in, cudaStream_t s) {
@@ -794,6 +813,146 @@ static mg_status solve_mixed(Hier& H, double* u, const double* b, double tol, in
   return MG_OK;
 }
 
+// ---- persistent cooperative solve -------------------------------------------------
+
+template <typename T>
+static PLevel<T> make_plevel(const Hier& H, int l, T* u_fin, const T* b_fin) {
+  const DevLevel& D = H.lv[l];
+  PLevel<T> P{};
+  P.d = D.d;
+  const bool coarse = l < H.L;
+  if constexpr (std::is_same<T, double>::value) {
+    P.eps = D.eps;
+    P.ahat = (coarse && H.galerkin) ? D.ahat : nullptr;
+    P.phat = (coarse && H.boxmg) ? D.phat : nullptr;
+    P.u = coarse ? D.u : u_fin;
+    P.b = coarse ? D.b : const_cast<T*>(b_fin);
+    P.r = D.r;
+    P.t = D.t;
+  } else {
+    P.eps = D.eps32;
+    P.ahat = (coarse && H.galerkin) ? D.a16 : nullptr;
+    P.ascale = (coarse && H.galerkin) ? D.ascale : nullptr;
+    P.phat = (coarse && H.boxmg) ? D.p16 : nullptr;
+    P.pscale = (coarse && H.boxmg) ? D.pscale : nullptr;
+    P.u = D.u32;
+    P.b = D.b32;
+    P.r = D.r32;
+    P.t = D.t32;
+  }
+  P.R = pick_slab(D.d.B, D.d.n_bricks, kSweepTargetCtas);
+  P.nitems = static_cast<int>(D.d.n_bricks * (D.d.B / P.R));
+  return P;
+}
+
+template <typename T>
+static size_t tile_bytes(const Hier& H, int l, int R) {
+  const int B = H.lv[l].d.B;
+  const size_t upl = H.dim == 2 ? B + 2 : (B + 2) * (B + 2);
+  const size_t epl = H.dim == 2 ? B + 1 : (B + 1) * (B + 1);
+  return (upl * (R + 2) + epl * (R + 1)) * sizeof(T);
+}
+
+static mg_status solve_persistent(Hier& H, double* u, const double* b, double tol, int max_cycles,
+                                  mg_solve_stats* st, cudaStream_t s) {
+  DevLevel& Fd = H.lv[H.L];
+  MG_TRY_CUDA(cudaMemsetAsync(u, 0, Fd.d.n_slots * sizeof(double), s));
+  const int amc = H.galerkin ? (H.mixed ? (H.fmt == 1 ? 2 : 3) : 1) : 0;
+  const int pm = H.boxmg ? (H.mixed ? (H.fmt == 1 ? 2 : 3) : 1) : 0;
+  int grid = 0;
+  cudaError_t e;
+  if (!H.mixed) {
+    PSolve<double> p{};
+    p.L = H.L;
+    p.c = H.c;
+    p.nu1 = H.opt.nu1;
+    p.nu2 = H.opt.nu2;
+    p.omega = H.opt.omega;
+    size_t smem = 0;
+    for (int l = H.c; l <= H.L; ++l) {
+      p.lv[l] = make_plevel<double>(H, l, u, b);
+      smem = std::max(smem, tile_bytes<double>(H, l, p.lv[l].R));
+    }
+    p.chol = H.c_mat;
+    p.n_c = H.n_c;
+    p.c_slots = H.c_slots;
+    p.partial = Fd.partial;
+    p.hist = H.d_hist;
+    p.hist_cap = kHistCap;
+    p.out_int = H.d_pint;
+    p.out_dbl = H.d_pdbl;
+    p.tol = tol;
+    p.max_cycles = max_cycles;
+    MG_TRY_CUDA(cudaMemcpyAsync(H.d_psolve, &p, sizeof(p), cudaMemcpyHostToDevice, s));
+    e = H.dim == 2 ? persist_launch_fp64<2>(static_cast<const PSolve<double>*>(H.d_psolve), amc, pm, smem, s, &grid)
+                   : persist_launch_fp64<3>(static_cast<const PSolve<double>*>(H.d_psolve), amc, pm, smem, s, &grid);
+  } else {
+    PSolve<float> p{};
+    p.L = H.L;
+    p.c = H.c;
+    p.nu1 = H.opt.nu1;
+    p.nu2 = H.opt.nu2;
+    p.omega = static_cast<float>(H.opt.omega);
+    size_t smem = 0;
+    for (int l = H.c; l <= H.L; ++l) {
+      p.lv[l] = make_plevel<float>(H, l, nullptr, nullptr);
+      smem = std::max(smem, tile_bytes<float>(H, l, p.lv[l].R));
+    }
+    p.f64 = make_plevel<double>(H, H.L, u, b);
+    smem = std::max(smem, tile_bytes<double>(H, H.L, p.f64.R));
+    p.chol = H.c_mat;
+    p.n_c = H.n_c;
+    p.c_slots = H.c_slots;
+    p.partial = Fd.partial;
+    p.hist = H.d_hist;
+    p.hist_cap = kHistCap;
+    p.out_int = H.d_pint;
+    p.out_dbl = H.d_pdbl;
+    p.tol = tol;
+    p.max_cycles = max_cycles;
+    p.inv_count = Fd.n_dofs > 0 ? 1.0 / static_cast<double>(Fd.n_dofs) : 0.0;
+    MG_TRY_CUDA(cudaMemcpyAsync(H.d_psolve, &p, sizeof(p), cudaMemcpyHostToDevice, s));
+    e = H.dim == 2 ? persist_launch_mixed<2>(static_cast<const PSolve<float>*>(H.d_psolve), amc, pm, smem, s, &grid)
+                   : persist_launch_mixed<3>(static_cast<const PSolve<float>*>(H.d_psolve), amc, pm, smem, s, &grid);
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    set_error(std::string("persistent solve launch: ") + cudaGetErrorString(e));
+    return MG_ERR_CUDA;
+  }
+  MG_TRY_CUDA(cudaMemcpyAsync(H.h_pin + 8, H.d_pdbl, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  MG_TRY_CUDA(cudaMemcpyAsync(reinterpret_cast<int*>(H.h_pin + 12), H.d_pint, 3 * sizeof(int), cudaMemcpyDeviceToHost, s));
+  MG_TRY_CUDA(cudaStreamSynchronize(s));
+  const int* oi = reinterpret_cast<const int*>(H.h_pin + 12);
+  const int cycles = oi[0], outer = oi[1], status = oi[2];
+  const double r0 = H.h_pin[8], rel = H.h_pin[9];
+  if (st) {
+    st->cycles = cycles;
+    st->outer_steps = outer;
+    st->r0_norm = r0;
+    st->rel_residual = rel;
+    const int nh = std::min(H.mixed ? std::max(outer - 1, 0) : cycles, std::min(st->history_capacity, kHistCap));
+    st->history_len = 0;
+    if (st->history && nh > 0) {
+      MG_TRY_CUDA(cudaMemcpy(st->history, H.d_hist, nh * sizeof(double), cudaMemcpyDeviceToHost));
+      st->history_len = nh;
+    }
+  }
+  if (status == 2) {
+    set_error("mg_solve: non-finite residual");
+    return MG_ERR_NONFINITE;
+  }
+  if (status == 3) {
+    set_error("mg_solve: residual grew by more than 1e6 (diverged)");
+    return MG_ERR_DIVERGED;
+  }
+  if (status == 1) {
+    set_error("mg_solve: not converged within max_cycles");
+    return MG_ERR_NOT_CONVERGED;
+  }
+  return MG_OK;
+}
+
 }  // namespace mg
 
 using namespace mg;
@@ -832,6 +991,7 @@ void mg_default_options(mg_options* o) {
   o->coarsest_level = 1;
   o->inner_cycles = 8;
   o->use_graphs = 1;
+  o->persistent = 0;
 }
 
 mg_status mg_hier_create(const mg_grid* grid, const mg_options* opt, mg_hier** out) {
@@ -897,10 +1057,8 @@ mg_status mg_residual(mg_hier* h, int level, const double* u, const double* b, d
     return MG_ERR_INVALID_ARG;
   }
   cudaStream_t s = pick(*H, stream);
-  DevLevel& D = H->lv[level];
-  sweep<double>(*H, level, kResidual, u, b, r, D.partial, s);
+  sweep<double>(*H, level, kResidual, u, b, r, norm2_host ? H->d_scal + 3 : nullptr, s);
   if (norm2_host) {
-    reduce(D, H->d_scal + 3, s);
     MG_TRY_CUDA(cudaMemcpyAsync(H->h_pin + 3, H->d_scal + 3, sizeof(double), cudaMemcpyDeviceToHost, s));
     MG_TRY_CUDA(cudaStreamSynchronize(s));
     *norm2_host = H->h_pin[3];
@@ -938,10 +1096,8 @@ mg_status mg_residual_f32(mg_hier* h, int level, const float* u, const float* b,
     return MG_ERR_INVALID_ARG;
   }
   cudaStream_t s = pick(*H, stream);
-  DevLevel& D = H->lv[level];
-  sweep<float>(*H, level, kResidual, u, b, r, D.partial, s);
+  sweep<float>(*H, level, kResidual, u, b, r, norm2_host ? H->d_scal + 3 : nullptr, s);
   if (norm2_host) {
-    reduce(D, H->d_scal + 3, s);
     MG_TRY_CUDA(cudaMemcpyAsync(H->h_pin + 3, H->d_scal + 3, sizeof(double), cudaMemcpyDeviceToHost, s));
     MG_TRY_CUDA(cudaStreamSynchronize(s));
     *norm2_host = H->h_pin[3];
@@ -1020,8 +1176,10 @@ mg_status mg_solve(mg_hier* h, double* u, const double* b, double rel_tol, int m
   }
   cudaStream_t s = pick(*H, stream);
   const auto t0 = std::chrono::steady_clock::now();
-  const mg_status st = H->mixed ? solve_mixed(*H, u, b, rel_tol, max_cycles, stats, s)
-                                : solve_fp64(*H, u, b, rel_tol, max_cycles, stats, s);
+  const bool persistent = H->opt.persistent && H->n_c <= 64 && H->L < kMaxLevels;
+  const mg_status st = persistent ? solve_persistent(*H, u, b, rel_tol, max_cycles, stats, s)
+                       : H->mixed ? solve_mixed(*H, u, b, rel_tol, max_cycles, stats, s)
+                                  : solve_fp64(*H, u, b, rel_tol, max_cycles, stats, s);
   if (stats)
     stats->solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   return st;

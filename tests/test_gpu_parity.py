@@ -113,9 +113,14 @@ def test_vcycle_matches(case):
     assert rel_inf(case.host(ud), ref) < TOL * case.amplification()
 
 
-def test_solve_matches_oracle(case):
+@pytest.mark.parametrize("persistent", [0, 1])
+def test_solve_matches_oracle(case, persistent):
+    H = case.H
+    if persistent:
+        H = case.mg.Hierarchy(case.grid, transfer=case.O.transfer, coarse=case.O.coarse, persistent=1)
+        H.setup(case.eps_dev)
     u = case.torch.zeros(case.n(case.L), dtype=case.torch.float64, device="cuda")
-    res = case.H.solve(u, case.b_dev, rel_tol=1e-10, max_cycles=400)
+    res = H.solve(u, case.b_dev, rel_tol=1e-10, max_cycles=400)
     ref, hist = case.O.solve(case.b, 1e-10, 400)
     assert res["cycles"] == len(hist) - 1
     assert rel_inf(case.host(u), ref) < 10 * TOL * case.amplification()
@@ -141,6 +146,26 @@ def test_fp32_finest_sweep_within_fp32_rounding(dim, L, eps):
     bound = np.abs(u32) + c.O.omega * (np.abs(b32) + abs(o.A) @ np.abs(u32)) / o.diag
     err = np.abs(c.host(ud).astype(np.float64) - ref)
     assert np.all(err <= 64 * 2.0**-24 * bound + 1e-30)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed_bf16"])
+def test_host_stepped_solve_matches_persistent(precision):
+    # the same solve through the host-stepped CUDA-graph driver and the persistent
+    # cooperative kernel: identical kernels' arithmetic, so identical cycle counts
+    # and iterates within the solve tolerance
+    res, us = [], []
+    for persistent in (1, 0):
+        c = Case(2, 4, "grf", precision=precision, persistent=persistent, oracle=(persistent == 1))
+        u = c.torch.zeros(c.n(4), dtype=c.torch.float64, device="cuda")
+        res.append(c.H.solve(u, c.b_dev, rel_tol=1e-10, max_cycles=500))
+        us.append(c.host(u))
+        if persistent == 1:
+            ref = c.O.direct(c.b)
+    assert res[0]["rel_residual"] <= 1e-10 and res[1]["rel_residual"] <= 1e-10
+    if precision == "fp64":
+        assert res[0]["cycles"] == res[1]["cycles"]
+        assert rel_inf(us[0], us[1]) < 1e-11
+    assert rel_inf(us[0], ref) < 1e-8 and rel_inf(us[1], ref) < 1e-8
 
 
 def test_encoder_matches_oracle_bit_exact():
