@@ -331,6 +331,125 @@ def run_sweeps(args):
     print(json.dumps(out))
 
 
+def run_batched(args, n_problems=512, seed=3):
+    """Task config 4: n independent 2D problems, edge 3^m cells with m ~ U{3,4,5,6},
+    log-normal eps (sigma 2, correlation length 0.1, seed 1000+i), f ~ U[-1,1]
+    (seed 2000+i), solved to 1e-10 together (mg_batch_solve): mixed vs FP64."""
+    import torch
+
+    import paper_1607_00648_gb300 as mg
+
+    torch.cuda.set_device(0)
+    n = args.batch_size or n_problems
+    ms = syn.batch_problem_sizes(n, seed)
+    grids = {int(m): mg.Grid(2, int(m)) for m in sorted(set(ms.tolist()))}
+    t0 = time.perf_counter()
+    probs = []
+    for i, m in enumerate(ms.tolist()):
+        g = grids[m]
+        eps = syn.lognormal_grf_eps(m, 2, sigma=2.0, seed=1000 + i)
+        b = g.to_slots(m, syn.uniform_load(m, 2, 2000 + i))
+        probs.append((g, m, torch.from_numpy(g.cells_to_concat({m: eps})).cuda(), torch.from_numpy(b).cuda()))
+    t_inputs = time.perf_counter() - t0
+    total_dofs = sum(g.info(m).n_dofs for g, m, _, _ in probs)
+    out = {"workload": f"batch{n}-2d", "problems": n, "dofs": total_dofs, "inputs_s": t_inputs,
+           "sizes": {str(3**m): int((ms == m).sum()) for m in sorted(set(ms.tolist()))}}
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    for prec in ("mixed_bf16", "fp64"):
+        Hs = [mg.Hierarchy(g, precision=prec) for g, m, _, _ in probs]
+        us = [torch.zeros_like(b) for _, _, _, b in probs]
+        bs = [b for _, _, _, b in probs]
+
+        for H, (_, _, e, _) in zip(Hs, probs):
+            H.setup(e)
+        batch = mg.Batch(Hs)
+        eps_list = [e for _, _, e, _ in probs]
+
+        def setup_all():
+            batch.setup(eps_list)
+
+        batch.solve(us, bs, rel_tol=1e-10, max_cycles=3000)  # warm-up (graph capture)
+        times, setups = [], []
+        for _ in range(max(1, args.steps)):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record()
+            setup_all()
+            e1.record()
+            status, stats = batch.solve(us, bs, rel_tol=1e-10, max_cycles=3000)
+            e2.record()
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e2))
+            setups.append(e0.elapsed_time(e1))
+        t = statistics.median(times) / 1e3
+        cyc = [s["cycles"] for s in stats]
+        out[prec] = {"solves_per_s": n / t, "dof_per_s": total_dofs / t, "s_per_batch": t,
+                     "setup_s": statistics.median(setups) / 1e3, "status": status,
+                     "cycles_median": statistics.median(cyc), "cycles_max": max(cyc),
+                     "max_rel_residual": max(s["rel_residual"] for s in stats)}
+        del batch, Hs
+        torch.cuda.empty_cache()
+    out["mixed_speedup"] = out["mixed_bf16"]["solves_per_s"] / out["fp64"]["solves_per_s"]
+    print(json.dumps(out))
+
+
+def run_serve(args, seed=4):
+    """Task config 5: Poisson arrivals (mean 200 req/s) of 3D solves with edges
+    {27, 81, 243} cells (weights 6:3:1), log-normal eps (sigma 1.5, correlation length
+    0.1), f ~ U[-1,1], tolerance 1e-8 each, mixed precision, served by mg_server with
+    an HBM budget; reports solves/s and p50 / p99 latency from submission."""
+    import torch
+
+    import paper_1607_00648_gb300 as mg
+
+    torch.cuda.set_device(0)
+    n = args.serve_requests
+    arrivals, levels = syn.poisson_arrivals(n, 200.0, seed)
+    grids = {int(L): mg.Grid(3, int(L)) for L in sorted(set(levels.tolist()))}
+    reqs = []
+    t0 = time.perf_counter()
+    for i, L in enumerate(levels.tolist()):
+        g = grids[L]
+        inf = g.info(L)
+        eps = syn.lognormal_grf_eps_torch(L, 3, sigma=1.5, seed=1000 + i)
+        c = torch.from_numpy(g.tables(L)["coords"]).cuda().long()
+        ok = c[:, 0] >= 0
+        cat = torch.zeros(g.n_slots_total(), dtype=torch.float64, device="cuda")
+        sl = torch.zeros(inf.n_slots, dtype=torch.float64, device="cuda")
+        sl[ok] = eps[c[ok, 0], c[ok, 1], c[ok, 2]]
+        cat[inf.slot_offset: inf.slot_offset + inf.n_slots] = sl
+        gen = torch.Generator(device="cuda")
+        gen.manual_seed(2000 + i)
+        f = torch.rand(inf.n_slots, generator=gen, device="cuda", dtype=torch.float64) * 2 - 1
+        dof = torch.from_numpy(g.dof_mask(L)).cuda()
+        b = torch.where(dof, f * (3.0**-L) ** 3, torch.zeros_like(f))
+        reqs.append((g, L, cat, b, torch.zeros_like(b)))
+    torch.cuda.synchronize()
+    t_inputs = time.perf_counter() - t0
+    budget = int(args.serve_budget_gb * (1 << 30))
+    sv = mg.Server(budget, precision="mixed_bf16")
+    start = time.perf_counter()
+    tickets = []
+    for (g, L, e, b, u), ta in zip(reqs, arrivals.tolist()):
+        now = time.perf_counter() - start
+        if ta > now:
+            time.sleep(ta - now)
+        tickets.append(sv.submit(g, e, b, u, rel_tol=1e-8, max_cycles=2000))
+    res = [sv.poll(t, wait=True) for t in tickets]
+    wall = time.perf_counter() - start
+    sv.close()
+    lat = sorted(r["latency_ms"] for r in res)
+    dofs = sum(g.info(L).n_dofs for g, L, _, _, _ in reqs)
+    out = {"workload": f"serve{n}-3d", "requests": n, "solves_per_s": n / wall, "dof_per_s": dofs / wall,
+           "p50_ms": lat[len(lat) // 2], "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+           "max_ms": lat[-1], "wall_s": wall, "arrival_span_s": float(arrivals[-1]), "inputs_s": t_inputs,
+           "failed": sum(1 for r in res if r["status"] != 0),
+           "max_rel_residual": max(r["rel_residual"] for r in res), "budget_gb": args.serve_budget_gb,
+           "sizes": {str(3**L): int((levels == L).sum()) for L in sorted(set(levels.tolist()))}}
+    print(json.dumps(out))
+
+
 def cpu_baseline(w, gpu_cycles, sample_cycles=15):
     """The oracle as it stands on one host core: setup + a bounded number of V-cycles of
     the full workload, extrapolated to the cycle count of the solve."""
@@ -412,10 +531,19 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="checker2d-l6", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline leg")
+    ap.add_argument("--batched", action="store_true", help="task config 4: batched mixed vs FP64 solves")
+    ap.add_argument("--serve", action="store_true", help="task config 5: served 3D requests, p50 / p99 latency")
+    ap.add_argument("--serve-requests", type=int, default=300)
+    ap.add_argument("--serve-budget-gb", type=float, default=64.0)
+    ap.add_argument("--batch-size", type=int, default=0)
     ap.add_argument("--sweep-level", type=int, default=0,
                     help="time only the finest-level FP64 / FP32 sweeps on a 2D grid of this level")
     args = ap.parse_args()
-    if args.sweep_level:
+    if args.serve:
+        run_serve(args)
+    elif args.batched:
+        run_batched(args)
+    elif args.sweep_level:
         run_sweeps(args)
     elif args.impl == "reference":
         run_reference(args)

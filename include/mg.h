@@ -158,6 +158,10 @@ void mg_default_options(mg_options* opt); /* BoxMG, Galerkin, FP64, V(2,2), omeg
  * options this build does not handle). */
 mg_status mg_hier_create(const mg_grid* grid, const mg_options* opt, mg_hier** out);
 
+/* Device bytes mg_hier_create would allocate for this grid and options (admission
+ * control and capacity planning).  opt NULL = defaults. */
+mg_status mg_hier_footprint(const mg_grid* grid, const mg_options* opt, size_t* bytes);
+
 /* Setup (A8-A11): from leaf-cell coefficients eps (device, level-concatenated cell
  * slots, n = sum of n_slots over levels 0..L, read at existing unrefined cells),
  * compute coarse coefficients (mean of the 3^d children), BoxMG P per coarse
@@ -243,6 +247,71 @@ typedef struct mg_solve_stats {
  * the last iterate. */
 mg_status mg_solve(mg_hier* h, double* u, const double* b, double rel_tol, int max_cycles,
                    mg_solve_stats* stats, void* stream);
+
+/* ---------------------------------------------------------------- A13 batched solves */
+
+typedef struct mg_batch mg_batch;
+
+/* Group n set-up hierarchies (same dimension and options, any sizes) into one batch.
+ * The problems of a batch advance through their V-cycles in lockstep, aligned by
+ * depth below their own finest level; every phase of a cycle is one launch per brick
+ * edge over the work items of all problems.  hiers: host array of n handles that must
+ * outlive the batch (the batch reads their operators; re-running mg_setup on them
+ * keeps the batch valid).  Errors: MG_ERR_INVALID_ARG on mismatched options or
+ * hierarchies not set up (or with more than 64 coarsest DoFs). */
+mg_status mg_batch_create(int n, mg_hier* const* hiers, mg_batch** out);
+
+/* mg_setup of every problem of the batch (eps: host array of n device pointers, as in
+ * mg_setup), enqueued back to back with one synchronisation and one status check at
+ * the end instead of one per problem.  Errors as mg_setup (the first failing problem). */
+mg_status mg_batch_setup(mg_batch* batch, const double* const* eps, void* stream);
+
+/* Solve all problems of the batch from u = 0 to rel_tol each (FP64, or FP64
+ * refinement around inner_cycles FP32 V-cycles for mixed hierarchies).  u, b: host
+ * arrays of n device pointers (finest-level vectors of each problem).  stats: host
+ * array of n entries (nullable); per-problem cycles, r0, final relative residual,
+ * status.  Converged problems retire on the device while the others continue.
+ * Synchronises the stream.  Returns the first non-OK per-problem status. */
+mg_status mg_batch_solve(mg_batch* batch, double* const* u, const double* const* b, double rel_tol, int max_cycles,
+                         mg_solve_stats* stats, void* stream);
+
+void mg_batch_destroy(mg_batch* batch);
+
+/* ---------------------------------------------------------------- A13 serving */
+
+typedef struct mg_server mg_server;
+
+typedef struct mg_request {
+  const mg_grid* grid; /* uniform grid of the problem (caller-owned, alive until done) */
+  const double* eps;   /* device, level-concatenated leaf coefficients (as mg_setup) */
+  const double* b;     /* device, finest-level right-hand side */
+  double* u;           /* device, finest-level solution (written by the server) */
+  double rel_tol;
+  int32_t max_cycles;
+  int32_t reserved;
+} mg_request;
+
+/* Start a server on the current device: a thread that admits submitted requests in
+ * arrival order while their hierarchies fit hbm_budget_bytes, sets them up, and runs
+ * all admitted requests as one continuously re-formed batch (requests join at the next
+ * step boundary and retire, releasing their memory, as soon as they converge).  opt:
+ * options of every request (NULL = defaults). */
+mg_status mg_server_create(size_t hbm_budget_bytes, const mg_options* opt, mg_server** out);
+
+/* Queue a request; *ticket identifies it.  The request's buffers must stay valid until
+ * it is done.  MG_ERR_BUDGET if its hierarchy alone exceeds the budget. */
+mg_status mg_server_submit(mg_server* server, const mg_request* req, uint64_t* ticket);
+
+/* *done = 1 once the request finished (then stats, nullable, get its cycles, r0,
+ * final relative residual and latency from submission in solve_ms, and the ticket is
+ * released); wait != 0 blocks until then.  Returns the request's status when done. */
+mg_status mg_server_poll(mg_server* server, uint64_t ticket, int wait, int* done, mg_solve_stats* stats);
+
+/* Queue length, running requests and device bytes held by admitted requests. */
+mg_status mg_server_info(mg_server* server, int64_t* queued, int64_t* running, size_t* bytes_in_use);
+
+/* Stops the thread (requests still queued or running are abandoned) and frees everything. */
+void mg_server_destroy(mg_server* server);
 
 /* ---------------------------------------------------------------- inspection (parity tests) */
 

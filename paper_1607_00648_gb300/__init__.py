@@ -13,7 +13,7 @@ import numpy as np
 from . import _lib
 from ._lib import MgError, Options, SolveStats, check, load
 
-__all__ = ["Grid", "Hierarchy", "MgError", "default_options", "encode_deltas", "load"]
+__all__ = ["Batch", "Server", "Grid", "Hierarchy", "MgError", "default_options", "encode_deltas", "load"]
 
 TRANSFER = {"dlinear": 0, "boxmg": 1}
 COARSE = {"redisc": 0, "galerkin": 1}
@@ -133,6 +133,14 @@ def default_options(**kw) -> Options:
     return o
 
 
+def hier_footprint(grid, **options) -> int:
+    """Device bytes a hierarchy of this grid and options would hold."""
+    o = default_options(**options)
+    n = C.c_size_t()
+    check(load().mg_hier_footprint(grid.handle, C.byref(o), C.byref(n)), "mg_hier_footprint")
+    return n.value
+
+
 class Hierarchy:
     """Device-resident multigrid hierarchy of a grid (mg_hier_create / mg_setup / solvers)."""
 
@@ -217,6 +225,81 @@ class Hierarchy:
         f = lambda t: _dptr(t) if t is not None else None
         check(load().mg_get_codes(self._h, level, f(a_codes), f(a_scale), f(p_codes), f(p_scale),
                                   _stream_ptr(stream)), "mg_get_codes")
+
+
+class Batch:
+    """Many set-up hierarchies solved together (mg_batch_create / mg_batch_solve)."""
+
+    def __init__(self, hierarchies):
+        self.hiers = list(hierarchies)  # keep the handles alive as long as the batch
+        arr = (C.c_void_p * len(self.hiers))(*[h.handle.value for h in self.hiers])
+        h = C.c_void_p()
+        check(load().mg_batch_create(len(self.hiers), arr, C.byref(h)), "mg_batch_create")
+        self._h = h
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            load().mg_batch_destroy(h)
+            self._h = None
+
+    def setup(self, eps_list, stream=None):
+        n = len(self.hiers)
+        ea = (C.c_void_p * n)(*[e.data_ptr() for e in eps_list])
+        check(load().mg_batch_setup(self._h, ea, _stream_ptr(stream)), "mg_batch_setup")
+
+    def solve(self, us, bs, rel_tol=1e-10, max_cycles=500, stream=None, raise_on_fail=True):
+        n = len(self.hiers)
+        ua = (C.c_void_p * n)(*[u.data_ptr() for u in us])
+        ba = (C.c_void_p * n)(*[b.data_ptr() for b in bs])
+        st = (SolveStats * n)()
+        status = load().mg_batch_solve(self._h, ua, ba, rel_tol, max_cycles, st, _stream_ptr(stream))
+        if raise_on_fail:
+            check(status, "mg_batch_solve")
+        return status, [{"cycles": s.cycles, "outer_steps": s.outer_steps, "rel_residual": s.rel_residual,
+                         "r0_norm": s.r0_norm, "solve_ms": s.solve_ms} for s in st]
+
+
+class Server:
+    """Continuous-batching solve server (mg_server_*): submit requests, poll results."""
+
+    def __init__(self, hbm_budget_bytes: int, **options):
+        self.options = default_options(**options)
+        h = C.c_void_p()
+        check(load().mg_server_create(int(hbm_budget_bytes), C.byref(self.options), C.byref(h)), "mg_server_create")
+        self._h = h
+        self._keep = {}
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            load().mg_server_destroy(h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def submit(self, grid, eps, b, u, rel_tol=1e-8, max_cycles=500) -> int:
+        req = _lib.Request(grid.handle.value, eps.data_ptr(), b.data_ptr(), u.data_ptr(), rel_tol, max_cycles, 0)
+        t = C.c_uint64()
+        check(load().mg_server_submit(self._h, C.byref(req), C.byref(t)), "mg_server_submit")
+        self._keep[t.value] = (grid, eps, b, u)
+        return t.value
+
+    def poll(self, ticket: int, wait: bool = False):
+        done = C.c_int(0)
+        st = SolveStats()
+        status = load().mg_server_poll(self._h, ticket, 1 if wait else 0, C.byref(done), C.byref(st))
+        if not done.value:
+            return None
+        self._keep.pop(ticket, None)
+        return {"status": status, "cycles": st.cycles, "rel_residual": st.rel_residual, "r0_norm": st.r0_norm,
+                "latency_ms": st.solve_ms}
+
+    def info(self):
+        q, r, b = C.c_int64(), C.c_int64(), C.c_size_t()
+        check(load().mg_server_info(self._h, C.byref(q), C.byref(r), C.byref(b)), "mg_server_info")
+        return {"queued": q.value, "running": r.value, "bytes_in_use": b.value}
 
 
 def encode_deltas(delta, codes, scale, fmt: int, stream=None):

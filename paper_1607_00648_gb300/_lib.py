@@ -46,6 +46,11 @@ class SolveStats(C.Structure):
                 ("history_capacity", C.c_int32), ("history_len", C.c_int32)]
 
 
+class Request(C.Structure):
+    _fields_ = [("grid", C.c_void_p), ("eps", C.c_void_p), ("b", C.c_void_p), ("u", C.c_void_p),
+                ("rel_tol", C.c_double), ("max_cycles", C.c_int32), ("reserved", C.c_int32)]
+
+
 _P = C.c_void_p
 _I32P = C.POINTER(C.c_int32)
 _U8P = C.POINTER(C.c_uint8)
@@ -59,6 +64,7 @@ _SIGS = {
     "mg_destroy_grid": (None, [_P]),
     "mg_default_options": (None, [C.POINTER(Options)]),
     "mg_hier_create": (C.c_int, [_P, C.POINTER(Options), C.POINTER(_P)]),
+    "mg_hier_footprint": (C.c_int, [_P, C.POINTER(Options), C.POINTER(C.c_size_t)]),
     "mg_setup": (C.c_int, [_P, _P, _P]),
     "mg_smooth": (C.c_int, [_P, C.c_int, _P, _P, C.c_int, _P]),
     "mg_residual": (C.c_int, [_P, C.c_int, _P, _P, _P, _F64P, _P]),
@@ -75,6 +81,15 @@ _SIGS = {
     "mg_get_deltas": (C.c_int, [_P, C.c_int, _P, _P, _P]),
     "mg_get_codes": (C.c_int, [_P, C.c_int, _P, _P, _P, _P, _P]),
     "mg_encode_deltas": (C.c_int, [C.c_int64, C.c_int, _P, C.c_int, _P, _P, _P]),
+    "mg_batch_create": (C.c_int, [C.c_int, C.POINTER(_P), C.POINTER(_P)]),
+    "mg_batch_solve": (C.c_int, [_P, C.POINTER(_P), C.POINTER(_P), C.c_double, C.c_int, C.POINTER(SolveStats), _P]),
+    "mg_batch_setup": (C.c_int, [_P, C.POINTER(_P), _P]),
+    "mg_batch_destroy": (None, [_P]),
+    "mg_server_create": (C.c_int, [C.c_size_t, C.POINTER(Options), C.POINTER(_P)]),
+    "mg_server_submit": (C.c_int, [_P, C.POINTER(Request), C.POINTER(C.c_uint64)]),
+    "mg_server_poll": (C.c_int, [_P, C.c_uint64, C.c_int, C.POINTER(C.c_int), C.POINTER(SolveStats)]),
+    "mg_server_info": (C.c_int, [_P, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_size_t)]),
+    "mg_server_destroy": (None, [_P]),
     "mg_destroy_hier": (None, [_P]),
     "mg_last_error": (C.c_char_p, []),
     "mg_version": (C.c_char_p, []),

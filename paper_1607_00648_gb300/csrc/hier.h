@@ -71,4 +71,25 @@ struct Hier {
   Graph g_cycle64, g_outer, g_inner;
 };
 
+// enqueue a hierarchy's setup without synchronising; setup_status interprets d_status
+mg_status setup_enqueue(Hier& H, const double* eps, cudaStream_t s);
+mg_status setup_status(Hier& H, int status);
+
+// ---- batched solves (batch.cu), used by the batch C ABI and the server ----
+struct Batch;
+struct ProblemState {
+  int active, cycles, status;  // status: 0 converged, 1 not converged (yet), 2 non-finite, 3 diverged
+  double r0, rel, sigma, tol;
+  int max_cycles;
+};
+mg_status batch_create(const std::vector<Hier*>& hs, Batch** out);
+void batch_destroy(Batch* bt);
+void batch_set_graph(Batch* bt, bool use_graph);
+mg_status batch_begin(Batch& bt, double* const* u, const double* const* b, const std::vector<ProblemState>& init,
+                      const std::vector<int>& fresh, cudaStream_t s);
+mg_status batch_run(Batch& bt, int max_steps, cudaStream_t s, int* n_active);
+mg_status batch_read(Batch& bt, std::vector<ProblemState>& out, cudaStream_t s);
+mg_status status_of(int st);
+size_t hier_footprint(const Grid& g, const mg_options& o);
+
 }  // namespace mg

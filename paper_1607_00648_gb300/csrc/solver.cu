@@ -409,6 +409,28 @@ static mg_status create(const Grid* g, const mg_options& o, Hier** out) {
   return MG_OK;
 }
 
+// device bytes mg_hier_create allocates for a grid and options (admission by HBM footprint)
+size_t hier_footprint(const Grid& g, const mg_options& o) {
+  const int d = g.dim;
+  const size_t n3 = ipow(3, d), n5 = ipow(5, d), full = 1u << d;
+  const bool galerkin = o.coarse == MG_COARSE_GALERKIN, boxmg = o.transfer == MG_TRANSFER_BOXMG;
+  const bool mixed = o.precision != MG_PREC_FP64;
+  size_t bytes = 64 * 1024;  // small fixed buffers (status, scalars, history, parameter block)
+  for (int l = o.coarsest_level; l <= g.L; ++l) {
+    const HostLevel& hl = g.levels[l];
+    const size_t ns = static_cast<size_t>(hl.n_slots), nb = static_cast<size_t>(hl.n_bricks);
+    bytes += nb * n3 * 4 + nb * d * 4 + hl.brick_rank.size() * 4 + 2 * ns + ns * full * 12;
+    bytes += 3 * ns * 8 + nb * hl.B * 8 + 4;
+    if (l < g.L) bytes += 2 * ns * 8 + (galerkin ? ns * n3 * 8 : 0) + (boxmg ? ns * n5 * 8 : 0);
+    if (mixed) {
+      bytes += 5 * ns * 4;
+      if (l < g.L) bytes += (galerkin ? ns * n3 * 2 + ns * 4 : 0) + (boxmg ? ns * n5 * 2 + ns * 4 : 0);
+    }
+  }
+  const size_t nc = static_cast<size_t>(g.levels[o.coarsest_level].n_dofs);
+  return bytes + nc * nc * 8 + g.levels[o.coarsest_level].n_slots * 4 + nc * 4;
+}
+
 // ----------------------------------------------------------------------------- kernel dispatch
 
 constexpr int64_t kSweepTargetCtas = 4 * 152;  // spread small levels over the SMs
@@ -543,7 +565,7 @@ static void residual_norm(Hier& H, const T* u, const T* b, T* r, int slot, cudaS
   sweep<T>(H, H.L, kResidual, u, b, r, H.d_scal + slot, s);
 }
 
-static mg_status run_setup(Hier& H, const double* eps_in, cudaStream_t s) {
+static mg_status run_setup(Hier& H, const double* eps_in, cudaStream_t s, bool check_now = true) {
   const Grid& g = *H.g;
   const int d = H.dim;
   for (int l = H.c; l <= H.L; ++l) {
@@ -627,9 +649,17 @@ static mg_status run_setup(Hier& H, const double* eps_in, cudaStream_t s) {
     }
     MG_CHECK(last_launch("setup: encode"));
   }
+  if (!check_now) {  // the caller reads d_status after one synchronisation for many hierarchies
+    H.ready = true;
+    return MG_OK;
+  }
   int status = 0;
   MG_TRY_CUDA(cudaMemcpyAsync(&status, H.d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
   MG_TRY_CUDA(cudaStreamSynchronize(s));
+  return setup_status(H, status);
+}
+
+mg_status setup_status(Hier& H, int status) {
   if (status == 1) {
     set_error("mg_setup: a BoxMG patch system is singular");
     return MG_ERR_INDEFINITE_COARSE;
@@ -645,6 +675,8 @@ static mg_status run_setup(Hier& H, const double* eps_in, cudaStream_t s) {
   H.ready = true;
   return MG_OK;
 }
+
+mg_status setup_enqueue(Hier& H, const double* eps, cudaStream_t s) { return run_setup(H, eps, s, false); }
 
 static cudaStream_t pick(Hier& H, void* stream) {
   return stream ? static_cast<cudaStream_t>(stream) : H.own;
@@ -1024,6 +1056,25 @@ mg_status mg_hier_create(const mg_grid* grid, const mg_options* opt, mg_hier** o
     set_error("mg_hier_create: out of host memory");
     return MG_ERR_OOM;
   }
+  return MG_OK;
+}
+
+mg_status mg_hier_footprint(const mg_grid* grid, const mg_options* opt, size_t* bytes) {
+  if (!grid || !bytes) {
+    set_error("mg_hier_footprint: NULL argument");
+    return MG_ERR_INVALID_ARG;
+  }
+  mg_options o;
+  if (opt)
+    o = *opt;
+  else
+    mg_default_options(&o);
+  const Grid* g = reinterpret_cast<const Grid*>(grid);
+  if (o.coarsest_level < 1 || o.coarsest_level >= g->L) {
+    set_error("mg_hier_footprint: invalid coarsest level");
+    return MG_ERR_INVALID_ARG;
+  }
+  *bytes = hier_footprint(*g, o);
   return MG_OK;
 }
 

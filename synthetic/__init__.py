@@ -111,6 +111,28 @@ def lognormal_grf_eps(level: int, dim: int, sigma: float, seed: int,
     return eps.astype(np.float32).astype(np.float64)
 
 
+def lognormal_grf_eps_torch(level: int, dim: int, sigma: float, seed: int, corr_len: float = 0.1,
+                            device: str = "cuda"):
+    """The same recipe as lognormal_grf_eps, generated on a GPU with torch.fft (for
+    fields too large to synthesise quickly on the host); returns an FP64 torch tensor
+    indexed [x, y(, z)].  Its random stream is torch's, not numpy's."""
+    import torch
+
+    n = 3**level
+    m = 2 * n
+    gen = torch.Generator(device=device)
+    gen.manual_seed(seed)
+    freqs = torch.fft.fftfreq(m, d=1.0 / n, device=device, dtype=torch.float64)
+    ks = torch.meshgrid(*([freqs] * dim), indexing="ij")
+    k2 = sum(k * k for k in ks)
+    spec = torch.exp(-2.0 * (math.pi**2) * (corr_len**2) * k2)
+    noise = torch.randn((m,) * dim, generator=gen, device=device, dtype=torch.float64)
+    field = torch.fft.ifftn(torch.fft.fftn(noise) * torch.sqrt(spec)).real
+    g = field[tuple(slice(0, n) for _ in range(dim))]
+    g = (g - g.mean()) / g.std()
+    return torch.exp(sigma * g).float().double()
+
+
 def sphere_shell_mask(level: int, dim: int = 3, radius: float = 0.3,
                       centre=(0.5, 0.5, 0.5)) -> np.ndarray:
     """Refinement mask on a uniform level: cells whose box grown by one cell meets |x-c| = r."""
