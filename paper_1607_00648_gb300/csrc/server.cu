@@ -39,7 +39,8 @@ struct Request {
   int max_cycles = 500;
   size_t footprint = 0;
   Hier* h = nullptr;
-  int state = 0;  // 0 queued, 1 admitted (not yet in the batch), 2 running, 3 done
+  int state = 0;  // 0 queued, 1 setting up, 2 running, 3 done
+  cudaEvent_t ev = nullptr;  // completion of the request's setup
   ProblemState ps{};
   mg_status status = MG_OK;
   Clock::time_point t_submit, t_admit, t_done;
@@ -61,6 +62,10 @@ struct Server {
   std::string error;
   std::thread th;
   cudaStream_t stream = nullptr;
+  static constexpr int kSetupStreams = 8;
+  cudaStream_t setup_streams[kSetupStreams] = {};
+  int next_setup = 0;
+  std::vector<Request*> pending;  // setting up (server thread only)
   Batch* batch = nullptr;
   std::vector<Request*> members;  // requests of the current batch, in batch order
 
@@ -71,6 +76,10 @@ struct Server {
 void Server::retire(Request* r, mg_status st) {
   r->status = st;
   r->t_done = Clock::now();
+  if (r->ev) {
+    cudaEventDestroy(r->ev);
+    r->ev = nullptr;
+  }
   if (r->h) {
     mg_destroy_hier(reinterpret_cast<mg_hier*>(r->h));
     r->h = nullptr;
@@ -85,7 +94,7 @@ void Server::loop() {
     std::vector<Request*> admitted;
     {
       std::unique_lock<std::mutex> lk(mu);
-      cv.wait(lk, [&] { return stop || !queue.empty() || !running.empty(); });
+      cv.wait(lk, [&] { return stop || !queue.empty() || !running.empty() || !pending.empty(); });
       if (stop) break;
       // admission by HBM footprint, in arrival order
       while (!queue.empty() && used + queue.front()->footprint <= budget) {
@@ -97,14 +106,18 @@ void Server::loop() {
         admitted.push_back(r);
       }
     }
-    // hierarchies and setups of the admitted requests (outside the lock)
-    std::vector<Request*> ready;
+    // hierarchies of the admitted requests; their setups run concurrently on a pool of
+    // streams, overlapping each other and the running batch
     for (Request* r : admitted) {
       mg_hier* h = nullptr;
       mg_status st = mg_hier_create(reinterpret_cast<const mg_grid*>(r->grid), &opt, &h);
       if (st == MG_OK) {
         r->h = reinterpret_cast<Hier*>(h);
-        st = setup_enqueue(*r->h, r->eps, stream);
+        cudaStream_t ss = setup_streams[next_setup++ % kSetupStreams];
+        st = setup_enqueue(*r->h, r->eps, ss);
+        if (st == MG_OK && (cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming) != cudaSuccess ||
+                            cudaEventRecord(r->ev, ss) != cudaSuccess))
+          st = MG_ERR_CUDA;
       }
       if (st != MG_OK) {
         std::lock_guard<std::mutex> lk(mu);
@@ -112,14 +125,27 @@ void Server::loop() {
         cv.notify_all();
         continue;
       }
-      ready.push_back(r);
+      pending.push_back(r);
     }
-    if (!ready.empty()) {
-      cudaStreamSynchronize(stream);
-      for (Request* r : ready) {
+    // requests whose setup finished join the running set
+    {
+      std::vector<Request*> still;
+      bool any_running;
+      {
+        std::lock_guard<std::mutex> lk(mu);
+        any_running = !running.empty();
+      }
+      for (size_t i = 0; i < pending.size(); ++i) {
+        Request* r = pending[i];
+        cudaError_t q = cudaEventQuery(r->ev);
+        if (q == cudaErrorNotReady && !any_running && still.empty()) q = cudaEventSynchronize(r->ev);
+        if (q == cudaErrorNotReady) {
+          still.push_back(r);
+          continue;
+        }
         int status = 0;
-        cudaMemcpy(&status, r->h->d_status, sizeof(int), cudaMemcpyDeviceToHost);
-        const mg_status st = setup_status(*r->h, status);
+        if (q == cudaSuccess) cudaMemcpy(&status, r->h->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+        const mg_status st = q == cudaSuccess ? setup_status(*r->h, status) : MG_ERR_CUDA;
         std::lock_guard<std::mutex> lk(mu);
         if (st != MG_OK) {
           retire(r, st);
@@ -129,6 +155,7 @@ void Server::loop() {
           running.push_back(r);
         }
       }
+      pending.swap(still);
     }
     // re-form the batch when its membership changed, carrying the state over
     std::vector<Request*> now;
@@ -231,7 +258,10 @@ mg_status mg_server_create(size_t hbm_budget_bytes, const mg_options* opt, mg_se
   else
     mg_default_options(&sv->opt);
   cudaGetDevice(&sv->device);
-  if (cudaStreamCreateWithFlags(&sv->stream, cudaStreamNonBlocking) != cudaSuccess) {
+  bool ok = cudaStreamCreateWithFlags(&sv->stream, cudaStreamNonBlocking) == cudaSuccess;
+  for (int i = 0; i < Server::kSetupStreams && ok; ++i)
+    ok = cudaStreamCreateWithFlags(&sv->setup_streams[i], cudaStreamNonBlocking) == cudaSuccess;
+  if (!ok) {
     delete sv;
     set_error("mg_server_create: cudaStreamCreate failed");
     return MG_ERR_CUDA;
@@ -343,11 +373,15 @@ void mg_server_destroy(mg_server* server) {
   if (sv->th.joinable()) sv->th.join();
   cudaSetDevice(sv->device);
   if (sv->batch) batch_destroy(sv->batch);
+  cudaDeviceSynchronize();
   for (auto& kv : sv->all) {
     if (kv.second->h) mg_destroy_hier(reinterpret_cast<mg_hier*>(kv.second->h));
+    if (kv.second->ev) cudaEventDestroy(kv.second->ev);
     delete kv.second;
   }
   cudaStreamDestroy(sv->stream);
+  for (int i = 0; i < Server::kSetupStreams; ++i)
+    if (sv->setup_streams[i]) cudaStreamDestroy(sv->setup_streams[i]);
   delete sv;
 }
 

@@ -70,9 +70,9 @@ __device__ __forceinline__ bool small_solve(double (&M)[NMAX][NMAX], double (&rh
   return true;
 }
 
-// BoxMG prolongation (Sect. 4.4, App. C).  One thread per coarse vertex V; for
-// each of its 2^d patches (sign vector sigma) the 3^d P entries of V inside the
-// patch solve C(s) p = f in the reference orientation: c-point p = 1, then for
+// BoxMG prolongation (Sect. 4.4, App. C).  One thread per coarse vertex V and
+// patch (sign vector sigma, one of the 2^d cells around V): the 3^d P entries of
+// V inside the patch solve C(s) p = f in the reference orientation: c-point p = 1, then for
 // each set N of non-zero axes (lines, then faces, then the interior) the
 // 2^|N| unknowns with exactly those axes non-zero, from stencils collapsed over
 // the other axes; unknowns at reference coordinate 3 vanish.  The system is
@@ -80,19 +80,22 @@ __device__ __forceinline__ bool small_solve(double (&M)[NMAX][NMAX], double (&rh
 // entry lying on a line / face through V is written by the patch with
 // sigma_i = +1 on its zero axes.  Output: P_hat = P - P_dlin on 5^d planes.
 template <int DIM>
-__global__ void __launch_bounds__(128) k_boxmg(LevelDesc Lc, LevelDesc Lf, const double* eps_f,
-                                                 const double* ahat_f, double* phat_c, int* status) {
+__global__ void __launch_bounds__(64) k_boxmg(LevelDesc Lc, LevelDesc Lf, const double* eps_f,
+                                                const double* ahat_f, double* phat_c, int* status) {
   constexpr int N3 = cpow(3, DIM), N5 = cpow(5, DIM);
-  const int64_t cs = blockIdx.x * static_cast<int64_t>(128) + threadIdx.x;
+  // one thread per (coarse slot, patch): the patches of a vertex write disjoint entries
+  const int64_t tid = blockIdx.x * static_cast<int64_t>(64) + threadIdx.x;
+  const int64_t cs = tid >> DIM;
+  const int sg = static_cast<int>(tid & ((1 << DIM) - 1));
   if (cs >= Lc.n_slots) return;
   int V[DIM];
   const bool valid = coords_of<DIM>(Lc, cs, V);
   if (!valid || !is_dof(Lc.vflags[cs])) {
-    if (valid)
+    if (valid && sg == 0)
       for (int k = 0; k < N5; ++k) phat_c[plane_index(Lc, cs, k, N5)] = 0.0;
     return;
   }
-  for (int sg = 0; sg < (1 << DIM); ++sg) {
+  {
     int sigma[DIM];
 #pragma unroll
     for (int i = 0; i < DIM; ++i) sigma[i] = ((sg >> i) & 1) ? -1 : 1;
@@ -212,7 +215,7 @@ template <int DIM, int PMODE>
 __global__ void __launch_bounds__(128) k_rap(LevelDesc Lc, LevelDesc Lf, const double* eps_f, const double* ahat_f,
                                                const double* eps_c, const double* phat_c, double* ahat_c) {
   constexpr int N3 = cpow(3, DIM), N5 = cpow(5, DIM);
-  const int64_t cs = blockIdx.x * static_cast<int64_t>(128) + threadIdx.x;
+  const int64_t cs = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
   if (cs >= Lc.n_slots) return;
   int V[DIM];
   const bool valid = coords_of<DIM>(Lc, cs, V);

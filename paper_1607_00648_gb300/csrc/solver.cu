@@ -588,22 +588,24 @@ static mg_status run_setup(Hier& H, const double* eps_in, cudaStream_t s, bool c
     const double* ahat_f = (l < H.L && H.galerkin) ? F.ahat : nullptr;
     const unsigned gb = static_cast<unsigned>((C.d.n_slots + 127) / 128);
     if (H.boxmg) {
+      const unsigned gp = static_cast<unsigned>(((C.d.n_slots << d) + 63) / 64);
       if (d == 2)
-        k_boxmg<2><<<gb, 128, 0, s>>>(C.d, F.d, F.eps, ahat_f, C.phat, H.d_status);
+        k_boxmg<2><<<gp, 64, 0, s>>>(C.d, F.d, F.eps, ahat_f, C.phat, H.d_status);
       else
-        k_boxmg<3><<<gb, 128, 0, s>>>(C.d, F.d, F.eps, ahat_f, C.phat, H.d_status);
+        k_boxmg<3><<<gp, 64, 0, s>>>(C.d, F.d, F.eps, ahat_f, C.phat, H.d_status);
     }
     if (H.galerkin) {
+      const unsigned gr = static_cast<unsigned>((C.d.n_slots + 31) / 32);  // small CTAs: spread small levels
       if (d == 2) {
         if (H.boxmg)
-          k_rap<2, 1><<<gb, 128, 0, s>>>(C.d, F.d, F.eps, ahat_f, C.eps, C.phat, C.ahat);
+          k_rap<2, 1><<<gr, 32, 0, s>>>(C.d, F.d, F.eps, ahat_f, C.eps, C.phat, C.ahat);
         else
-          k_rap<2, 0><<<gb, 128, 0, s>>>(C.d, F.d, F.eps, ahat_f, C.eps, C.phat, C.ahat);
+          k_rap<2, 0><<<gr, 32, 0, s>>>(C.d, F.d, F.eps, ahat_f, C.eps, C.phat, C.ahat);
       } else {
         if (H.boxmg)
-          k_rap<3, 1><<<gb, 128, 0, s>>>(C.d, F.d, F.eps, ahat_f, C.eps, C.phat, C.ahat);
+          k_rap<3, 1><<<gr, 32, 0, s>>>(C.d, F.d, F.eps, ahat_f, C.eps, C.phat, C.ahat);
         else
-          k_rap<3, 0><<<gb, 128, 0, s>>>(C.d, F.d, F.eps, ahat_f, C.eps, C.phat, C.ahat);
+          k_rap<3, 0><<<gr, 32, 0, s>>>(C.d, F.d, F.eps, ahat_f, C.eps, C.phat, C.ahat);
       }
     }
     MG_CHECK(last_launch("setup: BoxMG / Galerkin"));
