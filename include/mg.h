@@ -154,8 +154,13 @@ void mg_default_options(mg_options* opt); /* BoxMG, Galerkin, FP64, V(2,2), omeg
 
 /* Allocate the device-resident hierarchy of a grid (operators, deltas, work
  * vectors) on the current device.  Allocation happens here only.
- * Errors: MG_ERR_INVALID_ARG, MG_ERR_OOM, MG_ERR_UNSUPPORTED (adaptive grids with
- * options this build does not handle). */
+ * Adaptive grids (Sect. 3, hierarchical generating system): a grid whose levels
+ * 0 .. L-2 are refined everywhere, so that level t = L-1 is complete and only its
+ * refinement to level L is partial, gets a composite hierarchy: BoxMG / Galerkin
+ * operators on the complete levels t .. c, d-linear transfer between t and L, and
+ * the composite cycle of mg_vcycle / mg_solve.  Needs coarsest_level < L-1.
+ * Errors: MG_ERR_INVALID_ARG, MG_ERR_OOM, MG_ERR_UNSUPPORTED (an adaptive grid
+ * refined in part below level L-1). */
 mg_status mg_hier_create(const mg_grid* grid, const mg_options* opt, mg_hier** out);
 
 /* Device bytes mg_hier_create would allocate for this grid and options (admission
@@ -202,7 +207,7 @@ mg_status mg_interpolate_hanging(mg_hier* h, int level, const double* u_coarse, 
 mg_status mg_smooth_f32(mg_hier* h, int level, float* u, const float* b, int nu, void* stream);
 mg_status mg_residual_f32(mg_hier* h, int level, const float* u, const float* b, float* r, double* norm2_host,
                           void* stream);
-mg_status mg_vcycle_f32(mg_hier* h, float* u, const float* b, void* stream);
+mg_status mg_vcycle_f32(mg_hier* h, float* u, const float* b, void* stream); /* uniform grids only */
 
 /* Allocation-free residual: r = b - A u on level and the squared norm of r over the
  * DoFs, written to the device double *norm2 (no host copy, no synchronisation).
@@ -225,7 +230,18 @@ mg_status mg_residual_norm_noalloc(mg_hier* h, int level, const double* u, const
 
 /* One V(nu1, nu2) cycle on the finest level (correction scheme; on uniform
  * grids with Galerkin coarse operators this is the FAS/HTMG cycle of Sect. 3 /
- * Alg. 1).  u, b device finest-level vectors; u updated in place. FP64. */
+ * Alg. 1).  u, b device finest-level vectors; u updated in place. FP64.
+ * Adaptive hierarchy: one composite cycle (Sect. 3: FAS on the levels t = L-1 and
+ * L; nu1 Jacobi sweeps on level L with hanging values interpolated from level t,
+ * the level-t correction equation with R r_L at refined and the level-t residual
+ * at unrefined vertices solved by one V-cycle of levels t .. c, d-linear
+ * correction of level L, nu2 sweeps).  u and b are then level-concatenated vectors
+ * (slot_offset / n_slots of mg_grid_info, like eps); only the level-L and level-t
+ * segments are read or written.  The unknowns are the level-L DoFs and the
+ * unrefined level-t DoFs; b is read there only.  On return the level-L hanging
+ * entries hold the interpolant of level t and the refined level-t entries the
+ * injected level-L value (Sect. 3, rules 1 and 2); on entry the hanging entries
+ * are recomputed and every other non-unknown entry must be zero. */
 mg_status mg_vcycle(mg_hier* h, double* u, const double* b, void* stream);
 
 typedef struct mg_solve_stats {
@@ -244,7 +260,10 @@ typedef struct mg_solve_stats {
  * update (iterative refinement) around inner_cycles FP32 V-cycles that read the
  * BF16/FP16 deltas.  u, b device; stats host, nullable.  Synchronises stream.
  * Returns MG_ERR_NOT_CONVERGED / MG_ERR_DIVERGED / MG_ERR_NONFINITE with u holding
- * the last iterate. */
+ * the last iterate.  Adaptive hierarchy: composite cycles on level-concatenated u
+ * and b (layout as in mg_vcycle); the residual is the composite one (level-L DoFs
+ * and unrefined level-t DoFs); the mixed path refines both levels in FP64 around
+ * FP32 composite cycles; `persistent` is ignored. */
 mg_status mg_solve(mg_hier* h, double* u, const double* b, double rel_tol, int max_cycles,
                    mg_solve_stats* stats, void* stream);
 

@@ -230,7 +230,7 @@ PLevel<T> batch_plevel(const Hier& h, int l) {
   const DevLevel& D = h.lv[l];
   PLevel<T> P{};
   P.d = D.d;
-  const bool coarse = l < h.L;
+  const bool coarse = l < h.top;
   if constexpr (std::is_same<T, double>::value) {
     P.eps = D.eps;
     P.ahat = (coarse && h.galerkin) ? D.ahat : nullptr;
@@ -358,7 +358,7 @@ mg_status build_batch(Batch& bt) {
       set_error("mg_batch_create: every hierarchy of a batch needs the same dimension and options");
       return MG_ERR_INVALID_ARG;
     }
-    if (!h->ready || h->n_c > 64 || h->L >= kMaxLevels) {
+    if (!h->ready || h->adaptive || h->n_c > 64 || h->L >= kMaxLevels) {
       set_error("mg_batch_create: hierarchies must be set up, with at most 64 coarsest DoFs");
       return MG_ERR_INVALID_ARG;
     }

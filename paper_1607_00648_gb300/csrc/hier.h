@@ -51,6 +51,12 @@ struct Hier {
   const Grid* g = nullptr;
   mg_options opt{};
   int L = 0, c = 1, dim = 2;
+  int top = 0;            // finest complete level (= L on uniform grids, L - 1 on adaptive ones)
+  bool adaptive = false;  // level L only partly refined: composite solve
+  int32_t* child_top = nullptr;  // level-top slot -> level-L slot at the same position
+  float* c32 = nullptr;   // mixed composite solve: FP32 level-top correction and its right-hand side
+  float* cb32 = nullptr;
+  int64_t n_comp_dofs = 0;  // composite unknowns: level-L DoFs + unrefined level-(L-1) DoFs
   bool galerkin = false, boxmg = false, mixed = false;
   int fmt = 1;  // 1 bf16, 2 fp16
   std::vector<DevLevel> lv;
@@ -68,7 +74,7 @@ struct Hier {
   void* d_psolve = nullptr;
   cudaStream_t own = nullptr;
   bool ready = false;
-  Graph g_cycle64, g_outer, g_inner;
+  Graph g_cycle64, g_outer, g_inner, g_comp64, g_comp_outer, g_comp_inner;
 };
 
 // enqueue a hierarchy's setup without synchronising; setup_status interprets d_status

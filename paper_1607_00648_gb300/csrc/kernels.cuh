@@ -203,7 +203,13 @@ __device__ __forceinline__ double sweep_item(const SweepArgs<T>& a, int64_t bric
     const int s = z0 * PLANE + i;
     const int64_t slot = base + s;
     T res = T(0);
-    if (is_dof(L.vflags[slot])) {
+    const uint8_t vf = L.vflags[slot];
+    if constexpr (OP == kJacobi || OP == kJacobiNorm) {
+      // hanging vertices keep their value: it is the coarser level's interpolant
+      // (Sect. 3, rule 2), refreshed by the composite cycle, not a smoother unknown
+      if (vf & MG_V_HANGING) res = a.u[slot];
+    }
+    if (is_dof(vf)) {
       const int x = s % B;
       const int y = DIM == 2 ? 0 : (s / B) % B;
       const int zl = s / PLANE - z0;

@@ -69,6 +69,60 @@ __global__ void k_update_f64(int64_t n, double* u, const float* e, const double*
   if (i < n) u[i] = fma(sigma[0], static_cast<double>(e[i]), u[i]);
 }
 
+// ---- composite (adaptive) grid kernels: level t = L - 1 of a tree refined to L in part
+
+// u_t(V) = u_L(3V) at refined level-t DoFs (Sect. 3, rule 1: injection)
+template <typename T>
+__global__ void k_inject(LevelDesc Lt, const int32_t* child, const T* uL, T* ut) {
+  const int64_t s = blockIdx.x * static_cast<int64_t>(kBlock) + threadIdx.x;
+  if (s >= Lt.n_slots) return;
+  const uint8_t f = Lt.vflags[s];
+  if (is_dof(f) && (f & MG_V_REFINED)) ut[s] = uL[child[s]];
+}
+
+// coarse-correction right-hand side: R r_L at refined level-t DoFs (already in
+// rhs), the level-t residual at unrefined ones, zero elsewhere
+template <typename T>
+__global__ void k_compose_rhs(LevelDesc Lt, const T* r_t, T* rhs) {
+  const int64_t s = blockIdx.x * static_cast<int64_t>(kBlock) + threadIdx.x;
+  if (s >= Lt.n_slots) return;
+  const uint8_t f = Lt.vflags[s];
+  if (!is_dof(f))
+    rhs[s] = T(0);
+  else if (!(f & MG_V_REFINED))
+    rhs[s] = r_t[s];
+}
+
+// u_t += e_t at unrefined level-t DoFs
+template <typename T>
+__global__ void k_add_unrefined(LevelDesc Lt, const T* e, T* ut) {
+  const int64_t s = blockIdx.x * static_cast<int64_t>(kBlock) + threadIdx.x;
+  if (s >= Lt.n_slots) return;
+  const uint8_t f = Lt.vflags[s];
+  if (is_dof(f) && !(f & MG_V_REFINED)) ut[s] += e[s];
+}
+
+// r_t = 0 off the unrefined level-t DoFs, and the sum of r_t^2 over them into
+// *norm2 (fixed-order CTA partials, grid-stride over the level)
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_masked_norm(LevelDesc Lt, T* r, double* partial, unsigned* counter,
+                                                          double* norm2) {
+  double part = 0.0;
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * kBlock;
+  for (int64_t s = blockIdx.x * static_cast<int64_t>(kBlock) + threadIdx.x; s < Lt.n_slots; s += stride) {
+    const uint8_t f = Lt.vflags[s];
+    if (is_dof(f) && !(f & MG_V_REFINED)) {
+      const double v = static_cast<double>(r[s]);
+      part += v * v;
+    } else {
+      r[s] = T(0);
+    }
+  }
+  store_partial_and_finish(part, partial, counter, norm2);
+}
+
+__global__ void k_sum2(const double* a, const double* b, double* out) { out[0] = a[0] + b[0]; }
+
 // Round an FP64 value to the nearest (ties to even) BF16 (FMT 1) or FP16 (FMT 2)
 // value, from the IEEE 754 definition of the target format: the quantum is
 // 2^(max(E, Emin) - fraction bits) for the leading-bit exponent E.
@@ -293,6 +347,9 @@ static void free_hier(Hier* H) {
   H->g_cycle64.reset();
   H->g_outer.reset();
   H->g_inner.reset();
+  H->g_comp64.reset();
+  H->g_comp_outer.reset();
+  H->g_comp_inner.reset();
   for (void* p : H->allocs) cudaFree(p);
   if (H->h_pin) cudaFreeHost(H->h_pin);
   if (H->own) cudaStreamDestroy(H->own);
@@ -311,6 +368,8 @@ static mg_status create(const Grid* g, const mg_options& o, Hier** out) {
   H->opt = o;
   H->L = g->L;
   H->c = o.coarsest_level;
+  H->adaptive = !g->uniform;
+  H->top = H->adaptive ? g->L - 1 : g->L;
   H->dim = g->dim;
   H->galerkin = o.coarse == MG_COARSE_GALERKIN;
   H->boxmg = o.transfer == MG_TRANSFER_BOXMG;
@@ -348,6 +407,8 @@ static mg_status create(const Grid* g, const mg_options& o, Hier** out) {
     if (l < H->L) {
       if ((st = dalloc(*H, &D.u, ns)) != MG_OK) return fail(st);
       if ((st = dalloc(*H, &D.b, ns)) != MG_OK) return fail(st);
+    }
+    if (l < H->top) {
       if (H->galerkin && (st = dalloc(*H, &D.ahat, ns * n3)) != MG_OK) return fail(st);
       if (H->boxmg && (st = dalloc(*H, &D.phat, ns * n5)) != MG_OK) return fail(st);
     }
@@ -357,7 +418,7 @@ static mg_status create(const Grid* g, const mg_options& o, Hier** out) {
       if ((st = dalloc(*H, &D.b32, ns)) != MG_OK) return fail(st);
       if ((st = dalloc(*H, &D.r32, ns)) != MG_OK) return fail(st);
       if ((st = dalloc(*H, &D.t32, ns)) != MG_OK) return fail(st);
-      if (l < H->L) {
+      if (l < H->top) {
         if (H->galerkin) {
           if ((st = dalloc(*H, &D.a16, ns * n3)) != MG_OK) return fail(st);
           if ((st = dalloc(*H, &D.ascale, ns)) != MG_OK) return fail(st);
@@ -367,6 +428,29 @@ static mg_status create(const Grid* g, const mg_options& o, Hier** out) {
           if ((st = dalloc(*H, &D.pscale, ns)) != MG_OK) return fail(st);
         }
       }
+    }
+  }
+  if (H->adaptive) {  // injection map of the composite solve and the FP32 composite vectors
+    const HostLevel& ht = g->levels[H->top];
+    const HostLevel& hf = g->levels[H->L];
+    std::vector<int32_t> child(ht.n_slots, -1);
+    int x[3];
+    for (int64_t s = 0; s < ht.n_slots; ++s) {
+      ht.coords_of(s, x);
+      if (x[0] < 0) continue;
+      for (int i = 0; i < d; ++i) x[i] *= 3;
+      child[s] = static_cast<int32_t>(hf.slot_of(x));
+    }
+    if ((st = upload(*H, &H->child_top, child)) != MG_OK) return fail(st);
+    int64_t unref = 0;
+    for (int64_t s = 0; s < ht.n_slots; ++s) {
+      const uint8_t f = ht.vflags[s];
+      if ((f & MG_V_EXISTS) && !(f & (MG_V_BOUNDARY | MG_V_HANGING | MG_V_REFINED))) ++unref;
+    }
+    H->n_comp_dofs = hf.n_dofs + unref;
+    if (H->mixed) {
+      if ((st = dalloc(*H, &H->c32, static_cast<size_t>(ht.n_slots))) != MG_OK) return fail(st);
+      if ((st = dalloc(*H, &H->cb32, static_cast<size_t>(ht.n_slots))) != MG_OK) return fail(st);
     }
   }
   // coarsest dense system
@@ -415,17 +499,20 @@ size_t hier_footprint(const Grid& g, const mg_options& o) {
   const size_t n3 = ipow(3, d), n5 = ipow(5, d), full = 1u << d;
   const bool galerkin = o.coarse == MG_COARSE_GALERKIN, boxmg = o.transfer == MG_TRANSFER_BOXMG;
   const bool mixed = o.precision != MG_PREC_FP64;
+  const int top = g.uniform ? g.L : g.L - 1;
   size_t bytes = 64 * 1024;  // small fixed buffers (status, scalars, history, parameter block)
   for (int l = o.coarsest_level; l <= g.L; ++l) {
     const HostLevel& hl = g.levels[l];
     const size_t ns = static_cast<size_t>(hl.n_slots), nb = static_cast<size_t>(hl.n_bricks);
     bytes += nb * n3 * 4 + nb * d * 4 + hl.brick_rank.size() * 4 + 2 * ns + ns * full * 12;
     bytes += 3 * ns * 8 + nb * hl.B * 8 + 4;
-    if (l < g.L) bytes += 2 * ns * 8 + (galerkin ? ns * n3 * 8 : 0) + (boxmg ? ns * n5 * 8 : 0);
+    if (l < g.L) bytes += 2 * ns * 8;
+    if (l < top) bytes += (galerkin ? ns * n3 * 8 : 0) + (boxmg ? ns * n5 * 8 : 0);
     if (mixed) {
       bytes += 5 * ns * 4;
-      if (l < g.L) bytes += (galerkin ? ns * n3 * 2 + ns * 4 : 0) + (boxmg ? ns * n5 * 2 + ns * 4 : 0);
+      if (l < top) bytes += (galerkin ? ns * n3 * 2 + ns * 4 : 0) + (boxmg ? ns * n5 * 2 + ns * 4 : 0);
     }
+    if (l == top && top < g.L) bytes += ns * 4 + (mixed ? 2 * ns * 4 : 0);  // injection map, FP32 composite vectors
   }
   const size_t nc = static_cast<size_t>(g.levels[o.coarsest_level].n_dofs);
   return bytes + nc * nc * 8 + g.levels[o.coarsest_level].n_slots * 4 + nc * 4;
@@ -438,7 +525,7 @@ constexpr int64_t kSweepTargetCtas = 4 * 152;  // spread small levels over the S
 template <typename T>
 static SweepArgs<T> sweep_args(const Hier& H, int l, const T* u, const T* b, T* out, int* amode) {
   const DevLevel& D = H.lv[l];
-  const bool coarse = l < H.L && H.galerkin;
+  const bool coarse = l < H.top && H.galerkin;
   SweepArgs<T> a{};
   a.L = D.d;
   a.u = u;
@@ -491,7 +578,7 @@ static void transfer(const Hier& H, int fine, bool restrict_op, const T* in, T* 
   int pmode = 0;
   const void* ph = nullptr;
   const float* ps = nullptr;
-  if (H.boxmg) {
+  if (H.boxmg && fine <= H.top) {
     if constexpr (std::is_same<T, double>::value) {
       pmode = 1;
       ph = C.phat;
@@ -582,10 +669,10 @@ static mg_status run_setup(Hier& H, const double* eps_in, cudaStream_t s, bool c
   }
   MG_CHECK(last_launch("setup: coefficients"));
   MG_TRY_CUDA(cudaMemsetAsync(H.d_status, 0, sizeof(int), s));
-  for (int l = H.L; l > H.c; --l) {
+  for (int l = H.top; l > H.c; --l) {  // BoxMG / Galerkin on the complete levels
     DevLevel& F = H.lv[l];
     DevLevel& C = H.lv[l - 1];
-    const double* ahat_f = (l < H.L && H.galerkin) ? F.ahat : nullptr;
+    const double* ahat_f = (l < H.top && H.galerkin) ? F.ahat : nullptr;
     const unsigned gb = static_cast<unsigned>((C.d.n_slots + 127) / 128);
     if (H.boxmg) {
       const unsigned gp = static_cast<unsigned>(((C.d.n_slots << d) + 63) / 64);
@@ -613,7 +700,7 @@ static mg_status run_setup(Hier& H, const double* eps_in, cudaStream_t s, bool c
   // diagonal audit of every level (Sect. 4.3 definiteness check) and coarsest factor
   for (int l = H.c; l <= H.L; ++l) {
     DevLevel& D = H.lv[l];
-    const double* ah = (l < H.L && H.galerkin) ? D.ahat : nullptr;
+    const double* ah = (l < H.top && H.galerkin) ? D.ahat : nullptr;
     if (d == 2)
       k_export_stencils<2><<<nblk(D.d.n_slots), kBlock, 0, s>>>(D.d, D.eps, ah, nullptr, H.d_status);
     else
@@ -621,7 +708,7 @@ static mg_status run_setup(Hier& H, const double* eps_in, cudaStream_t s, bool c
   }
   {
     DevLevel& C = H.lv[H.c];
-    const double* ah = (H.c < H.L && H.galerkin) ? C.ahat : nullptr;
+    const double* ah = (H.c < H.top && H.galerkin) ? C.ahat : nullptr;
     if (d == 2)
       k_coarse_assemble<2><<<nblk(H.n_c), kBlock, 0, s>>>(C.d, C.eps, ah, H.c_slots, H.c_map, H.n_c, H.c_mat);
     else
@@ -634,7 +721,7 @@ static mg_status run_setup(Hier& H, const double* eps_in, cudaStream_t s, bool c
     for (int l = H.c; l <= H.L; ++l) {
       DevLevel& D = H.lv[l];
       k_to_f32<<<nblk(D.d.n_slots), kBlock, 0, s>>>(D.d.n_slots, D.eps, D.eps32);
-      if (l < H.L) {
+      if (l < H.top) {
         if (H.galerkin) {
           if (H.fmt == 1)
             k_encode_planes<1><<<nblk(D.d.n_slots), kBlock, 0, s>>>(D.d, n3, D.ahat, D.a16, D.ascale);
@@ -847,6 +934,223 @@ static mg_status solve_mixed(Hier& H, double* u, const double* b, double tol, in
   return MG_OK;
 }
 
+// ---- composite grid (Sect. 3): level L refined in part over the complete level t = L - 1
+
+template <typename T>
+static void fill_hanging(const Hier& H, const T* ut, T* uL, cudaStream_t s) {
+  const DevLevel& F = H.lv[H.L];
+  if (H.dim == 2)
+    k_hanging<2, T><<<nblk(F.d.n_slots), kBlock, 0, s>>>(F.d, F.hang_idx, F.hang_w, ut, uL);
+  else
+    k_hanging<3, T><<<nblk(F.d.n_slots), kBlock, 0, s>>>(F.d, F.hang_idx, F.hang_w, ut, uL);
+}
+
+template <typename T>
+static void inject(const Hier& H, const T* uL, T* ut, cudaStream_t s) {
+  const DevLevel& D = H.lv[H.top];
+  k_inject<T><<<nblk(D.d.n_slots), kBlock, 0, s>>>(D.d, H.child_top, uL, ut);
+}
+
+static inline unsigned norm_blocks(const DevLevel& D) {
+  const int64_t cap = D.d.n_bricks * D.d.B;  // entries of D.partial
+  return static_cast<unsigned>(std::max<int64_t>(1, std::min<int64_t>(nblk(D.d.n_slots), cap)));
+}
+
+// composite residual: r_L = b_L - A_L u_L on level-L DoFs (norm^2 into d_scal[sL]);
+// u_t refreshed by injection, r_t = b_t - A_t u_t on unrefined level-t DoFs (zero
+// elsewhere, norm^2 into d_scal[st]).  Hanging entries of u_L must be current.
+template <typename T>
+static void comp_residual_norm(Hier& H, const T* uL, const T* bL, T* ut, const T* bt, int sL, int st,
+                               cudaStream_t s) {
+  DevLevel& D = H.lv[H.top];
+  T* rt = lvec<T>(H, H.top, 2);
+  sweep<T>(H, H.L, kResidual, uL, bL, lvec<T>(H, H.L, 2), H.d_scal + sL, s);
+  inject<T>(H, uL, ut, s);
+  sweep<T>(H, H.top, kResidual, ut, bt, rt, nullptr, s);
+  k_masked_norm<T><<<norm_blocks(D), kBlock, 0, s>>>(D.d, rt, D.partial, D.counter, H.d_scal + st);
+}
+
+// One composite cycle (FAS two-level scheme on the hierarchical generating system,
+// Sect. 3 with Alg. 1's smoother): pre-smooth level L with hanging values from
+// level t, inject, form the level-t correction equation (R r_L at refined, the
+// level-t residual at unrefined vertices), one V-cycle of the uniform levels
+// t .. c for it, correct u_t (unrefined) and u_L (d-linear P), refresh the
+// hanging values, post-smooth.  Expects hanging entries of u_L current on entry.
+template <typename T>
+static void composite_cycle(Hier& H, T* uL, const T* bL, T* ut, const T* bt, cudaStream_t s) {
+  const int L = H.L, t = H.top;
+  T* tmpL = lvec<T>(H, L, 3);
+  T* rL = lvec<T>(H, L, 2);
+  T* et = lvec<T>(H, t, 0);
+  T* rhs = lvec<T>(H, t, 1);
+  T* rt = lvec<T>(H, t, 2);
+  const DevLevel& D = H.lv[t];
+  smooth<T>(H, L, uL, bL, tmpL, H.opt.nu1, s);
+  sweep<T>(H, L, kResidual, uL, bL, rL, nullptr, s);
+  inject<T>(H, uL, ut, s);
+  sweep<T>(H, t, kResidual, ut, bt, rt, nullptr, s);
+  transfer<T>(H, L, true, rL, rhs, s);  // d-linear R = P^T (no operator-dependent transfer on level L)
+  k_compose_rhs<T><<<nblk(D.d.n_slots), kBlock, 0, s>>>(D.d, rt, rhs);
+  cudaMemsetAsync(et, 0, D.d.n_slots * sizeof(T), s);
+  vcycle<T>(H, t, et, rhs, s);
+  k_add_unrefined<T><<<nblk(D.d.n_slots), kBlock, 0, s>>>(D.d, et, ut);
+  transfer<T>(H, L, false, et, uL, s);
+  fill_hanging<T>(H, ut, uL, s);
+  smooth<T>(H, L, uL, bL, tmpL, H.opt.nu2, s);
+}
+
+struct CompVecs {
+  double *uL, *ut;
+  const double *bL, *bt;
+};
+
+static CompVecs comp_vecs(const Hier& H, double* u, const double* b) {
+  const Grid& g = *H.g;
+  const int64_t oL = g.levels[H.L].slot_offset, ot = g.levels[H.top].slot_offset;
+  return CompVecs{u + oL, u + ot, b + oL, b + ot};
+}
+
+static mg_status solve_comp_fp64(Hier& H, double* u, const double* b, double tol, int max_cycles,
+                                 mg_solve_stats* st, cudaStream_t s) {
+  const CompVecs v = comp_vecs(H, u, b);
+  MG_TRY_CUDA(cudaMemsetAsync(v.uL, 0, H.lv[H.L].d.n_slots * sizeof(double), s));
+  MG_TRY_CUDA(cudaMemsetAsync(v.ut, 0, H.lv[H.top].d.n_slots * sizeof(double), s));
+  comp_residual_norm<double>(H, v.uL, v.bL, v.ut, v.bt, 0, 4, s);
+  MG_TRY_CUDA(cudaMemcpyAsync(H.h_pin, H.d_scal, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  MG_TRY_CUDA(cudaStreamSynchronize(s));
+  const double r0 = std::sqrt(H.h_pin[0] + H.h_pin[4]);
+  if (st) {
+    st->r0_norm = r0;
+    st->history_len = 0;
+  }
+  if (!std::isfinite(r0)) {
+    set_error("mg_solve: non-finite initial residual");
+    return MG_ERR_NONFINITE;
+  }
+  double rel = r0 > 0 ? 1.0 : 0.0;
+  int cycles = 0;
+  while (rel > tol && cycles < max_cycles) {
+    MG_CHECK(graph_launch(H, H.g_comp64, u, b, s, [&](cudaStream_t ss) {
+      composite_cycle<double>(H, v.uL, v.bL, v.ut, v.bt, ss);
+      comp_residual_norm<double>(H, v.uL, v.bL, v.ut, v.bt, 0, 4, ss);
+      cudaMemcpyAsync(H.h_pin, H.d_scal, 8 * sizeof(double), cudaMemcpyDeviceToHost, ss);
+    }));
+    MG_TRY_CUDA(cudaStreamSynchronize(s));
+    ++cycles;
+    rel = std::sqrt(H.h_pin[0] + H.h_pin[4]) / r0;
+    if (st && st->history && st->history_len < st->history_capacity) st->history[st->history_len++] = rel;
+    if (!std::isfinite(rel)) {
+      set_error("mg_solve: non-finite residual");
+      if (st) st->cycles = cycles;
+      return MG_ERR_NONFINITE;
+    }
+    if (rel > 1e6) {
+      set_error("mg_solve: residual grew by more than 1e6 (diverged)");
+      if (st) st->cycles = cycles;
+      return MG_ERR_DIVERGED;
+    }
+  }
+  if (st) {
+    st->cycles = cycles;
+    st->outer_steps = cycles;
+    st->rel_residual = rel;
+  }
+  if (rel > tol) {
+    set_error("mg_solve: not converged within max_cycles");
+    return MG_ERR_NOT_CONVERGED;
+  }
+  return MG_OK;
+}
+
+// FP64 iterative refinement around FP32 composite cycles: the composite residual
+// (r_L, r_t) in FP64, scaled by sigma = sqrt(|r|^2 / n) into the FP32 correction
+// equation, solved from zero by FP32 composite cycles, then u += sigma e on both levels
+static mg_status solve_comp_mixed(Hier& H, double* u, const double* b, double tol, int max_cycles,
+                                  mg_solve_stats* st, cudaStream_t s) {
+  const CompVecs v = comp_vecs(H, u, b);
+  DevLevel& F = H.lv[H.L];
+  DevLevel& D = H.lv[H.top];
+  const int64_t nL = F.d.n_slots, nt = D.d.n_slots;
+  const double inv_count = H.n_comp_dofs > 0 ? 1.0 / static_cast<double>(H.n_comp_dofs) : 0.0;
+  MG_TRY_CUDA(cudaMemsetAsync(v.uL, 0, nL * sizeof(double), s));
+  MG_TRY_CUDA(cudaMemsetAsync(v.ut, 0, nt * sizeof(double), s));
+  MG_TRY_CUDA(cudaMemsetAsync(F.u32, 0, nL * sizeof(float), s));
+  MG_TRY_CUDA(cudaMemsetAsync(H.c32, 0, nt * sizeof(float), s));
+  MG_TRY_CUDA(cudaMemsetAsync(H.d_scal + 2, 0, sizeof(double), s));
+  comp_residual_norm<double>(H, v.uL, v.bL, v.ut, v.bt, 0, 4, s);
+  MG_TRY_CUDA(cudaMemcpyAsync(H.h_pin, H.d_scal, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  MG_TRY_CUDA(cudaStreamSynchronize(s));
+  const double r0 = std::sqrt(H.h_pin[0] + H.h_pin[4]);
+  if (st) {
+    st->r0_norm = r0;
+    st->history_len = 0;
+  }
+  if (!std::isfinite(r0)) {
+    set_error("mg_solve: non-finite initial residual");
+    return MG_ERR_NONFINITE;
+  }
+  double rel = r0 > 0 ? 1.0 : 0.0;
+  int cycles = 0, outer = 0;
+  const int chunk = H.opt.inner_cycles > 0 ? H.opt.inner_cycles : 8;
+  bool first = true;
+  while (rel > tol && cycles < max_cycles) {
+    MG_CHECK(graph_launch(H, H.g_comp_outer, u, b, s, [&](cudaStream_t ss) {
+      k_update_f64<<<nblk(nL), kBlock, 0, ss>>>(nL, v.uL, F.u32, H.d_scal + 2);
+      k_update_f64<<<nblk(nt), kBlock, 0, ss>>>(nt, v.ut, H.c32, H.d_scal + 2);
+      fill_hanging<double>(H, v.ut, v.uL, ss);
+      comp_residual_norm<double>(H, v.uL, v.bL, v.ut, v.bt, 0, 4, ss);
+      k_sum2<<<1, 1, 0, ss>>>(H.d_scal, H.d_scal + 4, H.d_scal + 6);
+      k_scale_to_f32<<<nblk(nL), kBlock, 0, ss>>>(nL, F.r, H.d_scal + 6, inv_count, F.b32, H.d_scal + 2);
+      k_scale_to_f32<<<nblk(nt), kBlock, 0, ss>>>(nt, D.r, H.d_scal + 6, inv_count, H.cb32, H.d_scal + 2);
+      cudaMemsetAsync(F.u32, 0, nL * sizeof(float), ss);
+      cudaMemsetAsync(H.c32, 0, nt * sizeof(float), ss);
+      cudaMemcpyAsync(H.h_pin, H.d_scal, 8 * sizeof(double), cudaMemcpyDeviceToHost, ss);
+    }));
+    MG_TRY_CUDA(cudaStreamSynchronize(s));
+    ++outer;
+    rel = std::sqrt(H.h_pin[6]) / r0;
+    if (!first && st && st->history && st->history_len < st->history_capacity) st->history[st->history_len++] = rel;
+    first = false;
+    if (!std::isfinite(rel)) {
+      set_error("mg_solve: non-finite residual");
+      return MG_ERR_NONFINITE;
+    }
+    if (rel > 1e6) {
+      set_error("mg_solve: residual grew by more than 1e6 (diverged)");
+      return MG_ERR_DIVERGED;
+    }
+    if (rel <= tol) break;
+    const double target = std::max(1e-5, 0.3 * tol / rel);
+    double prev = 1.0;
+    while (cycles < max_cycles) {
+      MG_CHECK(graph_launch(H, H.g_comp_inner, nullptr, nullptr, s, [&](cudaStream_t ss) {
+        for (int k = 0; k < chunk; ++k) composite_cycle<float>(H, F.u32, F.b32, H.c32, H.cb32, ss);
+        comp_residual_norm<float>(H, F.u32, F.b32, H.c32, H.cb32, 1, 5, ss);
+        cudaMemcpyAsync(H.h_pin, H.d_scal, 8 * sizeof(double), cudaMemcpyDeviceToHost, ss);
+      }));
+      MG_TRY_CUDA(cudaStreamSynchronize(s));
+      cycles += chunk;
+      const double inner = std::sqrt((H.h_pin[1] + H.h_pin[5]) * inv_count);
+      if (!std::isfinite(inner)) {
+        set_error("mg_solve: non-finite FP32 inner residual");
+        return MG_ERR_NONFINITE;
+      }
+      if (inner <= target || inner > 0.9 * prev) break;
+      prev = inner;
+    }
+  }
+  if (st) {
+    st->cycles = cycles;
+    st->outer_steps = outer;
+    st->rel_residual = rel;
+  }
+  if (rel > tol) {
+    set_error("mg_solve: not converged within max_cycles");
+    return MG_ERR_NOT_CONVERGED;
+  }
+  return MG_OK;
+}
+
 // ---- persistent cooperative solve -------------------------------------------------
 
 template <typename T>
@@ -854,7 +1158,7 @@ static PLevel<T> make_plevel(const Hier& H, int l, T* u_fin, const T* b_fin) {
   const DevLevel& D = H.lv[l];
   PLevel<T> P{};
   P.d = D.d;
-  const bool coarse = l < H.L;
+  const bool coarse = l < H.top;
   if constexpr (std::is_same<T, double>::value) {
     P.eps = D.eps;
     P.ahat = (coarse && H.galerkin) ? D.ahat : nullptr;
@@ -1046,8 +1350,18 @@ mg_status mg_hier_create(const mg_grid* grid, const mg_options* opt, mg_hier** o
     return MG_ERR_INVALID_ARG;
   }
   if (!g->uniform) {
-    set_error("mg_hier_create: adaptive grids are not supported by this hierarchy yet");
-    return MG_ERR_UNSUPPORTED;
+    // composite solve: levels 0 .. L - 2 present and refined everywhere, so level
+    // L - 1 is complete and only its refinement towards level L is partial
+    for (int l = 0; l + 1 < g->L; ++l)
+      for (size_t c = 0; c < g->cells[l].size(); ++c)
+        if (!g->cells[l][c] || !g->refined[l][c]) {
+          set_error("mg_hier_create: adaptive grids must be complete up to level max_level - 1");
+          return MG_ERR_UNSUPPORTED;
+        }
+    if (o.coarsest_level >= g->L - 1) {
+      set_error("mg_hier_create: the coarsest level must lie below the finest complete level");
+      return MG_ERR_INVALID_ARG;
+    }
   }
   try {
     Hier* H = nullptr;
@@ -1166,6 +1480,10 @@ mg_status mg_vcycle_f32(mg_hier* h, float* u, const float* b, void* stream) {
     set_error("mg_vcycle_f32: NULL vector");
     return MG_ERR_INVALID_ARG;
   }
+  if (H->adaptive) {
+    set_error("mg_vcycle_f32: adaptive hierarchies run FP32 composite cycles inside mg_solve only");
+    return MG_ERR_UNSUPPORTED;
+  }
   vcycle<float>(*H, H->L, u, b, pick(*H, stream));
   return last_launch("mg_vcycle_f32");
 }
@@ -1215,7 +1533,15 @@ mg_status mg_vcycle(mg_hier* h, double* u, const double* b, void* stream) {
     set_error("mg_vcycle: NULL vector");
     return MG_ERR_INVALID_ARG;
   }
-  vcycle<double>(*H, H->L, u, b, pick(*H, stream));
+  cudaStream_t s = pick(*H, stream);
+  if (H->adaptive) {  // one composite cycle on the level-concatenated vectors
+    const CompVecs v = comp_vecs(*H, u, b);
+    fill_hanging<double>(*H, v.ut, v.uL, s);
+    composite_cycle<double>(*H, v.uL, v.bL, v.ut, v.bt, s);
+    inject<double>(*H, v.uL, v.ut, s);
+  } else {
+    vcycle<double>(*H, H->L, u, b, s);
+  }
   return last_launch("mg_vcycle");
 }
 
@@ -1229,10 +1555,12 @@ mg_status mg_solve(mg_hier* h, double* u, const double* b, double rel_tol, int m
   }
   cudaStream_t s = pick(*H, stream);
   const auto t0 = std::chrono::steady_clock::now();
-  const bool persistent = H->opt.persistent && H->n_c <= 64 && H->L < kMaxLevels;
-  const mg_status st = persistent ? solve_persistent(*H, u, b, rel_tol, max_cycles, stats, s)
-                       : H->mixed ? solve_mixed(*H, u, b, rel_tol, max_cycles, stats, s)
-                                  : solve_fp64(*H, u, b, rel_tol, max_cycles, stats, s);
+  const bool persistent = H->opt.persistent && !H->adaptive && H->n_c <= 64 && H->L < kMaxLevels;
+  const mg_status st = H->adaptive ? (H->mixed ? solve_comp_mixed(*H, u, b, rel_tol, max_cycles, stats, s)
+                                                 : solve_comp_fp64(*H, u, b, rel_tol, max_cycles, stats, s))
+                       : persistent ? solve_persistent(*H, u, b, rel_tol, max_cycles, stats, s)
+                       : H->mixed   ? solve_mixed(*H, u, b, rel_tol, max_cycles, stats, s)
+                                    : solve_fp64(*H, u, b, rel_tol, max_cycles, stats, s);
   if (stats)
     stats->solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   return st;
@@ -1246,7 +1574,7 @@ mg_status mg_get_stencils(mg_hier* h, int level, double* st, void* stream) {
     return MG_ERR_INVALID_ARG;
   }
   DevLevel& D = H->lv[level];
-  const double* ah = (level < H->L && H->galerkin) ? D.ahat : nullptr;
+  const double* ah = (level < H->top && H->galerkin) ? D.ahat : nullptr;
   cudaStream_t s = pick(*H, stream);
   if (H->dim == 2)
     k_export_stencils<2><<<nblk(D.d.n_slots), kBlock, 0, s>>>(D.d, D.eps, ah, st, nullptr);
@@ -1270,8 +1598,8 @@ __global__ void k_planes16_to_offset_major(mg::LevelDesc L, int K, const uint16_
 mg_status mg_get_deltas(mg_hier* h, int level, double* a_hat, double* p_hat, void* stream) {
   Hier* H = H_(h);
   MG_CHECK(check_level(H, level, true));
-  if (level >= H->L) {
-    set_error("mg_get_deltas: the finest level stores no deltas");
+  if (level >= H->top) {
+    set_error("mg_get_deltas: the finest complete level and above store no deltas");
     return MG_ERR_INVALID_ARG;
   }
   DevLevel& D = H->lv[level];
@@ -1297,7 +1625,7 @@ mg_status mg_get_codes(mg_hier* h, int level, uint16_t* a_codes, float* a_scale,
                        void* stream) {
   Hier* H = H_(h);
   MG_CHECK(check_level(H, level, true));
-  if (!H->mixed || level >= H->L) {
+  if (!H->mixed || level >= H->top) {
     set_error("mg_get_codes: no codes (FP64 hierarchy or finest level)");
     return MG_ERR_INVALID_ARG;
   }

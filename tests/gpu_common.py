@@ -129,3 +129,19 @@ def rowwise_rel(a, b):
     den = np.abs(b).max(axis=1)
     den = np.where(den > 0, den, 1.0)
     return (np.abs(a - b).max(axis=1) / den).max()
+
+
+def galerkin_amplification(O, tree, L, dim):
+    """Case.amplification for an oracle hierarchy O over `tree` with finest level L."""
+    from oracle import fem
+
+    S = {L: abs(O.ops[L].A)}
+    amp = 1.0
+    c = 3**dim // 2
+    for lv in range(L - 1, 0, -1):
+        S[lv] = (abs(O.ops[lv + 1].P).T @ S[lv + 1] @ abs(O.ops[lv + 1].P)).tocsr() if O.coarse == "galerkin" \
+            else abs(O.ops[lv].A)
+        st = fem.stencils(tree, lv, S[lv])
+        dof = tree.levels[lv].dof
+        amp = max(amp, float((st[dof, c] / np.abs(O.ops[lv].st[dof, c])).max()))
+    return amp

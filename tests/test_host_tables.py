@@ -96,3 +96,18 @@ def test_invalid_arguments_are_rejected(mg):
     g = mg.Grid(2, 2)
     with pytest.raises(mg.MgError):
         g.info(5)
+
+
+def test_adaptive_hierarchy_shape_is_checked_before_any_device_work(mg):
+    # the composite hierarchy needs levels 0 .. L-2 refined everywhere; both checks
+    # come before any allocation, so they run without a GPU
+    m1 = np.zeros((3, 3), bool)
+    m1[1, 1] = True
+    g = mg.Grid(2, 3, {1: m1})  # level 1 refined in part
+    with pytest.raises(mg.MgError) as e:
+        mg.Hierarchy(g)
+    assert e.value.status == 10  # MG_ERR_UNSUPPORTED
+    g2 = mg.Grid(2, 3, {2: syn.sphere_shell_mask(2, 2)})
+    with pytest.raises(mg.MgError) as e:
+        mg.Hierarchy(g2, coarsest_level=2)  # the coarsest level must lie below level L-1
+    assert e.value.status == 1  # MG_ERR_INVALID_ARG
