@@ -30,7 +30,10 @@ from .spacetree import HANGING, REFINED, Spacetree
 
 class Composite:
     def __init__(self, tree: Spacetree, leaf_eps: dict[int, np.ndarray], transfer: str = "boxmg",
-                 coarse: str = "galerkin", omega: float = 0.6, nu1: int = 2, nu2: int = 2, coarsest: int = 1):
+                 coarse: str = "galerkin", omega: float = 0.6, nu1: int = 2, nu2: int = 2, coarsest: int = 1,
+                 cycle: bool = True):
+        """cycle=False builds the composite system only (fill, residual, matrix), not
+        the transfer and the uniform sub-hierarchy that the cycle needs."""
         L = tree.max_level
         T = L - 1
         self.tree, self.L, self.T = tree, L, T
@@ -58,12 +61,14 @@ class Composite:
         child = tree.child_map(T)
         ref = np.nonzero(self.ref4)[0]
         self.Inj = sp.csr_matrix((np.ones(len(ref)), (ref, child[ref])), shape=(top.n_slots, fine.n_slots))
+        self.diag5 = np.where(self.dof5, self.A5.diagonal(), 1.0)
+        if not cycle:
+            return
         # d-linear transfer between the levels (the adaptive level has no BoxMG operator)
         self.P = prolongation(tree, L, None, "dlinear")
         # the uniform levels T .. coarsest as their own hierarchy
         self.sub = multigrid.Hierarchy(Spacetree(d, T), {T: self.eps[T]}, transfer=transfer, coarse=coarse,
                                        omega=omega, nu1=nu1, nu2=nu2, coarsest=coarsest)
-        self.diag5 = np.where(self.dof5, self.A5.diagonal(), 1.0)
 
     # --- the composite state: u5 (level-L slots), u4 (level-T slots) ---------------
     def fill(self, u5, u4):

@@ -158,3 +158,46 @@ def test_adaptive_entry_points_reject_what_they_do_not_cover(comp):
     u = torch.zeros(comp.nL, dtype=torch.float32, device="cuda")
     with pytest.raises(RuntimeError):
         comp.H.vcycle_f32(u, u)
+
+
+def test_full_size_sphere3d_l5_solves_reach_the_oracle_residual():
+    # the adaptive 3D workload at full size: uniform to level 4 (81^3 cells) and level 5
+    # in the shell around r = 0.3 (1,287,488 composite unknowns).  The oracle's composite
+    # system (no cycle) evaluates the residual of the GPU solutions: both the FP64 and
+    # the mixed BF16 solve must reach the 1e-10 drop in the oracle's arithmetic.
+    import torch
+
+    mg = lib()
+    dim, L, T = 3, 5, 4
+    mask = syn.sphere_shell_mask(T, dim, radius=0.3)
+    eps = {L: syn.sphere_eps(L, dim), T: syn.sphere_eps(T, dim)}
+    tree = stt.Spacetree(dim, L, {T: mask})
+    C = composite.Composite(tree, eps, cycle=False)
+    b5 = tree.vertices_to_slots(L, syn.uniform_load(L, dim, 2))
+    b4 = np.where(C.unref4, tree.vertices_to_slots(T, syn.uniform_load(T, dim, 3)), 0.0)
+    assert C.dof5.sum() + C.unref4.sum() == 1287488
+    grid = mg.Grid(dim, L, {T: mask})
+    iL, iT = grid.info(L), grid.info(T)
+    cat = np.zeros(grid.n_slots_total())
+    cat[iL.slot_offset: iL.slot_offset + iL.n_slots] = b5
+    cat[iT.slot_offset: iT.slot_offset + iT.n_slots] = b4
+    bd = torch.from_numpy(cat).cuda()
+    eps_dev = torch.from_numpy(grid.cells_to_concat(eps)).cuda()
+    r0 = np.sqrt(b5[C.dof5] @ b5[C.dof5] + b4[C.unref4] @ b4[C.unref4])
+    for precision in ("fp64", "mixed_bf16"):
+        H = mg.Hierarchy(grid, precision=precision)
+        H.setup(eps_dev)
+        ud = torch.zeros_like(bd)
+        res = H.solve(ud, bd, rel_tol=1e-10, max_cycles=3000)
+        a = ud.cpu().numpy()
+        u5 = np.where(C.dof5, a[iL.slot_offset: iL.slot_offset + iL.n_slots], 0.0)
+        u4 = np.where(C.unref4, a[iT.slot_offset: iT.slot_offset + iT.n_slots], 0.0)
+        r5, r4 = C.residual(u5, u4, b5, b4)
+        # two FP64 evaluations of b - A u differ by at most (terms) u sum|terms| per row (Higham)
+        f5, f4 = C.fill(u5, u4)
+        n5 = np.where(C.dof5, np.abs(b5) + abs(C.A5) @ np.abs(f5), 0.0)
+        n4 = np.where(C.unref4, np.abs(b4) + abs(C.A4) @ np.abs(f4), 0.0)
+        noise = 64 * 2.0**-53 * np.sqrt(n5 @ n5 + n4 @ n4)
+        assert res["rel_residual"] <= 1e-10
+        assert np.sqrt(r5 @ r5 + r4 @ r4) <= 1e-10 * r0 + noise, precision
+        del H
