@@ -150,7 +150,7 @@ def kernel_count_adaptive(L, c, nu1, nu2, precision, cycles, outer, chunk):
     """Kernels of ours launched by one mg_setup + composite mg_solve (memsets / copies excluded)."""
     t = L - 1
     vc = (t - c) * (nu1 + nu2 + 3) + 1  # the V-cycle of the uniform levels t .. c
-    cyc = nu1 + nu2 + 8 + vc  # sweeps, residuals L and t, inject, restrict, compose, add, prolong, hanging
+    cyc = nu1 + nu2 + 8 + vc  # sweeps, residuals L and t, inject, compose, restrict, add, prolong, hanging
     res = 4  # residual L, inject, residual t, masked norm
     setup = (L - c + 1) + (L - c) + 2 * (t - c) + (L - c + 1) + 2
     if precision == "fp64":
@@ -438,15 +438,16 @@ def run_ours(args):
 
 
 def run_sweeps(args):
-    """Finest-level in-situ Jacobi sweeps alone on a 2D checkerboard grid of level
-    args.sweep_level (level 8: 6561^2 cells, 43M DoFs, vectors far larger than L2):
-    per-launch time of the FP64 and the FP32 sweep kernels and their roofline."""
+    """Finest-level in-situ Jacobi sweeps alone on a uniform checkerboard grid of level
+    args.sweep_level and dimension args.sweep_dim (2D level 8: 6561^2 cells, 43M DoFs;
+    3D level 5: 243^3 cells, 14M DoFs; vectors larger than L2): per-launch time of the
+    FP64 and the FP32 sweep kernels and their roofline."""
     import torch
 
     import paper_1607_00648_gb300 as mg
 
     torch.cuda.set_device(0)
-    L, d = args.sweep_level, 2
+    L, d = args.sweep_level, args.sweep_dim
     eps = syn.checkerboard_eps(L, d, seed=0)
     grid = mg.Grid(d, L)
     n_dofs = grid.info(L).n_dofs
@@ -458,9 +459,11 @@ def run_sweeps(args):
     b32 = b64.float()
     u32 = torch.zeros_like(b32)
     hbm, src = peaks()
-    out = {"workload": f"sweep2d-l{L}", "dofs": n_dofs}
+    out = {"workload": f"sweep{d}d-l{L}", "dofs": n_dofs}
     for name, fn, u, bb, bpd in (("fp64", H.smooth, u64, b64, BYTES_PER_DOF_SWEEP_FP64),
                                  ("fp32", H.smooth_f32, u32, b32, BYTES_PER_DOF_SWEEP_FP32)):
+        if args.sweep_prec not in ("both", name):
+            continue
         for _ in range(3):
             fn(L, u, bb, 2)
         torch.cuda.synchronize()
@@ -683,7 +686,9 @@ def main():
     ap.add_argument("--serve-budget-gb", type=float, default=64.0)
     ap.add_argument("--batch-size", type=int, default=0)
     ap.add_argument("--sweep-level", type=int, default=0,
-                    help="time only the finest-level FP64 / FP32 sweeps on a 2D grid of this level")
+                    help="time only the finest-level FP64 / FP32 sweeps on a uniform grid of this level")
+    ap.add_argument("--sweep-dim", type=int, default=2, choices=(2, 3))
+    ap.add_argument("--sweep-prec", default="both", choices=("both", "fp64", "fp32"))
     args = ap.parse_args()
     if args.serve:
         run_serve(args)

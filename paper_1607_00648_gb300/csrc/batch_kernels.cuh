@@ -122,11 +122,9 @@ void blaunch_transfer(const BatchArgs<T>& ba, const BatchGroup& g, bool restrict
 template <int DIM, typename T, int B>
 static void bsweep_b(const BatchArgs<T>& ba, const BatchGroup& g, int op, int amc, int src, int dst, cudaStream_t s) {
   constexpr int VOL = DIM == 2 ? B * B : B * B * B;
-  constexpr int UPL = DIM == 2 ? B + 2 : (B + 2) * (B + 2);
-  constexpr int EPL = DIM == 2 ? B + 1 : (B + 1) * (B + 1);
   int threads = ((VOL + 31) / 32) * 32;
   if (threads > kBlock) threads = kBlock;
-  const size_t smem = (static_cast<size_t>(UPL) * (B + 2) + static_cast<size_t>(EPL) * (B + 1)) * sizeof(T);
+  const size_t smem = sweep_tile_bytes<DIM, T>(B, B);
   const unsigned grid = static_cast<unsigned>(g.count);
 #define MG_BS(AM, OP) k_bsweep<DIM, T, AM, OP, B><<<grid, threads, smem, s>>>(ba, g.items, g.part_off, src, dst)
 #define MG_BS_OPS(AM)                          \

@@ -57,6 +57,9 @@ struct Hier {
   float* c32 = nullptr;   // mixed composite solve: FP32 level-top correction and its right-hand side
   float* cb32 = nullptr;
   int64_t n_comp_dofs = 0;  // composite unknowns: level-L DoFs + unrefined level-(L-1) DoFs
+  // composite slot lists: refined level-top DoFs, level-L DoFs, level-L hanging vertices
+  int32_t *ref_top = nullptr, *dof_L = nullptr, *hang_L = nullptr;
+  int64_t n_ref_top = 0, n_dof_L = 0, n_hang_L = 0;
   bool galerkin = false, boxmg = false, mixed = false;
   int fmt = 1;  // 1 bf16, 2 fp16
   std::vector<DevLevel> lv;

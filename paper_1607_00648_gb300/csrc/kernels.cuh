@@ -196,6 +196,20 @@ __device__ __forceinline__ double sweep_item(const SweepArgs<T>& a, int64_t bric
     se[t] = nb >= 0 ? a.eps[static_cast<int64_t>(nb) * L.S + li] : T(0);
   }
   __syncthreads();
+  // 3D: per cell of the tile q_c = eps_c * (sum of its 8 corner values), shared by
+  // the 8 vertices of the cell (see the vertex formula below)
+  T* sq = se + EPL * (R + 1);
+  if constexpr (DIM == 3) {
+    for (int t = threadIdx.x; t < ne; t += nt) {
+      const int cx = t % Be, cy = (t / Be) % Be, cz = t / EPL;  // tile position of the cell's lower corner
+      const T* c0 = su + (cz * Bu + cy) * Bu + cx;
+      const T s4a = (c0[0] + c0[1]) + (c0[Bu] + c0[Bu + 1]);
+      const T s4b = (c0[UPL] + c0[UPL + 1]) + (c0[UPL + Bu] + c0[UPL + Bu + 1]);
+      const T ev = se[t];
+      sq[t] = ev != T(0) ? ev * (s4a + s4b) : T(0);  // absent cells (eps 0) cost no arithmetic
+    }
+    __syncthreads();
+  }
 
   const T hscale = DIM == 3 ? static_cast<T>(L.h) : T(1);
   double part = 0.0;
@@ -235,51 +249,33 @@ __device__ __forceinline__ double sweep_item(const SweepArgs<T>& a, int64_t bric
         D = k0 * sC;
         Au = fma(D, uc[0], fma(k1, a1, k2 * a2));
       } else {
-        T acc[DIM + 1];
-#pragma unroll
-        for (int c = 0; c <= DIM; ++c) acc[c] = T(0);
-        T es_centre = T(0);
-#pragma unroll
-        for (int k = 0; k < N3; ++k) {
-          int o[DIM];
-          int ham = 0, kk = k;
-#pragma unroll
-          for (int q = 0; q < DIM; ++q) {
-            o[q] = kk % 3 - 1;
-            kk /= 3;
-            ham += o[q] != 0;
-          }
-          if (elem_k(DIM, ham) == 0.0) continue;
-          T es = T(0);
-#pragma unroll
-          for (int e = 0; e < (1 << DIM); ++e) {
-            bool ok = true;
-            int cidx = ce, m = 1;
-#pragma unroll
-            for (int q = 0; q < DIM; ++q) {
-              const int eq = (e >> q) & 1;
-              const int tq = eq + o[q];
-              ok = ok && tq >= 0 && tq <= 1;
-              cidx -= eq * m;
-              m *= Be;
-            }
-            if (ok) es += se[cidx];
-          }
-          int uidx = cu, m = 1;
-#pragma unroll
-          for (int q = 0; q < DIM; ++q) {
-            uidx += o[q] * m;
-            m *= Bu;
-          }
-          acc[ham] = fma(es, su[uidx], acc[ham]);
-          if (ham == 0) es_centre = es;
-        }
-        Au = T(0);
-#pragma unroll
-        for (int c = 0; c <= DIM; ++c)
-          if (elem_k(DIM, c) != 0.0) Au = fma(static_cast<T>(elem_k(DIM, c)), acc[c], Au);
-        Au *= hscale;
-        D = static_cast<T>(elem_k(DIM, 0)) * es_centre * hscale;
+        // trilinear element matrix eps h {1/3, 0, -1/12, -1/12} by Hamming distance:
+        // within one cell c, (K u)_v = (5/12) u_v - S_c / 12 + E_c(v) / 12 with S_c the
+        // sum of the cell's corner values and E_c(v) that of v's three edge neighbours
+        // in c; summed over the 8 cells around v:
+        //   (A u)_v = h/12 (5 sC u_v - sum_c eps_c S_c + sum_axis nbr n  S_n u_n),
+        // S_n = sum of eps over the 4 cells that contain the edge v-n, sC = sum of eps.
+        const T* ec = se + ce;
+        const T* qc = sq + ce;
+        const T* uc = su + cu;
+        // cell e<bx><by><bz>: lower corner v - (bx, by, bz)
+        const T e000 = ec[0], e100 = ec[-1], e010 = ec[-Be], e110 = ec[-Be - 1];
+        const T e001 = ec[-EPL], e101 = ec[-EPL - 1], e011 = ec[-EPL - Be], e111 = ec[-EPL - Be - 1];
+        const T p00 = e000 + e001, p10 = e100 + e101, p01 = e010 + e011, p11 = e110 + e111;
+        const T sxp = p00 + p01, sxm = p10 + p11, syp = p00 + p10, sym = p01 + p11;
+        const T szp = (e000 + e100) + (e010 + e110), szm = (e001 + e101) + (e011 + e111);
+        const T sC = sxp + sxm;
+        const T Q = ((qc[0] + qc[-1]) + (qc[-Be] + qc[-Be - 1])) +
+                    ((qc[-EPL] + qc[-EPL - 1]) + (qc[-EPL - Be] + qc[-EPL - Be - 1]));
+        T a = sxp * uc[1];
+        a = fma(sxm, uc[-1], a);
+        a = fma(syp, uc[Bu], a);
+        a = fma(sym, uc[-Bu], a);
+        a = fma(szp, uc[UPL], a);
+        a = fma(szm, uc[-UPL], a);
+        const T acc = fma(T(5) * sC, uc[0], a - Q);
+        Au = acc * (hscale * static_cast<T>(1.0 / 12.0));
+        D = sC * (hscale * static_cast<T>(1.0 / 3.0));
       }
       if constexpr (AMODE != 0) {
 #pragma unroll
@@ -317,6 +313,29 @@ __global__ void __launch_bounds__(kBlock) k_sweep(SweepArgs<T> a) {
   if constexpr (OP == kResidual) {
     if (a.partial) store_partial_and_finish(part, a.partial, a.counter, a.norm2);
   }
+}
+
+// CTAs along x of a sweep launch (times B / R slabs along y): one brick per CTA
+template <typename T>
+inline int64_t sweep_ctas_x(int, int, T, int64_t n_bricks) {
+  return n_bricks;
+}
+
+// slab depth R (a divisor of B) of a sweep launch: enough CTAs to fill the GPU
+template <typename T>
+inline int sweep_slab(int, int B, int64_t n_bricks) {
+  int R = B;
+  while (R > 1 && n_bricks * (B / R) < 4 * 152) R /= 3;
+  return R;
+}
+
+// shared memory of one sweep item: the u tile with its halo, the cell coefficients
+// and, in 3D, the per-cell corner sums
+template <int DIM, typename T>
+inline size_t sweep_tile_bytes(int B, int R) {
+  const size_t upl = DIM == 2 ? B + 2 : (B + 2) * (B + 2);
+  const size_t epl = DIM == 2 ? B + 1 : (B + 1) * (B + 1);
+  return (upl * (R + 2) + epl * (R + 1) * (DIM == 3 ? 2 : 1)) * sizeof(T);
 }
 
 // slot of integer position x on a level with compile-time brick edge B
@@ -382,11 +401,54 @@ __device__ __forceinline__ void restrict_one(const LevelDesc& Lc, const LevelDes
   bc[cs] = acc;
 }
 
+// Restriction kernel: the 5^d taps of a coarse vertex are split over kRestrictWarps
+// warps.  Lane i of every warp serves coarse slot 32*blockIdx + i (so P_hat planes
+// and fine values are read coalesced across a warp), warp j sums taps j, j + 8, ...,
+// and the warps' partial sums are added in warp order (deterministic).  With a slot
+// list (composite grid: the refined coarse DoFs) lane i serves list[32*blockIdx + i]
+// and other coarse slots are not written.
+constexpr int kRestrictWarps = 8;
+
 template <int DIM, typename T, int PMODE, int BC, int BF>
-__global__ void __launch_bounds__(kBlock) k_restrict(LevelDesc Lc, LevelDesc Lf, const T* rf, T* bc,
-                                                       const void* phat, const float* pscale) {
-  const int64_t cs = blockIdx.x * static_cast<int64_t>(kBlock) + threadIdx.x;
-  if (cs < Lc.n_slots) restrict_one<DIM, T, PMODE, BC, BF>(Lc, Lf, rf, bc, phat, pscale, cs);
+__global__ void __launch_bounds__(32 * kRestrictWarps)
+    k_restrict(LevelDesc Lc, LevelDesc Lf, const T* rf, T* bc, const void* phat, const float* pscale,
+               const int32_t* list, int64_t n_list) {
+  constexpr int N5 = cpow(5, DIM);
+  __shared__ T part[kRestrictWarps][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t i = blockIdx.x * 32LL + lane;
+  const int64_t cs = list ? (i < n_list ? list[i] : -1) : (i < Lc.n_slots ? i : -1);
+  int X[DIM];
+  const bool dof = cs >= 0 && coords_of_b<DIM, BC>(Lc, cs, X) && is_dof(Lc.vflags[cs]);
+  T acc = T(0);
+  if (dof) {
+    const int64_t cb = cs / Lc.S, cl = cs - cb * Lc.S;
+    for (int k = warp; k < N5; k += kRestrictWarps) {
+      int y[DIM];
+      int kk = k;
+      double w = 1.0;
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) {
+        const int o = kk % 5 - 2;
+        kk /= 5;
+        y[a] = 3 * X[a] + o;
+        w *= wlin1(o);
+      }
+      const int64_t fs = slot_of_b<DIM, BF>(Lf, y);
+      if (fs < 0) continue;
+      T p = static_cast<T>(w);
+      if constexpr (PMODE != 0) p += load_delta<PMODE, T>(phat, pscale, (cb * N5 + k) * Lc.S + cl, cs);
+      acc = fma(p, rf[fs], acc);
+    }
+  }
+  part[warp][lane] = acc;
+  __syncthreads();
+  if (warp == 0 && cs >= 0) {
+    T t = part[0][lane];
+#pragma unroll
+    for (int j = 1; j < kRestrictWarps; ++j) t += part[j][lane];
+    bc[cs] = dof ? t : T(0);
+  }
 }
 
 // u_f(v) += sum over coarse parents V of P(V, v - 3V) e_c(V) (coarse-grid
@@ -433,20 +495,33 @@ __device__ __forceinline__ void prolong_one(const LevelDesc& Lc, const LevelDesc
   uf[fs] += acc;
 }
 
+// (list: fine DoF slots to serve, thread i -> list[i]; nullptr: every fine slot)
 template <int DIM, typename T, int PMODE, int BC, int BF>
 __global__ void __launch_bounds__(kBlock) k_prolong(LevelDesc Lc, LevelDesc Lf, const T* ec, T* uf,
-                                                      const void* phat, const float* pscale) {
-  const int64_t fs = blockIdx.x * static_cast<int64_t>(kBlock) + threadIdx.x;
-  if (fs < Lf.n_slots) prolong_one<DIM, T, PMODE, BC, BF>(Lc, Lf, ec, uf, phat, pscale, fs);
+                                                      const void* phat, const float* pscale,
+                                                      const int32_t* list, int64_t n_list) {
+  const int64_t i = blockIdx.x * static_cast<int64_t>(kBlock) + threadIdx.x;
+  if (list) {
+    if (i < n_list) prolong_one<DIM, T, PMODE, BC, BF>(Lc, Lf, ec, uf, phat, pscale, list[i]);
+  } else if (i < Lf.n_slots) {
+    prolong_one<DIM, T, PMODE, BC, BF>(Lc, Lf, ec, uf, phat, pscale, i);
+  }
 }
 
 // u_f on HANGING slots = d-linear interpolant of the coarser level (Sect. 3, rule 2)
+// (list: the hanging slots, thread i -> list[i]; nullptr: every slot, flag-checked)
 template <int DIM, typename T>
 __global__ void __launch_bounds__(kBlock) k_hanging(LevelDesc Lf, const int32_t* hang_idx, const double* hang_w,
-                                                      const T* uc, T* uf) {
-  const int64_t fs = blockIdx.x * static_cast<int64_t>(kBlock) + threadIdx.x;
-  if (fs >= Lf.n_slots) return;
-  if (!(Lf.vflags[fs] & MG_V_HANGING)) return;
+                                                      const T* uc, T* uf, const int32_t* list, int64_t n_list) {
+  const int64_t i = blockIdx.x * static_cast<int64_t>(kBlock) + threadIdx.x;
+  int64_t fs;
+  if (list) {
+    if (i >= n_list) return;
+    fs = list[i];
+  } else {
+    if (i >= Lf.n_slots || !(Lf.vflags[i] & MG_V_HANGING)) return;
+    fs = i;
+  }
   T acc = T(0);
 #pragma unroll
   for (int e = 0; e < (1 << DIM); ++e) {
@@ -471,8 +546,11 @@ inline int pick_slab(int B, int64_t n_bricks, int64_t target) {
 template <int DIM, typename T>
 void launch_sweep(SweepArgs<T> a, int op, int amode, cudaStream_t s);
 
+// list / n_list: the coarse (restriction) or fine (prolongation) slots to serve;
+// nullptr serves every slot of the target level
 template <int DIM, typename T>
 void launch_transfer(const LevelDesc& Lc, const LevelDesc& Lf, bool restrict_op, int pmode, const T* in, T* out,
-                     const void* phat, const float* pscale, cudaStream_t s);
+                     const void* phat, const float* pscale, cudaStream_t s, const int32_t* list = nullptr,
+                     int64_t n_list = 0);
 
 }  // namespace mg

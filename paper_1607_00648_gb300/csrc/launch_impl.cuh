@@ -5,47 +5,74 @@
 #include <type_traits>
 
 #include "kernels.cuh"
+#include "sweep_fast.cuh"
 
 namespace mg {
 
 template <int DIM, typename T, int B>
 static void sweep_b(SweepArgs<T> a, int op, int amode, cudaStream_t s) {
   constexpr int PLANE = DIM == 2 ? B : B * B;
-  constexpr int UPL = DIM == 2 ? B + 2 : (B + 2) * (B + 2);
-  constexpr int EPL = DIM == 2 ? B + 1 : (B + 1) * (B + 1);
   const int R = a.R;
-  const dim3 grid(static_cast<unsigned>(a.L.n_bricks), static_cast<unsigned>(B / R));
-  int threads = ((R * PLANE + 31) / 32) * 32;
-  if (threads > kBlock) threads = kBlock;
-  const size_t smem = (static_cast<size_t>(UPL) * (R + 2) + static_cast<size_t>(EPL) * (R + 1)) * sizeof(T);
-#define MG_SW(AM, OP) k_sweep<DIM, T, AM, OP, B><<<grid, threads, smem, s>>>(a)
-  if constexpr (std::is_same<T, double>::value) {
-    if (op == kJacobi) {
-      if (amode == 1) MG_SW(1, kJacobi); else MG_SW(0, kJacobi);
-    } else {
-      if (amode == 1) MG_SW(1, kResidual); else MG_SW(0, kResidual);
-    }
-  } else {
+  const size_t smem = sweep_tile_bytes<DIM, T>(B, R);
+  if constexpr (std::is_same<T, float>::value && ((DIM == 2 && B == 27) || (DIM == 3 && B == 9))) {
+    // FP32 (issue- and latency-bound): column-marching kernels with the slab depth
+    // as a template parameter so every plane's loads are issued together
+    const dim3 grid(static_cast<unsigned>(sweep_ctas_x(DIM, B, T(0), a.L.n_bricks)), static_cast<unsigned>(B / R));
+    const size_t sm = DIM == 2 ? 0 : smem;
+#define MG_SWR(AM, OP, RR)                                                                \
+  do {                                                                                    \
+    if constexpr (DIM == 2) k_sweep2c<T, AM, OP, RR><<<grid, 128, 0, s>>>(a);               \
+    else k_sweep3c<T, AM, OP, (RR > 9 ? 9 : RR)><<<grid, 128, sm, s>>>(a);                  \
+  } while (0)
+#define MG_SW(AM, OP)                                                    \
+  do {                                                                   \
+    if (R == 1) MG_SWR(AM, OP, 1);                                       \
+    else if (R == 3) MG_SWR(AM, OP, 3);                                  \
+    else if (R == 9) MG_SWR(AM, OP, 9);                                  \
+    else MG_SWR(AM, OP, 27);                                             \
+  } while (0)
     if (op == kJacobi) {
       if (amode == 2) MG_SW(2, kJacobi); else if (amode == 3) MG_SW(3, kJacobi); else MG_SW(0, kJacobi);
     } else {
       if (amode == 2) MG_SW(2, kResidual); else if (amode == 3) MG_SW(3, kResidual); else MG_SW(0, kResidual);
     }
-  }
 #undef MG_SW
+#undef MG_SWR
+  } else {
+    const dim3 grid(static_cast<unsigned>(a.L.n_bricks), static_cast<unsigned>(B / R));
+    int threads = ((R * PLANE + 31) / 32) * 32;
+    if (threads > kBlock) threads = kBlock;
+#define MG_SW(AM, OP) k_sweep<DIM, T, AM, OP, B><<<grid, threads, smem, s>>>(a)
+    if constexpr (std::is_same<T, double>::value) {
+      if (op == kJacobi) {
+        if (amode == 1) MG_SW(1, kJacobi); else MG_SW(0, kJacobi);
+      } else {
+        if (amode == 1) MG_SW(1, kResidual); else MG_SW(0, kResidual);
+      }
+    } else {
+      if (op == kJacobi) {
+        if (amode == 2) MG_SW(2, kJacobi); else if (amode == 3) MG_SW(3, kJacobi); else MG_SW(0, kJacobi);
+      } else {
+        if (amode == 2) MG_SW(2, kResidual); else if (amode == 3) MG_SW(3, kResidual); else MG_SW(0, kResidual);
+      }
+    }
+#undef MG_SW
+  }
 }
 
 template <int DIM, typename T, int BC, int BF>
 static void transfer_b(const LevelDesc& Lc, const LevelDesc& Lf, bool restrict_op, int pmode, const T* in, T* out,
-                       const void* ph, const float* ps, cudaStream_t s) {
-  const unsigned gc = static_cast<unsigned>((Lc.n_slots + kBlock - 1) / kBlock);
-  const unsigned gf = static_cast<unsigned>((Lf.n_slots + kBlock - 1) / kBlock);
-#define MG_TR(PM)                                                                          \
-  do {                                                                                     \
-    if (restrict_op)                                                                       \
-      k_restrict<DIM, T, PM, BC, BF><<<gc, kBlock, 0, s>>>(Lc, Lf, in, out, ph, ps);      \
-    else                                                                                   \
-      k_prolong<DIM, T, PM, BC, BF><<<gf, kBlock, 0, s>>>(Lc, Lf, in, out, ph, ps);       \
+                       const void* ph, const float* ps, cudaStream_t s, const int32_t* li, int64_t nl) {
+  const int64_t nc = li ? nl : Lc.n_slots, nf = li ? nl : Lf.n_slots;
+  const unsigned gc = static_cast<unsigned>((nc + 31) / 32);
+  const unsigned gf = static_cast<unsigned>((nf + kBlock - 1) / kBlock);
+  if ((restrict_op ? gc : gf) == 0) return;
+#define MG_TR(PM)                                                                                   \
+  do {                                                                                              \
+    if (restrict_op)                                                                                \
+      k_restrict<DIM, T, PM, BC, BF><<<gc, 32 * kRestrictWarps, 0, s>>>(Lc, Lf, in, out, ph, ps, li, nl); \
+    else                                                                                            \
+      k_prolong<DIM, T, PM, BC, BF><<<gf, kBlock, 0, s>>>(Lc, Lf, in, out, ph, ps, li, nl);         \
   } while (0)
   if constexpr (std::is_same<T, double>::value) {
     if (pmode == 1) MG_TR(1); else MG_TR(0);
@@ -69,9 +96,10 @@ static void transfer_b(const LevelDesc& Lc, const LevelDesc& Lf, bool restrict_o
   }                                                                                                         \
   template <>                                                                                               \
   void launch_transfer<DIM, T>(const LevelDesc& Lc, const LevelDesc& Lf, bool r, int pmode, const T* in,     \
-                               T* out, const void* ph, const float* ps, cudaStream_t s) {                   \
-    if (Lc.B == 3 && Lf.B == 9) transfer_b<DIM, T, 3, 9>(Lc, Lf, r, pmode, in, out, ph, ps, s);              \
-    else if (Lc.B == 9 && Lf.B == 9) transfer_b<DIM, T, 9, 9>(Lc, Lf, r, pmode, in, out, ph, ps, s);         \
+                               T* out, const void* ph, const float* ps, cudaStream_t s, const int32_t* li,  \
+                               int64_t nl) {                                                                \
+    if (Lc.B == 3 && Lf.B == 9) transfer_b<DIM, T, 3, 9>(Lc, Lf, r, pmode, in, out, ph, ps, s, li, nl);      \
+    else if (Lc.B == 9 && Lf.B == 9) transfer_b<DIM, T, 9, 9>(Lc, Lf, r, pmode, in, out, ph, ps, s, li, nl); \
     else MG_TRANSFER_27(DIM, T)                                                                             \
   }                                                                                                         \
   }

@@ -84,7 +84,7 @@ int64_t launch_residual(const Hier& H, const DevLevel& D, bool coarse_delta, con
     launch_sweep<2, double>(a, kResidual, coarse_delta ? 1 : 0, s);
   else
     launch_sweep<3, double>(a, kResidual, coarse_delta ? 1 : 0, s);
-  return D.d.n_bricks * (D.d.B / a.R);
+  return sweep_ctas_x(H.dim, D.d.B, 0.0, D.d.n_bricks) * (D.d.B / a.R);
 }
 
 }  // namespace
@@ -113,8 +113,9 @@ extern "C" mg_status mg_residual_norm_noalloc(mg_hier* h, int level, const doubl
   const mg_status st = partials_on_current_device(&partial);
   if (st != MG_OK) return st;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const bool coarse_delta = level < H->L && H->galerkin;
-  if (D.d.n_bricks * (D.d.B / pick_slab(D.d.B, D.d.n_bricks, kSweepTargetCtas)) > kMaxBricks) {
+  const bool coarse_delta = level < H->top && H->galerkin;
+  if (sweep_ctas_x(H->dim, D.d.B, 0.0, D.d.n_bricks) * (D.d.B / pick_slab(D.d.B, D.d.n_bricks, kSweepTargetCtas)) >
+      kMaxBricks) {
     set_error("mg_residual_norm_noalloc: level needs more than 4096 partial sums; use mg_residual");
     return MG_ERR_INVALID_ARG;
   }

@@ -207,86 +207,142 @@ __global__ void __launch_bounds__(64) k_boxmg(LevelDesc Lc, LevelDesc Lf, const 
   }
 }
 
-// Galerkin coarse operator A_c = P^T A_f P per coarse vertex V (Sect. 4.3):
-// A_c(V, W) = sum_{v in supp P(V)} P(V,v) sum_{w in stencil(v)} A_f(v,w) P(W,w),
-// with the fine stencils rebuilt in situ.  Stores A_hat = A_c - A_redisc(eps_c),
-// zero on entries pointing to non-DoF vertices (they keep the rediscretised value).
+// Galerkin coarse operator A_c = P^T A_f P (Sect. 4.3), one group of kRapTpv
+// threads per coarse vertex V: thread j takes the fine vertex f = 3V + d(j) of the
+// support of P(V, .) (5^d of them), rebuilds f's fine stencil in situ and forms its
+// contributions P(f,V) A_f(f,g) P(g,W) to the 3^d coarse entries W = V + o; the
+// group then adds them in a fixed order (warp shuffles, then warps in order).
+// Stores A_hat = A_c - A_redisc(eps_c), zero on entries to non-DoF vertices (they
+// keep the rediscretised value), zero planes on non-DoF coarse vertices.
+template <int DIM>
+constexpr int rap_tpv() { return DIM == 2 ? 32 : 128; }
+
 template <int DIM, int PMODE>
 __global__ void __launch_bounds__(128) k_rap(LevelDesc Lc, LevelDesc Lf, const double* eps_f, const double* ahat_f,
                                                const double* eps_c, const double* phat_c, double* ahat_c) {
   constexpr int N3 = cpow(3, DIM), N5 = cpow(5, DIM);
-  const int64_t cs = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
-  if (cs >= Lc.n_slots) return;
+  constexpr int TPV = rap_tpv<DIM>(), VPB = 128 / TPV, WPV = TPV / 32;
+  __shared__ int64_t pbase[VPB][N3];   // plane-0 index of P_hat(W) for W = V + o if W is a DoF, else -1
+  __shared__ double sred[VPB][N3];     // A_redisc(V, V + o)
+  __shared__ double part[VPB][N3][WPV];
+  __shared__ double plin[N5];          // d-linear weights by 5^d offset
+  __shared__ double sst[128][N3];      // P(f,V) * fine stencil of f, per thread
+  const int sub = threadIdx.x / TPV, j = threadIdx.x % TPV;
+  const int64_t cs = blockIdx.x * static_cast<int64_t>(VPB) + sub;
   int V[DIM];
-  const bool valid = coords_of<DIM>(Lc, cs, V);
-  if (!valid || !is_dof(Lc.vflags[cs])) {
-    if (valid)
-      for (int k = 0; k < N3; ++k) ahat_c[plane_index(Lc, cs, k, N3)] = 0.0;
-    return;
-  }
-  double acc[N3];
-  for (int k = 0; k < N3; ++k) acc[k] = 0.0;
-  for (int k5 = 0; k5 < N5; ++k5) {
-    int o[DIM], v[DIM], kk = k5;
-#pragma unroll
+  const bool valid = cs < Lc.n_slots && coords_of<DIM>(Lc, cs, V);
+  const bool vdof = valid && is_dof(Lc.vflags[cs]);
+  for (int k = threadIdx.x; k < N5; k += blockDim.x) {
+    double w = 1.0;
+    int kk = k;
     for (int i = 0; i < DIM; ++i) {
-      o[i] = kk % 5 - 2;
+      w *= wlin1(kk % 5 - 2);
       kk /= 5;
-      v[i] = 3 * V[i] + o[i];
     }
-    const int64_t fs = slot_of<DIM>(Lf, v);
-    if (fs < 0 || !is_dof(Lf.vflags[fs])) continue;
-    const double pV = p_entry_d<DIM, PMODE>(Lc, phat_c, cs, o);
-    double st[N3];
-    full_stencil<DIM>(Lf, eps_f, ahat_f, v, fs, st);
-    for (int t = 0; t < N3; ++t) {
-      int w[DIM], tt = t;
-#pragma unroll
-      for (int i = 0; i < DIM; ++i) {
-        w[i] = v[i] + tt % 3 - 1;
-        tt /= 3;
-      }
-      const double a = pV * st[t];
-      int lo[DIM], cnt[DIM];
-#pragma unroll
-      for (int i = 0; i < DIM; ++i) {
-        lo[i] = w[i] >= 0 ? w[i] / 3 : -1;
-        cnt[i] = (w[i] >= 0 && w[i] % 3 == 0) ? 1 : 2;
-      }
-      for (int e = 0; e < (1 << DIM); ++e) {
-        int W[DIM], ow[DIM];
-        bool ok = true;
-        int q = 0, m = 1;
-#pragma unroll
-        for (int i = 0; i < DIM; ++i) {
-          const int ei = (e >> i) & 1;
-          if (ei >= cnt[i]) ok = false;
-          W[i] = lo[i] + ei;
-          ow[i] = w[i] - 3 * W[i];
-          const int dq = W[i] - V[i];
-          if (dq < -1 || dq > 1) ok = false;
-          q += (dq + 1) * m;
-          m *= 3;
-        }
-        if (!ok) continue;
-        const int64_t ws = slot_of<DIM>(Lc, W);
-        if (ws < 0 || !is_dof(Lc.vflags[ws])) continue;
-        acc[q] = fma(a, p_entry_d<DIM, PMODE>(Lc, phat_c, ws, ow), acc[q]);
-      }
-    }
+    plin[k] = w;
   }
-  double sr[N3];
-  full_stencil<DIM>(Lc, eps_c, nullptr, V, cs, sr);
-  for (int q = 0; q < N3; ++q) {
-    int W[DIM], qq = q;
+  if (vdof && j < N3) {
+    int W[DIM], jj = j;
 #pragma unroll
     for (int i = 0; i < DIM; ++i) {
-      W[i] = V[i] + qq % 3 - 1;
-      qq /= 3;
+      W[i] = V[i] + jj % 3 - 1;
+      jj /= 3;
     }
     const int64_t ws = slot_of<DIM>(Lc, W);
-    const bool dofw = ws >= 0 && is_dof(Lc.vflags[ws]);
-    ahat_c[plane_index(Lc, cs, q, N3)] = dofw ? acc[q] - sr[q] : 0.0;
+    pbase[sub][j] = (ws >= 0 && is_dof(Lc.vflags[ws])) ? plane_index(Lc, ws, 0, N5) : -1;
+  }
+  if (vdof && j == 0) {
+    double sr[N3];
+    full_stencil<DIM>(Lc, eps_c, nullptr, V, cs, sr);
+#pragma unroll
+    for (int q = 0; q < N3; ++q) sred[sub][q] = sr[q];
+  }
+  // this thread's fine vertex f = 3V + d and which of its stencil neighbours are DoFs
+  int d[DIM];
+  uint32_t gdof = 0;
+  {
+    int f[DIM], jj = j;
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) {
+      d[i] = jj % 5 - 2;
+      jj /= 5;
+      f[i] = 3 * V[i] + d[i];
+    }
+    const int64_t fs = (vdof && j < N5) ? slot_of<DIM>(Lf, f) : -1;
+    if (fs >= 0 && is_dof(Lf.vflags[fs])) {
+      const double pV = p_entry_d<DIM, PMODE>(Lc, phat_c, cs, d);
+      double st[N3];
+      full_stencil<DIM>(Lf, eps_f, ahat_f, f, fs, st);
+#pragma unroll
+      for (int e = 0; e < N3; ++e) {
+        int g[DIM], ee = e;
+#pragma unroll
+        for (int i = 0; i < DIM; ++i) {
+          g[i] = f[i] + ee % 3 - 1;
+          ee /= 3;
+        }
+        const int64_t gs = slot_of<DIM>(Lf, g);
+        if (gs >= 0 && is_dof(Lf.vflags[gs])) gdof |= 1u << e;
+        sst[threadIdx.x][e] = pV * st[e];
+      }
+    }
+  }
+  __syncthreads();
+
+  // c[q] = sum over stencil neighbours g of f with |g - 3W| <= 2 (W = V + o_q) of
+  // P(f,V) A_f(f,g) P(g,W); per axis the admissible g offsets form a range
+  double c[N3];
+#pragma unroll
+  for (int q = 0; q < N3; ++q) c[q] = 0.0;
+  if (gdof) {
+    const int64_t Sc = Lc.S;
+#pragma unroll
+    for (int q = 0; q < N3; ++q) {
+      const int64_t pb = pbase[sub][q];
+      if (pb < 0) continue;
+      int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0}, qq = q;
+#pragma unroll
+      for (int i = 0; i < DIM; ++i) {
+        const int o3 = 3 * (qq % 3 - 1);
+        qq /= 3;
+        lo[i] = max(-1, o3 - 2 - d[i]);
+        hi[i] = min(1, o3 + 2 - d[i]);
+      }
+      double acc = 0.0;
+      for (int ez = lo[2]; ez <= hi[2]; ++ez)
+        for (int ey = lo[1]; ey <= hi[1]; ++ey)
+          for (int ex = lo[0]; ex <= hi[0]; ++ex) {
+            const int e = DIM == 2 ? (ex + 1) + 3 * (ey + 1) : (ex + 1) + 3 * (ey + 1) + 9 * (ez + 1);
+            if (!((gdof >> e) & 1u)) continue;
+            // offset of g from 3W, per axis d + e - 3 o in [-2, 2]
+            int k5 = (d[0] + ex - 3 * (q % 3 - 1)) + 2 + 5 * ((d[1] + ey - 3 * ((q / 3) % 3 - 1)) + 2);
+            if (DIM == 3) k5 += 25 * ((d[2] + ez - 3 * (q / 9 - 1)) + 2);
+            double p = plin[k5];
+            if constexpr (PMODE == 1) p += phat_c[pb + k5 * Sc];
+            acc = fma(sst[threadIdx.x][e], p, acc);
+          }
+      c[q] = acc;
+    }
+  }
+  // fixed-order reduction over the group: shuffles within each warp, then warps in order
+  const int lane = threadIdx.x & 31, wig = j / 32;
+#pragma unroll
+  for (int q = 0; q < N3; ++q) {
+    double v = c[q];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    if (lane == 0) part[sub][q][wig] = v;
+  }
+  __syncthreads();
+  if (valid && j < N3) {
+    double out = 0.0;
+    if (vdof && pbase[sub][j] >= 0) {
+      double acc = part[sub][j][0];
+#pragma unroll
+      for (int w = 1; w < WPV; ++w) acc += part[sub][j][w];
+      out = acc - sred[sub][j];
+    }
+    ahat_c[plane_index(Lc, cs, j, N3)] = out;
   }
 }
 

@@ -80,8 +80,8 @@ __global__ void k_inject(LevelDesc Lt, const int32_t* child, const T* uL, T* ut)
   if (is_dof(f) && (f & MG_V_REFINED)) ut[s] = uL[child[s]];
 }
 
-// coarse-correction right-hand side: R r_L at refined level-t DoFs (already in
-// rhs), the level-t residual at unrefined ones, zero elsewhere
+// coarse-correction right-hand side off the refined vertices: the level-t residual
+// at unrefined DoFs, zero at non-DoFs (the restriction fills the refined DoFs)
 template <typename T>
 __global__ void k_compose_rhs(LevelDesc Lt, const T* r_t, T* rhs) {
   const int64_t s = blockIdx.x * static_cast<int64_t>(kBlock) + threadIdx.x;
@@ -443,11 +443,27 @@ static mg_status create(const Grid* g, const mg_options& o, Hier** out) {
     }
     if ((st = upload(*H, &H->child_top, child)) != MG_OK) return fail(st);
     int64_t unref = 0;
+    std::vector<int32_t> ref, dofL, hangL;
     for (int64_t s = 0; s < ht.n_slots; ++s) {
       const uint8_t f = ht.vflags[s];
-      if ((f & MG_V_EXISTS) && !(f & (MG_V_BOUNDARY | MG_V_HANGING | MG_V_REFINED))) ++unref;
+      if (!(f & MG_V_EXISTS) || (f & (MG_V_BOUNDARY | MG_V_HANGING))) continue;
+      if (f & MG_V_REFINED)
+        ref.push_back(static_cast<int32_t>(s));
+      else
+        ++unref;
+    }
+    for (int64_t s = 0; s < hf.n_slots; ++s) {
+      const uint8_t f = hf.vflags[s];
+      if (!(f & MG_V_EXISTS) || (f & MG_V_BOUNDARY)) continue;
+      ((f & MG_V_HANGING) ? hangL : dofL).push_back(static_cast<int32_t>(s));
     }
     H->n_comp_dofs = hf.n_dofs + unref;
+    H->n_ref_top = static_cast<int64_t>(ref.size());
+    H->n_dof_L = static_cast<int64_t>(dofL.size());
+    H->n_hang_L = static_cast<int64_t>(hangL.size());
+    if (!ref.empty() && (st = upload(*H, &H->ref_top, ref)) != MG_OK) return fail(st);
+    if (!dofL.empty() && (st = upload(*H, &H->dof_L, dofL)) != MG_OK) return fail(st);
+    if (!hangL.empty() && (st = upload(*H, &H->hang_L, hangL)) != MG_OK) return fail(st);
     if (H->mixed) {
       if ((st = dalloc(*H, &H->c32, static_cast<size_t>(ht.n_slots))) != MG_OK) return fail(st);
       if ((st = dalloc(*H, &H->cb32, static_cast<size_t>(ht.n_slots))) != MG_OK) return fail(st);
@@ -532,7 +548,7 @@ static SweepArgs<T> sweep_args(const Hier& H, int l, const T* u, const T* b, T* 
   a.b = b;
   a.out = out;
   a.omega = static_cast<T>(H.opt.omega);
-  a.R = pick_slab(D.d.B, D.d.n_bricks, kSweepTargetCtas);
+  a.R = sweep_slab<T>(H.dim, D.d.B, D.d.n_bricks);
   *amode = 0;
   if constexpr (std::is_same<T, double>::value) {
     a.eps = D.eps;
@@ -572,7 +588,8 @@ static void sweep(const Hier& H, int l, int op, const T* u, const T* b, T* out, 
 }
 
 template <typename T>
-static void transfer(const Hier& H, int fine, bool restrict_op, const T* in, T* out, cudaStream_t s) {
+static void transfer(const Hier& H, int fine, bool restrict_op, const T* in, T* out, cudaStream_t s,
+                     const int32_t* list = nullptr, int64_t n_list = 0) {
   const DevLevel& F = H.lv[fine];
   const DevLevel& C = H.lv[fine - 1];
   int pmode = 0;
@@ -589,9 +606,9 @@ static void transfer(const Hier& H, int fine, bool restrict_op, const T* in, T* 
     }
   }
   if (H.dim == 2)
-    launch_transfer<2, T>(C.d, F.d, restrict_op, pmode, in, out, ph, ps, s);
+    launch_transfer<2, T>(C.d, F.d, restrict_op, pmode, in, out, ph, ps, s, list, n_list);
   else
-    launch_transfer<3, T>(C.d, F.d, restrict_op, pmode, in, out, ph, ps, s);
+    launch_transfer<3, T>(C.d, F.d, restrict_op, pmode, in, out, ph, ps, s, list, n_list);
 }
 
 template <typename T>
@@ -682,17 +699,19 @@ static mg_status run_setup(Hier& H, const double* eps_in, cudaStream_t s, bool c
         k_boxmg<3><<<gp, 64, 0, s>>>(C.d, F.d, F.eps, ahat_f, C.phat, H.d_status);
     }
     if (H.galerkin) {
-      const unsigned gr = static_cast<unsigned>((C.d.n_slots + 31) / 32);  // small CTAs: spread small levels
+      // 128-thread CTAs: 4 coarse vertices (2D) or 1 (3D) per CTA
+      const unsigned gr = static_cast<unsigned>((C.d.n_slots + (128 / rap_tpv<2>()) - 1) / (128 / rap_tpv<2>()));
       if (d == 2) {
         if (H.boxmg)
-          k_rap<2, 1><<<gr, 32, 0, s>>>(C.d, F.d, F.eps, ahat_f, C.eps, C.phat, C.ahat);
+          k_rap<2, 1><<<gr, 128, 0, s>>>(C.d, F.d, F.eps, ahat_f, C.eps, C.phat, C.ahat);
         else
-          k_rap<2, 0><<<gr, 32, 0, s>>>(C.d, F.d, F.eps, ahat_f, C.eps, C.phat, C.ahat);
+          k_rap<2, 0><<<gr, 128, 0, s>>>(C.d, F.d, F.eps, ahat_f, C.eps, C.phat, C.ahat);
       } else {
+        const unsigned g3 = static_cast<unsigned>(C.d.n_slots);
         if (H.boxmg)
-          k_rap<3, 1><<<gr, 32, 0, s>>>(C.d, F.d, F.eps, ahat_f, C.eps, C.phat, C.ahat);
+          k_rap<3, 1><<<g3, 128, 0, s>>>(C.d, F.d, F.eps, ahat_f, C.eps, C.phat, C.ahat);
         else
-          k_rap<3, 0><<<gr, 32, 0, s>>>(C.d, F.d, F.eps, ahat_f, C.eps, C.phat, C.ahat);
+          k_rap<3, 0><<<g3, 128, 0, s>>>(C.d, F.d, F.eps, ahat_f, C.eps, C.phat, C.ahat);
       }
     }
     MG_CHECK(last_launch("setup: BoxMG / Galerkin"));
@@ -939,10 +958,11 @@ static mg_status solve_mixed(Hier& H, double* u, const double* b, double tol, in
 template <typename T>
 static void fill_hanging(const Hier& H, const T* ut, T* uL, cudaStream_t s) {
   const DevLevel& F = H.lv[H.L];
+  if (H.n_hang_L == 0) return;
   if (H.dim == 2)
-    k_hanging<2, T><<<nblk(F.d.n_slots), kBlock, 0, s>>>(F.d, F.hang_idx, F.hang_w, ut, uL);
+    k_hanging<2, T><<<nblk(H.n_hang_L), kBlock, 0, s>>>(F.d, F.hang_idx, F.hang_w, ut, uL, H.hang_L, H.n_hang_L);
   else
-    k_hanging<3, T><<<nblk(F.d.n_slots), kBlock, 0, s>>>(F.d, F.hang_idx, F.hang_w, ut, uL);
+    k_hanging<3, T><<<nblk(H.n_hang_L), kBlock, 0, s>>>(F.d, F.hang_idx, F.hang_w, ut, uL, H.hang_L, H.n_hang_L);
 }
 
 template <typename T>
@@ -989,12 +1009,14 @@ static void composite_cycle(Hier& H, T* uL, const T* bL, T* ut, const T* bt, cud
   sweep<T>(H, L, kResidual, uL, bL, rL, nullptr, s);
   inject<T>(H, uL, ut, s);
   sweep<T>(H, t, kResidual, ut, bt, rt, nullptr, s);
-  transfer<T>(H, L, true, rL, rhs, s);  // d-linear R = P^T (no operator-dependent transfer on level L)
+  // d-linear R = P^T at refined level-t DoFs (no operator-dependent transfer on
+  // level L), the level-t residual at unrefined ones, zero elsewhere
   k_compose_rhs<T><<<nblk(D.d.n_slots), kBlock, 0, s>>>(D.d, rt, rhs);
+  transfer<T>(H, L, true, rL, rhs, s, H.ref_top, H.n_ref_top);
   cudaMemsetAsync(et, 0, D.d.n_slots * sizeof(T), s);
   vcycle<T>(H, t, et, rhs, s);
   k_add_unrefined<T><<<nblk(D.d.n_slots), kBlock, 0, s>>>(D.d, et, ut);
-  transfer<T>(H, L, false, et, uL, s);
+  transfer<T>(H, L, false, et, uL, s, H.dof_L, H.n_dof_L);
   fill_hanging<T>(H, ut, uL, s);
   smooth<T>(H, L, uL, bL, tmpL, H.opt.nu2, s);
 }
@@ -1186,9 +1208,7 @@ static PLevel<T> make_plevel(const Hier& H, int l, T* u_fin, const T* b_fin) {
 template <typename T>
 static size_t tile_bytes(const Hier& H, int l, int R) {
   const int B = H.lv[l].d.B;
-  const size_t upl = H.dim == 2 ? B + 2 : (B + 2) * (B + 2);
-  const size_t epl = H.dim == 2 ? B + 1 : (B + 1) * (B + 1);
-  return (upl * (R + 2) + epl * (R + 1)) * sizeof(T);
+  return H.dim == 2 ? sweep_tile_bytes<2, T>(B, R) : sweep_tile_bytes<3, T>(B, R);
 }
 
 static mg_status solve_persistent(Hier& H, double* u, const double* b, double tol, int max_cycles,
@@ -1520,9 +1540,11 @@ mg_status mg_interpolate_hanging(mg_hier* h, int level, const double* u_coarse, 
   DevLevel& F = H->lv[level];
   cudaStream_t s = pick(*H, stream);
   if (H->dim == 2)
-    k_hanging<2, double><<<nblk(F.d.n_slots), kBlock, 0, s>>>(F.d, F.hang_idx, F.hang_w, u_coarse, u_fine);
+    k_hanging<2, double><<<nblk(F.d.n_slots), kBlock, 0, s>>>(F.d, F.hang_idx, F.hang_w, u_coarse, u_fine,
+                                                              nullptr, 0);
   else
-    k_hanging<3, double><<<nblk(F.d.n_slots), kBlock, 0, s>>>(F.d, F.hang_idx, F.hang_w, u_coarse, u_fine);
+    k_hanging<3, double><<<nblk(F.d.n_slots), kBlock, 0, s>>>(F.d, F.hang_idx, F.hang_w, u_coarse, u_fine,
+                                                              nullptr, 0);
   return last_launch("mg_interpolate_hanging");
 }
 

@@ -1,0 +1,263 @@
+// Sweep kernels for the brick edges that carry the fine levels (2D: 27, 3D: 9),
+// with every index fixed per thread and advanced incrementally along the last
+// axis.  Same operations and results as sweep_item (in-situ stencil from the
+// adjacent cells' coefficients, + stored delta on coarse levels, Jacobi / residual),
+// with a fraction of its integer work: the generic kernel spends most of its issue
+// slots on per-element index arithmetic, which bounds the FP32 sweeps.
+#pragma once
+
+#include "kernels.cuh"
+
+namespace mg {
+
+// 4-byte asynchronous global -> shared copy (cp.async); src_ok false writes zero
+// (src-size 0) and reads nothing, so `g` only has to be a valid address
+__device__ __forceinline__ void cp_async4(void* s, const void* g, bool src_ok) {
+  const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(s));
+  const int n = src_ok ? 4 : 0;
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(g), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// The 9-point bilinear stencil at one vertex from its 3x3 values and 4 cells
+// (cells sw, se, nw, ne; values row-major m = y-1, 0 = y, p = y+1; l/r = x -+ 1).
+template <typename T>
+__device__ __forceinline__ void stencil2(T sw, T se, T nw, T ne, T um_l, T um, T um_r, T u0_l, T u0, T u0_r, T up_l,
+                                         T up, T up_r, T& Au, T& D) {
+  const T sW = sw + nw, sE = se + ne, sS = sw + se, sN = nw + ne;
+  const T sC = sW + sE;
+  T a1 = sW * u0_l;
+  a1 = fma(sE, u0_r, a1);
+  a1 = fma(sS, um, a1);
+  a1 = fma(sN, up, a1);
+  T a2 = sw * um_l;
+  a2 = fma(se, um_r, a2);
+  a2 = fma(nw, up_l, a2);
+  a2 = fma(ne, up_r, a2);
+  const T k0 = static_cast<T>(elem_k(2, 0)), k1 = static_cast<T>(elem_k(2, 1)), k2 = static_cast<T>(elem_k(2, 2));
+  D = k0 * sC;
+  Au = fma(D, u0, fma(k1, a1, k2 * a2));
+}
+
+// 2D, brick edge 27 (FP32): one CTA of 128 threads per (brick, slab of R rows).
+// Lane l of warp g holds tile column x = l - 1 (x in [-1, 27]) and rows g, g + 4, ...
+// of the slab with its halo.  The tile is filled by asynchronous copies (cp.async:
+// no registers held, every load in flight at once), b and the flags of a thread's
+// vertices are fetched into registers meanwhile; after one barrier each thread
+// applies the stencil to its vertices from shared memory.
+template <typename T, int AMODE, int OP, int R>
+__global__ void __launch_bounds__(128) k_sweep2c(SweepArgs<T> a) {
+  constexpr int B = 27, Bu = B + 2, Be = B + 1, NR = (R + 3) / 4;
+  __shared__ __align__(16) T su[(R + 2) * Bu];
+  __shared__ __align__(16) T se[(R + 1) * Be];
+  const LevelDesc& L = a.L;
+  const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
+  const int64_t brick = blockIdx.x, base = brick * L.S;
+  const int z0 = blockIdx.y * R;
+  const int32_t* bn = L.brick_nbr + brick * 9;
+  const int x = lane - 1;
+  // this thread's vertices: rows zl = g + 4 k of the slab, column x in [0, 27)
+  const bool vcol = x >= 0 && x < B;
+  T bv[NR];
+  uint8_t fv[NR];
+#pragma unroll
+  for (int k = 0; k < NR; ++k) {
+    const int zl = g + 4 * k;
+    const bool on = vcol && zl < R;
+    const int64_t slot = base + (z0 + zl) * B + x;
+    fv[k] = on ? L.vflags[slot] : 0;
+    bv[k] = (on && is_dof(fv[k])) ? a.b[slot] : T(0);
+  }
+  if (x <= B) {
+    const int ox = x < 0 ? -1 : (x >= B ? 1 : 0);
+    const int lx = x - ox * B;
+    const int32_t nb_lo = bn[ox + 1], nb_mid = bn[ox + 4], nb_hi = bn[ox + 7];
+    for (int zz = g; zz < R + 2; zz += 4) {
+      const int y = z0 - 1 + zz;
+      const int oy = y < 0 ? -1 : (y >= B ? 1 : 0);
+      const int32_t nb = oy < 0 ? nb_lo : (oy > 0 ? nb_hi : nb_mid);
+      const int64_t idx = nb >= 0 ? static_cast<int64_t>(nb) * L.S + (y - oy * B) * B + lx : 0;
+      cp_async4(su + zz * Bu + lane, a.u + idx, nb >= 0);
+      if (x < B && zz <= R) cp_async4(se + zz * Be + lane, a.eps + idx, nb >= 0);
+    }
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  double part = 0.0;
+  if (vcol) {
+#pragma unroll
+    for (int k = 0; k < NR; ++k) {
+      const int zl = g + 4 * k;
+      if (zl >= R) break;
+      const int64_t slot = base + (z0 + zl) * B + x;
+      const uint8_t vf = fv[k];
+      const T* uc = su + (zl + 1) * Bu + lane;  // tile column of x is lane
+      const T* ec = se + (zl + 1) * Be + lane;  // cell with lower corner (x, y)
+      T res = T(0);
+      if constexpr (OP == kJacobi || OP == kJacobiNorm) {
+        if (vf & MG_V_HANGING) res = uc[0];  // hanging values come from the coarser level (Sect. 3)
+      }
+      if (is_dof(vf)) {
+        const T um_l = uc[-Bu - 1], um = uc[-Bu], um_r = uc[-Bu + 1];
+        const T u0_l = uc[-1], u0 = uc[0], u0_r = uc[1];
+        const T up_l = uc[Bu - 1], up = uc[Bu], up_r = uc[Bu + 1];
+        T Au, D;
+        stencil2<T>(ec[-Be - 1], ec[-Be], ec[-1], ec[0], um_l, um, um_r, u0_l, u0, u0_r, up_l, up, up_r, Au, D);
+        if constexpr (AMODE != 0) {
+          const T nbv[9] = {um_l, um, um_r, u0_l, u0, u0_r, up_l, up, up_r};
+          const int sl = (z0 + zl) * B + x;
+#pragma unroll
+          for (int q = 0; q < 9; ++q) {
+            const T d = load_delta<AMODE, T>(a.ahat, a.ascale, (brick * 9 + q) * L.S + sl, slot);
+            Au = fma(d, nbv[q], Au);
+            if (q == 4) D += d;
+          }
+        }
+        const T r = bv[k] - Au;
+        if constexpr (OP == kJacobi || OP == kJacobiNorm) {
+          res = fma(a.omega * r, recip_nr(D), u0);
+          if constexpr (OP == kJacobiNorm) part += static_cast<double>(r) * static_cast<double>(r);
+        } else {
+          res = r;
+          part += static_cast<double>(r) * static_cast<double>(r);
+        }
+      }
+      a.out[slot] = res;
+    }
+  }
+  if constexpr (OP == kResidual) {
+    if (a.partial) store_partial_and_finish(part, a.partial, a.counter, a.norm2);
+  }
+}
+
+// 3D, brick edge 9: one CTA of 128 threads per (brick, slab of R planes).  Thread t <
+// 121 loads tile column (x, y) in [-1, 9]^2 of u (and of the cell coefficients) for
+// every plane of the slab and its halo; thread t < 100 forms the per-cell corner
+// sums q_c = eps_c S_c of its cell column with a rolling plane sum; thread t < 81
+// marches its vertex column up the slab with the cells below / above and the values
+// below / at the vertex carried in registers.  Vertex formula as in sweep_item:
+//   (A u)_v = h/12 (5 sC u_v - sum_c q_c + sum_axis nbr n  S_n u_n).
+template <typename T, int AMODE, int OP, int R>
+__global__ void __launch_bounds__(128, 8) k_sweep3c(SweepArgs<T> a) {
+  constexpr int B = 9, Bu = 11, Be = 10, UPL = Bu * Bu, EPL = Be * Be, PL = B * B, N3 = 27;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const LevelDesc& L = a.L;
+  const int z0 = blockIdx.y * R;
+  const int64_t brick = blockIdx.x, base = brick * L.S;
+  const int32_t* bn = L.brick_nbr + brick * N3;
+  T* su = reinterpret_cast<T*>(smem_raw);
+  T* se = su + UPL * (R + 2);
+  T* sq = se + EPL * (R + 1);
+  const int t = threadIdx.x;
+  // b and flags of this thread's vertex column, fetched while the tile streams in
+  T bv[R];
+  uint8_t fv[R];
+#pragma unroll
+  for (int zl = 0; zl < R; ++zl) {
+    const int64_t slot = base + (z0 + zl) * PL + t;
+    fv[zl] = t < PL ? L.vflags[slot] : 0;
+    bv[zl] = (t < PL && is_dof(fv[zl])) ? a.b[slot] : T(0);
+  }
+  if (t < UPL) {
+    const int x = t % Bu - 1, y = t / Bu - 1;
+    const int ox = x < 0 ? -1 : (x >= B ? 1 : 0), oy = y < 0 ? -1 : (y >= B ? 1 : 0);
+    const int li = (y - oy * B) * B + (x - ox * B);
+    const int nbase = (ox + 1) + 3 * (oy + 1);
+    const int32_t nb_lo = bn[nbase], nb_mid = bn[nbase + 9], nb_hi = bn[nbase + 18];
+    const bool cell = x < B && y < B;
+    const int ce = (y + 1) * Be + (x + 1);
+#pragma unroll
+    for (int zz = 0; zz < R + 2; ++zz) {
+      const int z = z0 - 1 + zz;
+      const int oz = z < 0 ? -1 : (z >= B ? 1 : 0);
+      const int32_t nb = oz < 0 ? nb_lo : (oz > 0 ? nb_hi : nb_mid);
+      const int64_t idx = nb >= 0 ? static_cast<int64_t>(nb) * L.S + (z - oz * B) * PL + li : 0;
+      cp_async4(su + zz * UPL + t, a.u + idx, nb >= 0);
+      if (cell && zz <= R) cp_async4(se + zz * EPL + ce, a.eps + idx, nb >= 0);
+    }
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  if (t < EPL) {
+    const T* c0 = su + (t / Be) * Bu + (t % Be);  // lowest corner of cell column t
+    T plo = (c0[0] + c0[1]) + (c0[Bu] + c0[Bu + 1]);
+#pragma unroll
+    for (int zz = 0; zz <= R; ++zz) {
+      const T* c1 = c0 + (zz + 1) * UPL;
+      const T phi = (c1[0] + c1[1]) + (c1[Bu] + c1[Bu + 1]);
+      const T ev = se[zz * EPL + t];
+      sq[zz * EPL + t] = ev != T(0) ? ev * (plo + phi) : T(0);  // absent cells cost no arithmetic
+      plo = phi;
+    }
+  }
+  __syncthreads();
+  double part = 0.0;
+  if (t < PL) {
+    const int x = t % B, y = t / B;
+    const int cu = (y + 1) * Bu + (x + 1), ce = (y + 1) * Be + (x + 1);
+    const T hscale = static_cast<T>(L.h);
+    // cells below the first vertex (lower corner z0 - 1): e/q at (x, y), (x-1, y), (x, y-1), (x-1, y-1)
+    T eb0 = se[ce], eb1 = se[ce - 1], eb2 = se[ce - Be], eb3 = se[ce - Be - 1];
+    T qb0 = sq[ce], qb1 = sq[ce - 1], qb2 = sq[ce - Be], qb3 = sq[ce - Be - 1];
+    T ub = su[cu], u0 = su[UPL + cu];
+#pragma unroll
+    for (int zl = 0; zl < R; ++zl) {
+      const T* uc = su + (zl + 1) * UPL + cu;
+      const T ua = uc[UPL];
+      const T* ea = se + (zl + 1) * EPL + ce;
+      const T* qa = sq + (zl + 1) * EPL + ce;
+      const T ea0 = ea[0], ea1 = ea[-1], ea2 = ea[-Be], ea3 = ea[-Be - 1];
+      const T qa0 = qa[0], qa1 = qa[-1], qa2 = qa[-Be], qa3 = qa[-Be - 1];
+      const int s = (z0 + zl) * PL + t;
+      const int64_t slot = base + s;
+      const uint8_t vf = fv[zl];
+      T res = T(0);
+      if constexpr (OP == kJacobi || OP == kJacobiNorm) {
+        if (vf & MG_V_HANGING) res = u0;
+      }
+      if (is_dof(vf)) {
+        // cell e<bx><by><bz> has lower corner v - (bx, by, bz): a = above (bz 0), b = below
+        const T p00 = ea0 + eb0, p10 = ea1 + eb1, p01 = ea2 + eb2, p11 = ea3 + eb3;
+        const T sxp = p00 + p01, sxm = p10 + p11, syp = p00 + p10, sym = p01 + p11;
+        const T szp = (ea0 + ea1) + (ea2 + ea3), szm = (eb0 + eb1) + (eb2 + eb3);
+        const T sC = sxp + sxm;
+        const T Q = ((qa0 + qa1) + (qa2 + qa3)) + ((qb0 + qb1) + (qb2 + qb3));
+        T s1 = sxp * uc[1];
+        s1 = fma(sxm, uc[-1], s1);
+        s1 = fma(syp, uc[Bu], s1);
+        s1 = fma(sym, uc[-Bu], s1);
+        s1 = fma(szp, ua, s1);
+        s1 = fma(szm, ub, s1);
+        T Au = fma(T(5) * sC, u0, s1 - Q) * (hscale * static_cast<T>(1.0 / 12.0));
+        T D = sC * (hscale * static_cast<T>(1.0 / 3.0));
+        if constexpr (AMODE != 0) {
+#pragma unroll
+          for (int k = 0; k < N3; ++k) {
+            const int off = (k % 3 - 1) + Bu * ((k / 3) % 3 - 1) + UPL * (k / 9 - 1);
+            const T d = load_delta<AMODE, T>(a.ahat, a.ascale, (brick * N3 + k) * L.S + s, slot);
+            Au = fma(d, uc[off], Au);
+            if (k == N3 / 2) D += d;
+          }
+        }
+        const T r = bv[zl] - Au;
+        if constexpr (OP == kJacobi || OP == kJacobiNorm) {
+          res = fma(a.omega * r, recip_nr(D), u0);
+          if constexpr (OP == kJacobiNorm) part += static_cast<double>(r) * static_cast<double>(r);
+        } else {
+          res = r;
+          part += static_cast<double>(r) * static_cast<double>(r);
+        }
+      }
+      a.out[slot] = res;
+      eb0 = ea0; eb1 = ea1; eb2 = ea2; eb3 = ea3;
+      qb0 = qa0; qb1 = qa1; qb2 = qa2; qb3 = qa3;
+      ub = u0;
+      u0 = ua;
+    }
+  }
+  if constexpr (OP == kResidual) {
+    if (a.partial) store_partial_and_finish(part, a.partial, a.counter, a.norm2);
+  }
+}
+
+}  // namespace mg
