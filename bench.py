@@ -60,8 +60,12 @@ ADAPTIVE = {
 }
 
 FP64_PEAK_TFLOPS = 1.25  # nominal dense FP64 of a GB300 (2 FMA / clock / SM at ~2.07 GHz)
-FLOPS_PER_DOF_SWEEP_2D = 35  # FP64 flops per DoF of the finest 2D in-situ Jacobi sweep (division counted once)
-BYTES_PER_DOF_SWEEP_FP64 = 32  # u, b, eps read + u' written, 8 B each
+# FP64 flops per DoF of the finest 2D in-situ Jacobi sweep: 4 pair sums of cell
+# coefficients, 2 x (1 mul + 3 fma) for the edge and corner neighbour sums, 1 mul +
+# 1 fma for the off-diagonal part, b - off, (1 - omega) u and the final fma (an fma
+# counts 2 flops): 4 + 14 + 3 + 1 + 1 + 2
+FLOPS_PER_DOF_SWEEP_2D = 25
+BYTES_PER_DOF_SWEEP_FP64 = 40  # u, b, eps, omega/diag read + u' written, 8 B each
 BYTES_PER_DOF_SWEEP_FP32 = 16
 
 
@@ -140,7 +144,7 @@ def kernel_count(L, c, nu1, nu2, transfer, coarse, precision, cycles, outer, chu
     per_cycle = levels * (nu1 + nu2 + 3) + 1  # sweeps, residual, restrict, prolong per level; coarse solve
     setup = (levels + 1) + levels + levels * ((transfer == "boxmg") + (coarse == "galerkin")) + (levels + 1) + 2
     if precision == "fp64":
-        return setup + 2 + cycles * (per_cycle + 2)
+        return setup + (levels + 1) + 2 + cycles * (per_cycle + 2)  # + the Jacobi factors per level
     setup += (levels + 1) + levels * ((transfer == "boxmg") + (coarse == "galerkin"))
     inner_chunks = max(1, math.ceil(cycles / max(chunk, 1)))
     return setup + 2 + outer * 4 + cycles * per_cycle + inner_chunks * 2
@@ -154,7 +158,7 @@ def kernel_count_adaptive(L, c, nu1, nu2, precision, cycles, outer, chunk):
     res = 4  # residual L, inject, residual t, masked norm
     setup = (L - c + 1) + (L - c) + 2 * (t - c) + (L - c + 1) + 2
     if precision == "fp64":
-        return setup + res + cycles * (cyc + res)
+        return setup + (L - c + 1) + res + cycles * (cyc + res)
     setup += (L - c + 1) + 2 * (t - c)
     inner_chunks = max(1, math.ceil(cycles / max(chunk, 1)))
     return setup + res + outer * (3 + res + 3) + cycles * cyc + inner_chunks * res
@@ -453,17 +457,20 @@ def run_sweeps(args):
     n_dofs = grid.info(L).n_dofs
     eps_dev = torch.from_numpy(grid.cells_to_concat({L: eps})).cuda()
     b64 = torch.from_numpy(grid.to_slots(L, syn.uniform_load(L, d, 1))).cuda()
-    H = mg.Hierarchy(grid, precision="mixed_bf16")
+    H = mg.Hierarchy(grid, precision="mixed_bf16")  # FP32 sweeps
     H.setup(eps_dev)
+    H64 = mg.Hierarchy(grid, precision="fp64") if args.sweep_prec != "fp32" else None
+    if H64 is not None:
+        H64.setup(eps_dev)
     u64 = torch.zeros_like(b64)
     b32 = b64.float()
     u32 = torch.zeros_like(b32)
     hbm, src = peaks()
     out = {"workload": f"sweep{d}d-l{L}", "dofs": n_dofs}
-    for name, fn, u, bb, bpd in (("fp64", H.smooth, u64, b64, BYTES_PER_DOF_SWEEP_FP64),
-                                 ("fp32", H.smooth_f32, u32, b32, BYTES_PER_DOF_SWEEP_FP32)):
+    for name, bpd in (("fp64", BYTES_PER_DOF_SWEEP_FP64), ("fp32", BYTES_PER_DOF_SWEEP_FP32)):
         if args.sweep_prec not in ("both", name):
             continue
+        fn, u, bb = (H64.smooth, u64, b64) if name == "fp64" else (H.smooth_f32, u32, b32)
         for _ in range(3):
             fn(L, u, bb, 2)
         torch.cuda.synchronize()

@@ -31,6 +31,7 @@ struct DevLevel {
   float* pscale = nullptr;
   double *u = nullptr, *b = nullptr, *r = nullptr, *t = nullptr;
   float *u32 = nullptr, *b32 = nullptr, *r32 = nullptr, *t32 = nullptr;
+  double* dinv = nullptr;  // FP64 hierarchies: omega / diag(A) for the Jacobi sweeps
   double* partial = nullptr;
   unsigned* counter = nullptr;
   int64_t n_dofs = 0;

@@ -25,6 +25,7 @@ struct SweepArgs {
   unsigned* counter;    // completion counter for the fused final sum, nullable
   double* norm2;        // fused final sum of r^2 (written by the last CTA), nullable
   int R;                // slab thickness along the last axis (divides B)
+  const T* dinv;        // Jacobi: omega / diag(A) per vertex (setup), nullable
 };
 
 // Deterministic CTA reduction of one double per thread; thread 0 returns the sum.
@@ -196,21 +197,6 @@ __device__ __forceinline__ double sweep_item(const SweepArgs<T>& a, int64_t bric
     se[t] = nb >= 0 ? a.eps[static_cast<int64_t>(nb) * L.S + li] : T(0);
   }
   __syncthreads();
-  // 3D: per cell of the tile q_c = eps_c * (sum of its 8 corner values), shared by
-  // the 8 vertices of the cell (see the vertex formula below)
-  T* sq = se + EPL * (R + 1);
-  if constexpr (DIM == 3) {
-    for (int t = threadIdx.x; t < ne; t += nt) {
-      const int cx = t % Be, cy = (t / Be) % Be, cz = t / EPL;  // tile position of the cell's lower corner
-      const T* c0 = su + (cz * Bu + cy) * Bu + cx;
-      const T s4a = (c0[0] + c0[1]) + (c0[Bu] + c0[Bu + 1]);
-      const T s4b = (c0[UPL] + c0[UPL + 1]) + (c0[UPL + Bu] + c0[UPL + Bu + 1]);
-      const T ev = se[t];
-      sq[t] = ev != T(0) ? ev * (s4a + s4b) : T(0);  // absent cells (eps 0) cost no arithmetic
-    }
-    __syncthreads();
-  }
-
   const T hscale = DIM == 3 ? static_cast<T>(L.h) : T(1);
   double part = 0.0;
   for (int i = threadIdx.x; i < nin; i += nt) {
@@ -229,7 +215,7 @@ __device__ __forceinline__ double sweep_item(const SweepArgs<T>& a, int64_t bric
       const int zl = s / PLANE - z0;
       const int cu = DIM == 2 ? (zl + 1) * Bu + (x + 1) : ((zl + 1) * Bu + (y + 1)) * Bu + (x + 1);
       const int ce = DIM == 2 ? (zl + 1) * Be + (x + 1) : ((zl + 1) * Be + (y + 1)) * Be + (x + 1);
-      T Au, D;
+      T off, D;  // off-diagonal part of (A u)_v and the diagonal of A at v
       if constexpr (DIM == 2) {
         // explicit 2D form: cells sw, se, nw, ne; pair sums of the cells shared with
         // each edge neighbour; corners see one cell
@@ -247,35 +233,53 @@ __device__ __forceinline__ double sweep_item(const SweepArgs<T>& a, int64_t bric
         a2 = fma(e_ne, uc[Bu + 1], a2);
         const T k0 = static_cast<T>(elem_k(2, 0)), k1 = static_cast<T>(elem_k(2, 1)), k2 = static_cast<T>(elem_k(2, 2));
         D = k0 * sC;
-        Au = fma(D, uc[0], fma(k1, a1, k2 * a2));
+        off = fma(k1, a1, k2 * a2);
       } else {
-        // trilinear element matrix eps h {1/3, 0, -1/12, -1/12} by Hamming distance:
-        // within one cell c, (K u)_v = (5/12) u_v - S_c / 12 + E_c(v) / 12 with S_c the
-        // sum of the cell's corner values and E_c(v) that of v's three edge neighbours
-        // in c; summed over the 8 cells around v:
-        //   (A u)_v = h/12 (5 sC u_v - sum_c eps_c S_c + sum_axis nbr n  S_n u_n),
-        // S_n = sum of eps over the 4 cells that contain the edge v-n, sC = sum of eps.
-        const T* ec = se + ce;
-        const T* qc = sq + ce;
-        const T* uc = su + cu;
-        // cell e<bx><by><bz>: lower corner v - (bx, by, bz)
-        const T e000 = ec[0], e100 = ec[-1], e010 = ec[-Be], e110 = ec[-Be - 1];
-        const T e001 = ec[-EPL], e101 = ec[-EPL - 1], e011 = ec[-EPL - Be], e111 = ec[-EPL - Be - 1];
-        const T p00 = e000 + e001, p10 = e100 + e101, p01 = e010 + e011, p11 = e110 + e111;
-        const T sxp = p00 + p01, sxm = p10 + p11, syp = p00 + p10, sym = p01 + p11;
-        const T szp = (e000 + e100) + (e010 + e110), szm = (e001 + e101) + (e011 + e111);
-        const T sC = sxp + sxm;
-        const T Q = ((qc[0] + qc[-1]) + (qc[-Be] + qc[-Be - 1])) +
-                    ((qc[-EPL] + qc[-EPL - 1]) + (qc[-EPL - Be] + qc[-EPL - Be - 1]));
-        T a = sxp * uc[1];
-        a = fma(sxm, uc[-1], a);
-        a = fma(syp, uc[Bu], a);
-        a = fma(sym, uc[-Bu], a);
-        a = fma(szp, uc[UPL], a);
-        a = fma(szm, uc[-UPL], a);
-        const T acc = fma(T(5) * sC, uc[0], a - Q);
-        Au = acc * (hscale * static_cast<T>(1.0 / 12.0));
-        D = sC * (hscale * static_cast<T>(1.0 / 3.0));
+        T acc[DIM + 1];
+#pragma unroll
+        for (int c = 0; c <= DIM; ++c) acc[c] = T(0);
+        T es_centre = T(0);
+#pragma unroll
+        for (int k = 0; k < N3; ++k) {
+          int o[DIM];
+          int ham = 0, kk = k;
+#pragma unroll
+          for (int q = 0; q < DIM; ++q) {
+            o[q] = kk % 3 - 1;
+            kk /= 3;
+            ham += o[q] != 0;
+          }
+          if (elem_k(DIM, ham) == 0.0) continue;
+          T es = T(0);
+#pragma unroll
+          for (int e = 0; e < (1 << DIM); ++e) {
+            bool ok = true;
+            int cidx = ce, m = 1;
+#pragma unroll
+            for (int q = 0; q < DIM; ++q) {
+              const int eq = (e >> q) & 1;
+              const int tq = eq + o[q];
+              ok = ok && tq >= 0 && tq <= 1;
+              cidx -= eq * m;
+              m *= Be;
+            }
+            if (ok) es += se[cidx];
+          }
+          int uidx = cu, m = 1;
+#pragma unroll
+          for (int q = 0; q < DIM; ++q) {
+            uidx += o[q] * m;
+            m *= Bu;
+          }
+          acc[ham] = fma(es, su[uidx], acc[ham]);
+          if (ham == 0) es_centre = es;
+        }
+        off = T(0);
+#pragma unroll
+        for (int c = 1; c <= DIM; ++c)
+          if (elem_k(DIM, c) != 0.0) off = fma(static_cast<T>(elem_k(DIM, c)), acc[c], off);
+        off *= hscale;
+        D = static_cast<T>(elem_k(DIM, 0)) * es_centre * hscale;
       }
       if constexpr (AMODE != 0) {
 #pragma unroll
@@ -288,17 +292,26 @@ __device__ __forceinline__ double sweep_item(const SweepArgs<T>& a, int64_t bric
             m *= Bu;
           }
           const T d = load_delta<AMODE, T>(a.ahat, a.ascale, (brick * N3 + k) * L.S + s, slot);
-          Au = fma(d, su[uidx], Au);
-          if (k == N3 / 2) D += d;
+          if (k == N3 / 2)
+            D += d;
+          else
+            off = fma(d, su[uidx], off);
         }
       }
-      const T r = a.b[slot] - Au;
-      if constexpr (OP == kJacobi || OP == kJacobiNorm) {
-        res = fma(a.omega * r, recip_nr(D), su[cu]);
-        if constexpr (OP == kJacobiNorm) part += static_cast<double>(r) * static_cast<double>(r);
+      const T uv = su[cu];
+      if (OP == kJacobi && a.dinv) {
+        // u + omega (b - D u - off) / D = (1 - omega) u + (omega / D) (b - off), with
+        // omega / D from the setup: no division here (FP64 units are the bound)
+        res = fma(a.dinv[slot], a.b[slot] - off, (T(1) - a.omega) * uv);
       } else {
-        res = r;
-        part += static_cast<double>(r) * static_cast<double>(r);
+        const T r = a.b[slot] - fma(D, uv, off);
+        if constexpr (OP == kJacobi || OP == kJacobiNorm) {
+          res = fma(a.omega * r, recip_nr(D), uv);
+          if constexpr (OP == kJacobiNorm) part += static_cast<double>(r) * static_cast<double>(r);
+        } else {
+          res = r;
+          part += static_cast<double>(r) * static_cast<double>(r);
+        }
       }
     }
     a.out[slot] = res;
@@ -329,13 +342,13 @@ inline int sweep_slab(int, int B, int64_t n_bricks) {
   return R;
 }
 
-// shared memory of one sweep item: the u tile with its halo, the cell coefficients
-// and, in 3D, the per-cell corner sums
+// shared memory of one sweep item: the u tile with its halo and the cell
+// coefficients (cell_sums: the 3D column kernel also keeps per-cell corner sums)
 template <int DIM, typename T>
-inline size_t sweep_tile_bytes(int B, int R) {
+inline size_t sweep_tile_bytes(int B, int R, bool cell_sums = false) {
   const size_t upl = DIM == 2 ? B + 2 : (B + 2) * (B + 2);
   const size_t epl = DIM == 2 ? B + 1 : (B + 1) * (B + 1);
-  return (upl * (R + 2) + epl * (R + 1) * (DIM == 3 ? 2 : 1)) * sizeof(T);
+  return (upl * (R + 2) + epl * (R + 1) * (cell_sums ? 2 : 1)) * sizeof(T);
 }
 
 // slot of integer position x on a level with compile-time brick edge B

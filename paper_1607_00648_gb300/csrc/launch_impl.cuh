@@ -18,7 +18,7 @@ static void sweep_b(SweepArgs<T> a, int op, int amode, cudaStream_t s) {
     // FP32 (issue- and latency-bound): column-marching kernels with the slab depth
     // as a template parameter so every plane's loads are issued together
     const dim3 grid(static_cast<unsigned>(sweep_ctas_x(DIM, B, T(0), a.L.n_bricks)), static_cast<unsigned>(B / R));
-    const size_t sm = DIM == 2 ? 0 : smem;
+    const size_t sm = DIM == 2 ? 0 : sweep_tile_bytes<DIM, T>(B, R, true);
 #define MG_SWR(AM, OP, RR)                                                                \
   do {                                                                                    \
     if constexpr (DIM == 2) k_sweep2c<T, AM, OP, RR><<<grid, 128, 0, s>>>(a);               \

@@ -207,6 +207,30 @@ __global__ void __launch_bounds__(64) k_boxmg(LevelDesc Lc, LevelDesc Lf, const 
   }
 }
 
+// omega / diag(A) per DoF (rediscretised diagonal + stored delta), zero elsewhere:
+// the damped-Jacobi factor of Alg. 1, formed once per setup
+template <int DIM>
+__global__ void __launch_bounds__(kBlock) k_jacobi_dinv(LevelDesc L, const double* eps, const double* ahat,
+                                                          double omega, double* dinv) {
+  const int64_t s = blockIdx.x * static_cast<int64_t>(kBlock) + threadIdx.x;
+  if (s >= L.n_slots) return;
+  int x[DIM];
+  if (!coords_of<DIM>(L, s, x) || !is_dof(L.vflags[s])) {
+    dinv[s] = 0.0;
+    return;
+  }
+  double es = 0.0;
+  for (int e = 0; e < (1 << DIM); ++e) {
+    int c[DIM];
+    for (int i = 0; i < DIM; ++i) c[i] = x[i] - ((e >> i) & 1);
+    const int64_t cs = slot_of<DIM>(L, c);
+    if (cs >= 0) es += eps[cs];
+  }
+  double D = elem_k(DIM, 0) * es * (DIM == 3 ? L.h : 1.0);
+  if (ahat) D += ahat[plane_index(L, s, cpow(3, DIM) / 2, cpow(3, DIM))];
+  dinv[s] = omega / D;
+}
+
 // Galerkin coarse operator A_c = P^T A_f P (Sect. 4.3), one group of kRapTpv
 // threads per coarse vertex V: thread j takes the fine vertex f = 3V + d(j) of the
 // support of P(V, .) (5^d of them), rebuilds f's fine stencil in situ and forms its

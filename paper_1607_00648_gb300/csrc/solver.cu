@@ -403,6 +403,7 @@ static mg_status create(const Grid* g, const mg_options& o, Hier** out) {
     if ((st = dalloc(*H, &D.r, ns)) != MG_OK) return fail(st);
     if ((st = dalloc(*H, &D.t, ns)) != MG_OK) return fail(st);
     if ((st = dalloc(*H, &D.partial, static_cast<size_t>(hl.n_bricks) * hl.B)) != MG_OK) return fail(st);
+    if (!H->mixed && (st = dalloc(*H, &D.dinv, ns)) != MG_OK) return fail(st);
     if ((st = dalloc(*H, &D.counter, 1)) != MG_OK) return fail(st);
     if (l < H->L) {
       if ((st = dalloc(*H, &D.u, ns)) != MG_OK) return fail(st);
@@ -521,7 +522,7 @@ size_t hier_footprint(const Grid& g, const mg_options& o) {
     const HostLevel& hl = g.levels[l];
     const size_t ns = static_cast<size_t>(hl.n_slots), nb = static_cast<size_t>(hl.n_bricks);
     bytes += nb * n3 * 4 + nb * d * 4 + hl.brick_rank.size() * 4 + 2 * ns + ns * full * 12;
-    bytes += 3 * ns * 8 + nb * hl.B * 8 + 4;
+    bytes += 3 * ns * 8 + nb * hl.B * 8 + 4 + (mixed ? 0 : ns * 8);
     if (l < g.L) bytes += 2 * ns * 8;
     if (l < top) bytes += (galerkin ? ns * n3 * 8 : 0) + (boxmg ? ns * n5 * 8 : 0);
     if (mixed) {
@@ -552,6 +553,7 @@ static SweepArgs<T> sweep_args(const Hier& H, int l, const T* u, const T* b, T* 
   *amode = 0;
   if constexpr (std::is_same<T, double>::value) {
     a.eps = D.eps;
+    a.dinv = D.dinv;
     if (coarse) {
       *amode = 1;
       a.ahat = D.ahat;
@@ -716,7 +718,8 @@ static mg_status run_setup(Hier& H, const double* eps_in, cudaStream_t s, bool c
     }
     MG_CHECK(last_launch("setup: BoxMG / Galerkin"));
   }
-  // diagonal audit of every level (Sect. 4.3 definiteness check) and coarsest factor
+  // diagonal audit of every level (Sect. 4.3 definiteness check), Jacobi factors,
+  // coarsest factor
   for (int l = H.c; l <= H.L; ++l) {
     DevLevel& D = H.lv[l];
     const double* ah = (l < H.top && H.galerkin) ? D.ahat : nullptr;
@@ -724,6 +727,12 @@ static mg_status run_setup(Hier& H, const double* eps_in, cudaStream_t s, bool c
       k_export_stencils<2><<<nblk(D.d.n_slots), kBlock, 0, s>>>(D.d, D.eps, ah, nullptr, H.d_status);
     else
       k_export_stencils<3><<<nblk(D.d.n_slots), kBlock, 0, s>>>(D.d, D.eps, ah, nullptr, H.d_status);
+    if (D.dinv) {
+      if (d == 2)
+        k_jacobi_dinv<2><<<nblk(D.d.n_slots), kBlock, 0, s>>>(D.d, D.eps, ah, H.opt.omega, D.dinv);
+      else
+        k_jacobi_dinv<3><<<nblk(D.d.n_slots), kBlock, 0, s>>>(D.d, D.eps, ah, H.opt.omega, D.dinv);
+    }
   }
   {
     DevLevel& C = H.lv[H.c];
