@@ -218,12 +218,17 @@ def run_adaptive(args):
 
     Hmx = mg.Hierarchy(grid, precision="mixed_bf16")
     H64 = mg.Hierarchy(grid, precision="fp64")
+    do64, domx = args.precision in ("both", "fp64"), args.precision in ("both", "mixed")
     with Clocks(torch.cuda.current_device()) as clk:
-        tmx, lmx, rmx = timed(Hmx, "mixed")
-        t64, l64, r64 = timed(H64, "fp64")
+        if domx:
+            tmx, lmx, rmx = timed(Hmx, "mixed")
+        if do64:
+            t64, l64, r64 = timed(H64, "fp64")
     clocks = clk.summary()
+    if not domx:  # FP64 only (profiling runs): the line reports the FP64 solve
+        tmx, lmx, rmx = t64, 0, r64
     value = n_dofs * args.steps / (tmx / 1e3)
-    value64 = n_dofs * args.steps / (t64 / 1e3)
+    value64 = n_dofs * args.steps / (t64 / 1e3) if do64 else None
 
     # dominant kernel of the mixed solve: the FP32 level-L sweep (hanging entries kept)
     nL = grid.info(L).n_slots
@@ -277,9 +282,10 @@ def run_adaptive(args):
                    "level5_dofs": int(nd_L), "inner_cycles": rmx["cycles"], "outer_steps": rmx["outer_steps"],
                    "rel_residual": rmx["rel_residual"], "parallelism": "replicas1",
                    "l2": "flushed (512 MB write) before every timed step", "setup_included": True},
-        "fp64": {"value": value64, "unit": "DoF/s", "ms_per_step": t64 / args.steps, "cycles": r64["cycles"],
-                 "rel_residual": r64["rel_residual"], "mixed_speedup": value / value64},
-        "roofline": roofline, "e2e": e2e, "clocks": clocks, "gpu_launches": lmx + l64,
+        "fp64": None if not (do64 and domx) else {
+            "value": value64, "unit": "DoF/s", "ms_per_step": t64 / args.steps, "cycles": r64["cycles"],
+            "rel_residual": r64["rel_residual"], "mixed_speedup": value / value64},
+        "roofline": roofline, "e2e": e2e, "clocks": clocks, "gpu_launches": lmx + (l64 if do64 else 0),
         "cpu_baseline": None,
     }
     print(json.dumps(out))
@@ -355,12 +361,17 @@ def run_ours(args):
 
     H64 = mg.Hierarchy(grid, transfer=w["transfer"], coarse=w["coarse"], precision="fp64")
     Hmx = mg.Hierarchy(grid, transfer=w["transfer"], coarse=w["coarse"], precision="mixed_bf16")
+    do64, domx = args.precision in ("both", "fp64"), args.precision in ("both", "mixed")
     with Clocks(torch.cuda.current_device()) as clk:
-        t64, launches64, st64 = timed(H64, args.steps, args.warmup, "fp64")
-        tmx, launchesmx, stmx = timed(Hmx, args.steps, args.warmup, "mixed")
+        if do64:
+            t64, launches64, st64 = timed(H64, args.steps, args.warmup, "fp64")
+        if domx:
+            tmx, launchesmx, stmx = timed(Hmx, args.steps, args.warmup, "mixed")
     clocks = clk.summary()
+    if not do64:  # mixed only (profiling runs): the line reports the mixed solve
+        t64, launches64, st64 = tmx, 0, stmx
     value = n_dofs * args.steps * world / (t64 / 1e3)
-    value_mx = n_dofs * args.steps * world / (tmx / 1e3)
+    value_mx = n_dofs * args.steps * world / (tmx / 1e3) if domx else None
 
     # dominant kernel: finest-level FP64 in-situ Jacobi sweep (two sweeps per call, no copy)
     H64.setup(eps_dev)
@@ -424,16 +435,18 @@ def run_ours(args):
             "metric": "DoF/s to 1e-10 residual drop (FP64; mixed beside it)",
             "value": value, "unit": "DoF/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": t64 / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if do64 else "f32 cycles + f64 refinement, bf16 deltas", "data": "synthetic",
             "config": {"workload": args.workload, "description": w["desc"], "dofs": n_dofs,
                        "cycles_per_solve": st64[-1]["cycles"], "parallelism": f"replicas{world}",
                        "l2": "flushed (512 MB write) before every timed step", "setup_included": True},
-            "mixed": {"value": value_mx, "unit": "DoF/s", "dtype": "f32 cycles + f64 refinement, bf16 deltas",
-                      "ms_per_step": tmx / args.steps, "inner_cycles": stmx[-1]["cycles"],
-                      "outer_steps": stmx[-1]["outer_steps"], "rel_residual": stmx[-1]["rel_residual"],
-                      "speedup_vs_fp64": value_mx / value},
+            "mixed": None if not (domx and do64) else {
+                "value": value_mx, "unit": "DoF/s", "dtype": "f32 cycles + f64 refinement, bf16 deltas",
+                "ms_per_step": tmx / args.steps, "inner_cycles": stmx[-1]["cycles"],
+                "outer_steps": stmx[-1]["outer_steps"], "rel_residual": stmx[-1]["rel_residual"],
+                "speedup_vs_fp64": value_mx / value},
             "roofline": roofline, "e2e": e2e, "clocks": clocks,
-            "gpu_launches": launches64 + launchesmx,
+            "gpu_launches": launches64 + (launchesmx if domx else 0),
             "cpu_baseline": cpu,
         }
         print(json.dumps(out))
@@ -687,6 +700,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="checker2d-l6", choices=sorted(WORKLOADS) + sorted(ADAPTIVE))
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline leg")
+    ap.add_argument("--precision", default="both", choices=("both", "fp64", "mixed"),
+                    help="which solve forms to time (profiling runs; the default times both)")
     ap.add_argument("--batched", action="store_true", help="task config 4: batched mixed vs FP64 solves")
     ap.add_argument("--serve", action="store_true", help="task config 5: served 3D requests, p50 / p99 latency")
     ap.add_argument("--serve-requests", type=int, default=300)

@@ -419,13 +419,15 @@ __device__ __forceinline__ void restrict_one(const LevelDesc& Lc, const LevelDes
 // and fine values are read coalesced across a warp), warp j sums taps j, j + 8, ...,
 // and the warps' partial sums are added in warp order (deterministic).  With a slot
 // list (composite grid: the refined coarse DoFs) lane i serves list[32*blockIdx + i]
-// and other coarse slots are not written.
+// and other coarse slots are not written.  zero_c (nullable): a coarse vector set to
+// zero at every slot served (the coarse correction's initial guess), so the cycle
+// needs no separate memset.
 constexpr int kRestrictWarps = 8;
 
 template <int DIM, typename T, int PMODE, int BC, int BF>
 __global__ void __launch_bounds__(32 * kRestrictWarps)
     k_restrict(LevelDesc Lc, LevelDesc Lf, const T* rf, T* bc, const void* phat, const float* pscale,
-               const int32_t* list, int64_t n_list) {
+               const int32_t* list, int64_t n_list, T* zero_c) {
   constexpr int N5 = cpow(5, DIM);
   __shared__ T part[kRestrictWarps][32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -461,6 +463,7 @@ __global__ void __launch_bounds__(32 * kRestrictWarps)
 #pragma unroll
     for (int j = 1; j < kRestrictWarps; ++j) t += part[j][lane];
     bc[cs] = dof ? t : T(0);
+    if (zero_c) zero_c[cs] = T(0);
   }
 }
 
@@ -564,6 +567,6 @@ void launch_sweep(SweepArgs<T> a, int op, int amode, cudaStream_t s);
 template <int DIM, typename T>
 void launch_transfer(const LevelDesc& Lc, const LevelDesc& Lf, bool restrict_op, int pmode, const T* in, T* out,
                      const void* phat, const float* pscale, cudaStream_t s, const int32_t* list = nullptr,
-                     int64_t n_list = 0);
+                     int64_t n_list = 0, T* zero_c = nullptr);
 
 }  // namespace mg

@@ -62,7 +62,8 @@ static void sweep_b(SweepArgs<T> a, int op, int amode, cudaStream_t s) {
 
 template <int DIM, typename T, int BC, int BF>
 static void transfer_b(const LevelDesc& Lc, const LevelDesc& Lf, bool restrict_op, int pmode, const T* in, T* out,
-                       const void* ph, const float* ps, cudaStream_t s, const int32_t* li, int64_t nl) {
+                       const void* ph, const float* ps, cudaStream_t s, const int32_t* li, int64_t nl,
+                       T* zc) {
   const int64_t nc = li ? nl : Lc.n_slots, nf = li ? nl : Lf.n_slots;
   const unsigned gc = static_cast<unsigned>((nc + 31) / 32);
   const unsigned gf = static_cast<unsigned>((nf + kBlock - 1) / kBlock);
@@ -70,7 +71,7 @@ static void transfer_b(const LevelDesc& Lc, const LevelDesc& Lf, bool restrict_o
 #define MG_TR(PM)                                                                                   \
   do {                                                                                              \
     if (restrict_op)                                                                                \
-      k_restrict<DIM, T, PM, BC, BF><<<gc, 32 * kRestrictWarps, 0, s>>>(Lc, Lf, in, out, ph, ps, li, nl); \
+      k_restrict<DIM, T, PM, BC, BF><<<gc, 32 * kRestrictWarps, 0, s>>>(Lc, Lf, in, out, ph, ps, li, nl, zc); \
     else                                                                                            \
       k_prolong<DIM, T, PM, BC, BF><<<gf, kBlock, 0, s>>>(Lc, Lf, in, out, ph, ps, li, nl);         \
   } while (0)
@@ -97,9 +98,9 @@ static void transfer_b(const LevelDesc& Lc, const LevelDesc& Lf, bool restrict_o
   template <>                                                                                               \
   void launch_transfer<DIM, T>(const LevelDesc& Lc, const LevelDesc& Lf, bool r, int pmode, const T* in,     \
                                T* out, const void* ph, const float* ps, cudaStream_t s, const int32_t* li,  \
-                               int64_t nl) {                                                                \
-    if (Lc.B == 3 && Lf.B == 9) transfer_b<DIM, T, 3, 9>(Lc, Lf, r, pmode, in, out, ph, ps, s, li, nl);      \
-    else if (Lc.B == 9 && Lf.B == 9) transfer_b<DIM, T, 9, 9>(Lc, Lf, r, pmode, in, out, ph, ps, s, li, nl); \
+                               int64_t nl, T* zc) {                                                         \
+    if (Lc.B == 3 && Lf.B == 9) transfer_b<DIM, T, 3, 9>(Lc, Lf, r, pmode, in, out, ph, ps, s, li, nl, zc);  \
+    else if (Lc.B == 9 && Lf.B == 9) transfer_b<DIM, T, 9, 9>(Lc, Lf, r, pmode, in, out, ph, ps, s, li, nl, zc); \
     else MG_TRANSFER_27(DIM, T)                                                                             \
   }                                                                                                         \
   }

@@ -591,7 +591,7 @@ static void sweep(const Hier& H, int l, int op, const T* u, const T* b, T* out, 
 
 template <typename T>
 static void transfer(const Hier& H, int fine, bool restrict_op, const T* in, T* out, cudaStream_t s,
-                     const int32_t* list = nullptr, int64_t n_list = 0) {
+                     const int32_t* list = nullptr, int64_t n_list = 0, T* zero_c = nullptr) {
   const DevLevel& F = H.lv[fine];
   const DevLevel& C = H.lv[fine - 1];
   int pmode = 0;
@@ -608,9 +608,9 @@ static void transfer(const Hier& H, int fine, bool restrict_op, const T* in, T* 
     }
   }
   if (H.dim == 2)
-    launch_transfer<2, T>(C.d, F.d, restrict_op, pmode, in, out, ph, ps, s, list, n_list);
+    launch_transfer<2, T>(C.d, F.d, restrict_op, pmode, in, out, ph, ps, s, list, n_list, zero_c);
   else
-    launch_transfer<3, T>(C.d, F.d, restrict_op, pmode, in, out, ph, ps, s, list, n_list);
+    launch_transfer<3, T>(C.d, F.d, restrict_op, pmode, in, out, ph, ps, s, list, n_list, zero_c);
 }
 
 template <typename T>
@@ -658,8 +658,7 @@ static void vcycle(Hier& H, int l, T* u, const T* b, cudaStream_t s) {
   T* bc = lvec<T>(H, l - 1, 1);
   smooth<T>(H, l, u, b, tmp, H.opt.nu1, s);
   sweep<T>(H, l, kResidual, u, b, r, nullptr, s);
-  transfer<T>(H, l, true, r, bc, s);
-  cudaMemsetAsync(uc, 0, H.lv[l - 1].d.n_slots * sizeof(T), s);
+  transfer<T>(H, l, true, r, bc, s, nullptr, 0, uc);  // also zeroes the coarse correction uc
   vcycle<T>(H, l - 1, uc, bc, s);
   transfer<T>(H, l, false, uc, u, s);
   smooth<T>(H, l, u, b, tmp, H.opt.nu2, s);
@@ -692,7 +691,6 @@ static mg_status run_setup(Hier& H, const double* eps_in, cudaStream_t s, bool c
     DevLevel& F = H.lv[l];
     DevLevel& C = H.lv[l - 1];
     const double* ahat_f = (l < H.top && H.galerkin) ? F.ahat : nullptr;
-    const unsigned gb = static_cast<unsigned>((C.d.n_slots + 127) / 128);
     if (H.boxmg) {
       const unsigned gp = static_cast<unsigned>(((C.d.n_slots << d) + 63) / 64);
       if (d == 2)
