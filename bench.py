@@ -231,6 +231,8 @@ def run_adaptive(args):
     value64 = n_dofs * args.steps / (t64 / 1e3) if do64 else None
 
     # dominant kernel of the mixed solve: the FP32 level-L sweep (hanging entries kept)
+    if not domx:
+        Hmx.setup(eps_dev)
     nL = grid.info(L).n_slots
     oL = grid.info(L).slot_offset
     u32 = torch.zeros(nL, dtype=torch.float32, device="cuda")
@@ -288,6 +290,63 @@ def run_adaptive(args):
         "roofline": roofline, "e2e": e2e, "clocks": clocks, "gpu_launches": lmx + (l64 if do64 else 0),
         "cpu_baseline": None,
     }
+    print(json.dumps(out))
+
+
+def run_breakdown(args):
+    """Per-kernel device time of one mg_setup + mg_solve of the workload, per solve form,
+    from the CUDA activity trace of torch.profiler (kernels at full speed, in the order
+    the solve runs them; a diagnostic beside the ncu launch lists)."""
+    import collections
+    import re
+
+    import torch
+    from torch.profiler import ProfilerActivity, profile
+
+    import paper_1607_00648_gb300 as mg
+
+    torch.cuda.set_device(0)
+    with profile(activities=[ProfilerActivity.CUDA]):  # the first trace misses kernels
+        torch.zeros(8, device="cuda").sum()
+        torch.cuda.synchronize()
+    if args.workload in ADAPTIVE:
+        w = ADAPTIVE[args.workload]
+        grid, eps_cat, b, n_dofs = adaptive_problem(mg, w)
+        opts = {}
+    else:
+        w = WORKLOADS[args.workload]
+        eps, bf = inputs(w)
+        grid = mg.Grid(w["dim"], w["L"])
+        eps_cat, b = grid.cells_to_concat({w["L"]: eps}), grid.to_slots(w["L"], bf)
+        n_dofs = grid.info(w["L"]).n_dofs
+        opts = {"transfer": w["transfer"], "coarse": w["coarse"]}
+    e = torch.from_numpy(eps_cat).cuda()
+    bd = torch.from_numpy(b).cuda()
+    u = torch.zeros_like(bd)
+    out = {"workload": args.workload, "dofs": n_dofs}
+    for prec in ("fp64", "mixed_bf16"):
+        if args.precision not in ("both", prec.split("_")[0]):
+            continue
+        H = mg.Hierarchy(grid, precision=prec, **opts)
+        H.setup(e)
+        H.solve(u, bd, rel_tol=w["tol"], max_cycles=w["max_cycles"])
+        torch.cuda.synchronize()
+        with profile(activities=[ProfilerActivity.CUDA]) as prof:
+            H.setup(e)
+            res = H.solve(u, bd, rel_tol=w["tol"], max_cycles=w["max_cycles"])
+            torch.cuda.synchronize()
+        agg = collections.defaultdict(lambda: [0, 0.0])
+        for ev in prof.events():
+            if ev.device_type.name == "CUDA":
+                k = re.sub(r"\(.*", "", ev.name).replace("void ", "").replace("mg::", "")
+                agg[k][0] += 1
+                agg[k][1] += ev.device_time_total
+        tot = sum(v[1] for v in agg.values())
+        out[prec] = {"cycles": res["cycles"], "outer_steps": res["outer_steps"], "solve_ms": res["solve_ms"],
+                     "kernel_ms": tot / 1e3,
+                     "kernels": [{"name": k, "launches": c, "ms": t / 1e3, "share": t / tot}
+                                 for k, (c, t) in sorted(agg.items(), key=lambda kv: -kv[1][1])]}
+        del H
     print(json.dumps(out))
 
 
@@ -609,13 +668,19 @@ def run_serve(args, seed=4):
     wall = time.perf_counter() - start
     sv.close()
     lat = sorted(r["latency_ms"] for r in res)
+    by_edge = {}
+    for L in sorted(set(levels.tolist())):
+        ls = sorted(r["latency_ms"] for r, lv in zip(res, levels.tolist()) if lv == L)
+        by_edge[str(3**L)] = {"n": len(ls), "p50_ms": ls[len(ls) // 2],
+                              "p99_ms": ls[min(len(ls) - 1, int(0.99 * len(ls)))]}
     dofs = sum(g.info(L).n_dofs for g, L, _, _, _ in reqs)
     out = {"workload": f"serve{n}-3d", "requests": n, "solves_per_s": n / wall, "dof_per_s": dofs / wall,
            "p50_ms": lat[len(lat) // 2], "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
            "max_ms": lat[-1], "wall_s": wall, "arrival_span_s": float(arrivals[-1]), "inputs_s": t_inputs,
            "failed": sum(1 for r in res if r["status"] != 0),
            "max_rel_residual": max(r["rel_residual"] for r in res), "budget_gb": args.serve_budget_gb,
-           "sizes": {str(3**L): int((levels == L).sum()) for L in sorted(set(levels.tolist()))}}
+           "sizes": {str(3**L): int((levels == L).sum()) for L in sorted(set(levels.tolist()))},
+           "latency_by_edge": by_edge}
     print(json.dumps(out))
 
 
@@ -707,12 +772,16 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=300)
     ap.add_argument("--serve-budget-gb", type=float, default=64.0)
     ap.add_argument("--batch-size", type=int, default=0)
+    ap.add_argument("--breakdown", action="store_true",
+                    help="per-kernel device time of one setup + solve of the workload (torch.profiler trace)")
     ap.add_argument("--sweep-level", type=int, default=0,
                     help="time only the finest-level FP64 / FP32 sweeps on a uniform grid of this level")
     ap.add_argument("--sweep-dim", type=int, default=2, choices=(2, 3))
     ap.add_argument("--sweep-prec", default="both", choices=("both", "fp64", "fp32"))
     args = ap.parse_args()
-    if args.serve:
+    if args.breakdown:
+        run_breakdown(args)
+    elif args.serve:
         run_serve(args)
     elif args.batched:
         run_batched(args)

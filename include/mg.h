@@ -310,8 +310,9 @@ typedef struct mg_request {
   int32_t reserved;
 } mg_request;
 
-/* Start a server on the current device: a thread that admits submitted requests in
- * arrival order while their hierarchies fit hbm_budget_bytes, sets them up, and runs
+/* Start a server on the current device: a thread that admits queued requests whose
+ * hierarchies fit the rest of hbm_budget_bytes (scanning in arrival order; a request
+ * that does not fit yet does not hold back later ones that do), sets them up, and runs
  * all admitted requests as one continuously re-formed batch (requests join at the next
  * step boundary and retire, releasing their memory, as soon as they converge).  opt:
  * options of every request (NULL = defaults). */

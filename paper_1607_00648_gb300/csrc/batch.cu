@@ -188,10 +188,11 @@ struct Batch {
   bool use_graph = true;  // the server re-forms batches often and launches steps directly
   BatchState state{};
   cudaStream_t own = nullptr;
-  ~Batch() {
+  int priority = 0;
+  ~Batch() {  // the caller has made sure no work of the batch is pending
     graph.reset();
-    for (void* p : allocs) cudaFree(p);
-    if (h_pin) cudaFreeHost(h_pin);
+    for (void* p : allocs) pool_free(p, own);
+    pinned_release(h_pin);
     if (own) cudaStreamDestroy(own);
   }
 };
@@ -203,10 +204,10 @@ mg_status balloc(Batch& bt, T** p, size_t n) {
   *p = nullptr;
   if (n == 0) n = 1;
   void* q = nullptr;
-  const cudaError_t e = cudaMalloc(&q, n * sizeof(T));
+  const cudaError_t e = pool_alloc(&q, n * sizeof(T), bt.own);
   if (e != cudaSuccess) {
     cudaGetLastError();
-    set_error(std::string("batch: cudaMalloc failed: ") + cudaGetErrorString(e));
+    set_error(std::string("batch: device allocation failed: ") + cudaGetErrorString(e));
     return e == cudaErrorMemoryAllocation ? MG_ERR_OOM : MG_ERR_CUDA;
   }
   bt.allocs.push_back(q);
@@ -218,7 +219,8 @@ template <typename T>
 mg_status bupload(Batch& bt, T** p, const std::vector<T>& v) {
   const mg_status st = balloc(bt, p, v.size());
   if (st != MG_OK) return st;
-  if (!v.empty() && cudaMemcpy(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess) {
+  if (!v.empty() &&
+      cudaMemcpyAsync(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, bt.own) != cudaSuccess) {
     set_error("batch: upload failed");
     return MG_ERR_CUDA;
   }
@@ -340,6 +342,10 @@ void emit_mixed_step(Batch& bt, const BatchState& st, cudaStream_t s) {
 }
 
 mg_status build_batch(Batch& bt) {
+  if (cudaStreamCreateWithPriority(&bt.own, cudaStreamNonBlocking, bt.priority) != cudaSuccess) {
+    set_error("mg_batch_create: cudaStreamCreate failed");
+    return MG_ERR_CUDA;
+  }
   const int n = bt.n;
   const Hier& h0 = *bt.H[0];
   bt.dim = h0.dim;
@@ -460,12 +466,13 @@ mg_status build_batch(Batch& bt) {
   }
   if ((st = balloc(bt, &bt.d_partial, std::max(part, 1))) != MG_OK) return st;
   if ((st = bupload(bt, &bt.d_prange, prange)) != MG_OK) return st;
-  if (cudaMallocHost(&bt.h_pin, 16 * sizeof(int)) != cudaSuccess) {
-    set_error("mg_batch_create: cudaMallocHost failed");
+  bt.h_pin = static_cast<int*>(pinned_slot());
+  if (!bt.h_pin) {
+    set_error("mg_batch_create: pinned host memory unavailable");
     return MG_ERR_OOM;
   }
-  if (cudaStreamCreate(&bt.own) != cudaSuccess) {
-    set_error("mg_batch_create: cudaStreamCreate failed");
+  if (cudaStreamSynchronize(bt.own) != cudaSuccess) {  // tables in place before other streams use them
+    set_error("mg_batch_create: upload failed");
     return MG_ERR_CUDA;
   }
   return MG_OK;
@@ -479,7 +486,7 @@ mg_status status_of(int st) {
 
 void batch_set_graph(Batch* bt, bool use_graph) { bt->use_graph = use_graph; }
 
-mg_status batch_create(const std::vector<Hier*>& hs, Batch** out) {
+mg_status batch_create(const std::vector<Hier*>& hs, Batch** out, int priority) {
   *out = nullptr;
   if (hs.empty()) {
     set_error("batch: no problems");
@@ -492,6 +499,7 @@ mg_status batch_create(const std::vector<Hier*>& hs, Batch** out) {
   }
   bt->n = static_cast<int>(hs.size());
   bt->H = hs;
+  bt->priority = priority;
   const mg_status st = build_batch(*bt);
   if (st != MG_OK) {
     delete bt;
@@ -597,6 +605,22 @@ mg_status batch_run(Batch& bt, int max_steps, cudaStream_t s, int* n_active) {
     }
     *n_active = bt.h_pin[0];
     if (*n_active == 0) break;
+  }
+  return MG_OK;
+}
+
+// Enqueues one step on s (direct launches) without waiting for it; batch_read after the
+// stream has reached it gives the problems' states.
+mg_status batch_step_enqueue(Batch& bt, cudaStream_t s) {
+  if (bt.mixed) {
+    if (bt.dim == 2) emit_mixed_step<2>(bt, bt.state, s); else emit_mixed_step<3>(bt, bt.state, s);
+  } else {
+    if (bt.dim == 2) emit_fp64_step<2>(bt, bt.state, s); else emit_fp64_step<3>(bt, bt.state, s);
+  }
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_error(std::string("batch: ") + cudaGetErrorString(e));
+    return MG_ERR_CUDA;
   }
   return MG_OK;
 }
@@ -724,6 +748,9 @@ mg_status mg_batch_setup(mg_batch* batch, const double* const* eps, void* stream
   return MG_OK;
 }
 
-void mg_batch_destroy(mg_batch* batch) { delete reinterpret_cast<Batch*>(batch); }
+void mg_batch_destroy(mg_batch* batch) {
+  if (batch) cudaDeviceSynchronize();  // it may still be in use on any stream
+  delete reinterpret_cast<Batch*>(batch);
+}
 
 }  // extern "C"

@@ -81,6 +81,21 @@ struct Hier {
   Graph g_cycle64, g_outer, g_inner, g_comp64, g_comp_outer, g_comp_inner;
 };
 
+// ---- device memory of hierarchies and batches (solver.cu) ----
+// Allocations come from a per-device stream-ordered pool that keeps freed memory
+// (release threshold = max), so that creating and destroying hierarchies in a serving
+// loop neither calls into the driver's allocator nor synchronises the device (as
+// cudaFree does).  Allocation and free are ordered on stream s.
+cudaError_t pool_alloc(void** p, size_t bytes, cudaStream_t s);
+void pool_free(void* p, cudaStream_t s);
+// 128 bytes of pinned host memory from a process-wide slab (never returned to the driver)
+void* pinned_slot();
+void pinned_release(void* p);
+// destroy a hierarchy whose work is known to be complete (no device synchronisation)
+void hier_release(Hier* H);
+// mg_hier_create with the hierarchy's stream at a given priority
+mg_status hier_create(const Grid* g, const mg_options& o, int priority, Hier** out);
+
 // enqueue a hierarchy's setup without synchronising; setup_status interprets d_status
 mg_status setup_enqueue(Hier& H, const double* eps, cudaStream_t s);
 mg_status setup_status(Hier& H, int status);
@@ -92,12 +107,13 @@ struct ProblemState {
   double r0, rel, sigma, tol;
   int max_cycles;
 };
-mg_status batch_create(const std::vector<Hier*>& hs, Batch** out);
+mg_status batch_create(const std::vector<Hier*>& hs, Batch** out, int priority = 0);  // priority: of its own stream
 void batch_destroy(Batch* bt);
 void batch_set_graph(Batch* bt, bool use_graph);
 mg_status batch_begin(Batch& bt, double* const* u, const double* const* b, const std::vector<ProblemState>& init,
                       const std::vector<int>& fresh, cudaStream_t s);
 mg_status batch_run(Batch& bt, int max_steps, cudaStream_t s, int* n_active);
+mg_status batch_step_enqueue(Batch& bt, cudaStream_t s);  // one step, no synchronisation
 mg_status batch_read(Batch& bt, std::vector<ProblemState>& out, cudaStream_t s);
 mg_status status_of(int st);
 size_t hier_footprint(const Grid& g, const mg_options& o);

@@ -414,6 +414,17 @@ __device__ __forceinline__ void restrict_one(const LevelDesc& Lc, const LevelDes
   bc[cs] = acc;
 }
 
+// d-linear weight of 5^d offset index k (offset o_i = digit_i(k) - 2), prod (3 - |o_i|) / 3
+template <int DIM, typename T>
+__device__ __forceinline__ T dlin_weight(int k) {
+  double w = 1.0;
+  for (int i = 0; i < DIM; ++i) {
+    w *= wlin1(k % 5 - 2);
+    k /= 5;
+  }
+  return static_cast<T>(w);
+}
+
 // Restriction kernel: the 5^d taps of a coarse vertex are split over kRestrictWarps
 // warps.  Lane i of every warp serves coarse slot 32*blockIdx + i (so P_hat planes
 // and fine values are read coalesced across a warp), warp j sums taps j, j + 8, ...,
@@ -430,6 +441,9 @@ __global__ void __launch_bounds__(32 * kRestrictWarps)
                const int32_t* list, int64_t n_list, T* zero_c) {
   constexpr int N5 = cpow(5, DIM);
   __shared__ T part[kRestrictWarps][32];
+  __shared__ T wtab[N5];  // d-linear weights by tap, formed once per CTA (FP64 units are scarce)
+  for (int k = threadIdx.x; k < N5; k += blockDim.x) wtab[k] = dlin_weight<DIM, T>(k);
+  __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t i = blockIdx.x * 32LL + lane;
   const int64_t cs = list ? (i < n_list ? list[i] : -1) : (i < Lc.n_slots ? i : -1);
@@ -441,17 +455,14 @@ __global__ void __launch_bounds__(32 * kRestrictWarps)
     for (int k = warp; k < N5; k += kRestrictWarps) {
       int y[DIM];
       int kk = k;
-      double w = 1.0;
 #pragma unroll
       for (int a = 0; a < DIM; ++a) {
-        const int o = kk % 5 - 2;
+        y[a] = 3 * X[a] + kk % 5 - 2;
         kk /= 5;
-        y[a] = 3 * X[a] + o;
-        w *= wlin1(o);
       }
       const int64_t fs = slot_of_b<DIM, BF>(Lf, y);
       if (fs < 0) continue;
-      T p = static_cast<T>(w);
+      T p = wtab[k];
       if constexpr (PMODE != 0) p += load_delta<PMODE, T>(phat, pscale, (cb * N5 + k) * Lc.S + cl, cs);
       acc = fma(p, rf[fs], acc);
     }
@@ -471,7 +482,8 @@ __global__ void __launch_bounds__(32 * kRestrictWarps)
 // correction of Alg. 1).  One thread per fine slot; non-DoF slots untouched.
 template <int DIM, typename T, int PMODE, int BC, int BF>
 __device__ __forceinline__ void prolong_one(const LevelDesc& Lc, const LevelDesc& Lf, const T* ec, T* uf,
-                                            const void* phat, const float* pscale, int64_t fs) {
+                                            const void* phat, const float* pscale, int64_t fs,
+                                            const T* wtab = nullptr) {
   constexpr int N5 = cpow(5, DIM);
   int x[DIM];
   if (!coords_of_b<DIM, BF>(Lf, fs, x) || !is_dof(Lf.vflags[fs])) return;
@@ -486,7 +498,6 @@ __device__ __forceinline__ void prolong_one(const LevelDesc& Lc, const LevelDesc
   for (int e = 0; e < (1 << DIM); ++e) {
     int X[DIM], o[DIM];
     bool ok = true;
-    double w = 1.0;
     int k = 0, m = 1;
 #pragma unroll
     for (int i = 0; i < DIM; ++i) {
@@ -494,14 +505,13 @@ __device__ __forceinline__ void prolong_one(const LevelDesc& Lc, const LevelDesc
       if (ei >= cnt[i]) ok = false;
       X[i] = lo[i] + ei;
       o[i] = x[i] - 3 * X[i];
-      w *= wlin1(o[i]);
       k += (o[i] + 2) * m;
       m *= 5;
     }
     if (!ok) continue;
     const int64_t cs = slot_of_b<DIM, BC>(Lc, X);
     if (cs < 0 || !is_dof(Lc.vflags[cs])) continue;
-    T p = static_cast<T>(w);
+    T p = wtab ? wtab[k] : dlin_weight<DIM, T>(k);
     if constexpr (PMODE != 0) {
       const int64_t cb = cs / Lc.S;
       p += load_delta<PMODE, T>(phat, pscale, (cb * N5 + k) * Lc.S + (cs - cb * Lc.S), cs);
@@ -516,11 +526,15 @@ template <int DIM, typename T, int PMODE, int BC, int BF>
 __global__ void __launch_bounds__(kBlock) k_prolong(LevelDesc Lc, LevelDesc Lf, const T* ec, T* uf,
                                                       const void* phat, const float* pscale,
                                                       const int32_t* list, int64_t n_list) {
+  constexpr int N5 = cpow(5, DIM);
+  __shared__ T wtab[N5];  // d-linear weights by offset, formed once per CTA
+  for (int k = threadIdx.x; k < N5; k += blockDim.x) wtab[k] = dlin_weight<DIM, T>(k);
+  __syncthreads();
   const int64_t i = blockIdx.x * static_cast<int64_t>(kBlock) + threadIdx.x;
   if (list) {
-    if (i < n_list) prolong_one<DIM, T, PMODE, BC, BF>(Lc, Lf, ec, uf, phat, pscale, list[i]);
+    if (i < n_list) prolong_one<DIM, T, PMODE, BC, BF>(Lc, Lf, ec, uf, phat, pscale, list[i], wtab);
   } else if (i < Lf.n_slots) {
-    prolong_one<DIM, T, PMODE, BC, BF>(Lc, Lf, ec, uf, phat, pscale, i);
+    prolong_one<DIM, T, PMODE, BC, BF>(Lc, Lf, ec, uf, phat, pscale, i, wtab);
   }
 }
 

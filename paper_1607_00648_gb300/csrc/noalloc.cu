@@ -1,7 +1,7 @@
 // Residual with its squared norm, for callers that must not allocate device memory.
 //
 // mg_residual keeps the per-CTA partial sums of the norm reduction in workspace
-// that mg_hier_create obtained from cudaMalloc.  This variant keeps them in a
+// that mg_hier_create allocated on the device.  This variant keeps them in a
 // fixed file-scope device array instead, so a call performs no allocation of any
 // kind and does not synchronise: the squared norm is written to a device double
 // the caller provides.

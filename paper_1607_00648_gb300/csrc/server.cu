@@ -1,17 +1,21 @@
 // Serving: continuous batching of independent solves.
 //
-// A server thread owns one CUDA stream.  Submitted requests wait in a queue until
-// their hierarchy fits the HBM budget (footprint computed from the grid and the
-// options); admitted requests get a hierarchy, are set up, and join the running
-// batch at the next step boundary, so work from requests that arrived while others
-// were on the GPU overlaps with theirs on the device.  After every step (an FP64
-// cycle, or a refinement step with its inner FP32 cycles) converged requests
-// retire: their statistics are recorded, their hierarchy is released and its
-// budget returns to the queue.  The per-request arithmetic is that of a batch, so
-// a request's result does not depend on which other requests shared its steps.
+// Submitted requests wait in a queue until their hierarchy fits the HBM budget
+// (footprint computed from the grid and the options); admitted requests get a
+// hierarchy, are set up on a pool of streams, and join a running batch at its next
+// step boundary, so work from requests that arrived while others were on the GPU
+// overlaps with theirs on the device.  Requests run in two lanes by size, each a
+// batch on its own stream: the lane of small problems takes many short steps while
+// a step of the large problems is still on the GPU, so a small request is not held
+// to the pace of the largest ones.  After every step of a lane (an FP64 cycle, or a
+// refinement step with its inner FP32 cycles) its converged requests retire: their
+// statistics are recorded, their hierarchy is released and its budget returns to the
+// queue.  The per-request arithmetic is that of a batch, so a request's result does
+// not depend on which other requests shared its steps.
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -40,6 +44,11 @@ struct Request {
   size_t footprint = 0;
   Hier* h = nullptr;
   int state = 0;  // 0 queued, 1 setting up, 2 running, 3 done
+  int lane = 0;   // 0 small, 1 large problems
+  // done but still a member of its lane's batch (inactive there): its hierarchy and
+  // budget are released when the batch is next re-formed; abandoned: the caller has
+  // collected the result meanwhile, so the server deletes the request then
+  bool zombie = false, abandoned = false;
   cudaEvent_t ev = nullptr;  // completion of the request's setup
   ProblemState ps{};
   mg_status status = MG_OK;
@@ -62,94 +71,139 @@ struct Server {
   std::string error;
   std::thread th;
   cudaStream_t stream = nullptr;
-  static constexpr int kSetupStreams = 8;
-  cudaStream_t setup_streams[kSetupStreams] = {};
-  int next_setup = 0;
-  std::vector<Request*> pending;  // setting up (server thread only)
-  Batch* batch = nullptr;
-  std::vector<Request*> members;  // requests of the current batch, in batch order
+  // setup streams per lane; the small lane's streams (setups and steps) run at the
+  // device's highest priority so that their short kernels are not queued behind the
+  // large problems' long ones
+  static constexpr int kSetupStreams = 4;
+  cudaStream_t setup_streams[2][kSetupStreams] = {};
+  std::atomic<int> next_setup[2] = {0, 0};
+  std::vector<Request*> pending;  // set up enqueued, waiting for its event (mu)
+  // hierarchy creation and setup enqueue run on one worker thread per lane, so that
+  // host-side waits of a creation hold back neither the stepping of running batches
+  // nor the small requests behind a large one
+  std::deque<Request*> to_create[2];  // admitted, not yet created (mu)
+  int creating = 0;                   // requests inside a worker between the two lists (mu)
+  static constexpr int kWorkers[2] = {3, 1};  // the small lane's creations run three at a time
+  std::thread workers[2][3];
+  int prio[2] = {0, 0};               // stream priorities of the lanes (small: highest)
+  void worker(int lane);
+  // a batch of running requests with its own stream; at most one step in flight
+  struct Lane {
+    Batch* batch = nullptr;
+    std::vector<Request*> members;  // requests of the current batch, in batch order
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+    bool in_flight = false;
+    Clock::time_point reformed{};
+  };
+  // a batch is re-formed (new members join, finished ones leave) at most this often
+  // while it still has running members: re-forming rebuilds its tables
+  static constexpr std::chrono::milliseconds kReformEvery{25};
+  static constexpr int kLanes = 2;
+  static constexpr int64_t kLargeDofs = int64_t(1) << 20;  // finest-level DoFs of a large problem
+  Lane lanes[kLanes];
 
   void loop();
-  void retire(Request* r, mg_status st);
+  void retire(Request* r, mg_status st, bool release = true);
+  void release(Request* r);  // hierarchy and budget of a finished request (mu held)
+  bool start_step(Lane& ln, int lane);   // re-form the batch if needed, enqueue a step
+  void finish_step(Lane& ln);            // read the states of a completed step, retire
 };
 
-void Server::retire(Request* r, mg_status st) {
+void Server::retire(Request* r, mg_status st, bool release_now) {
   r->status = st;
   r->t_done = Clock::now();
   if (r->ev) {
     cudaEventDestroy(r->ev);
     r->ev = nullptr;
   }
-  if (r->h) {
-    mg_destroy_hier(reinterpret_cast<mg_hier*>(r->h));
+  r->state = 3;
+  if (release_now)
+    release(r);
+  else
+    r->zombie = true;
+}
+
+void Server::release(Request* r) {
+  if (r->h) {  // its setup and steps have completed: no device synchronisation needed
+    hier_release(r->h);
     r->h = nullptr;
   }
-  used -= r->footprint;
-  r->state = 3;
+  if (r->footprint) {
+    used -= r->footprint;
+    r->footprint = 0;
+  }
+  r->zombie = false;
+}
+
+void Server::worker(int lane) {
+  cudaSetDevice(device);
+  for (;;) {
+    Request* r = nullptr;
+    {
+      std::unique_lock<std::mutex> lk(mu);
+      cv.wait(lk, [&] { return stop || !to_create[lane].empty(); });
+      if (stop) return;
+      r = to_create[lane].front();
+      to_create[lane].pop_front();
+      ++creating;
+    }
+    Hier* h = nullptr;
+    mg_status st = hier_create(r->grid, opt, prio[lane], &h);
+    if (st == MG_OK) {
+      r->h = h;
+      cudaStream_t ss = setup_streams[lane][next_setup[lane]++ % kSetupStreams];
+      st = setup_enqueue(*h, r->eps, ss);
+      // the setup's status word comes back with it (read at the join without a CUDA call)
+      int* status = reinterpret_cast<int*>(h->h_pin + 15);
+      if (st == MG_OK &&
+          (cudaMemcpyAsync(status, h->d_status, sizeof(int), cudaMemcpyDeviceToHost, ss) != cudaSuccess ||
+           cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming) != cudaSuccess ||
+           cudaEventRecord(r->ev, ss) != cudaSuccess))
+        st = MG_ERR_CUDA;
+    }
+    std::lock_guard<std::mutex> lk(mu);
+    --creating;
+    if (st != MG_OK)
+      retire(r, st);
+    else
+      pending.push_back(r);
+    cv.notify_all();
+  }
 }
 
 void Server::loop() {
   cudaSetDevice(device);
   for (;;) {
-    std::vector<Request*> admitted;
     {
       std::unique_lock<std::mutex> lk(mu);
       cv.wait(lk, [&] { return stop || !queue.empty() || !running.empty() || !pending.empty(); });
       if (stop) break;
-      // admission by HBM footprint, in arrival order
-      while (!queue.empty() && used + queue.front()->footprint <= budget) {
-        Request* r = queue.front();
-        queue.pop_front();
+      // admission by HBM footprint, in arrival order with backfill: a request that does
+      // not fit yet keeps its place, later ones that fit go ahead of it
+      for (auto it = queue.begin(); it != queue.end();) {
+        Request* r = *it;
+        if (used + r->footprint > budget) {
+          ++it;
+          continue;
+        }
+        it = queue.erase(it);
         used += r->footprint;
         r->state = 1;
         r->t_admit = Clock::now();
-        admitted.push_back(r);
+        to_create[r->lane].push_back(r);
       }
-    }
-    // hierarchies of the admitted requests; their setups run concurrently on a pool of
-    // streams, overlapping each other and the running batch
-    for (Request* r : admitted) {
-      mg_hier* h = nullptr;
-      mg_status st = mg_hier_create(reinterpret_cast<const mg_grid*>(r->grid), &opt, &h);
-      if (st == MG_OK) {
-        r->h = reinterpret_cast<Hier*>(h);
-        cudaStream_t ss = setup_streams[next_setup++ % kSetupStreams];
-        st = setup_enqueue(*r->h, r->eps, ss);
-        if (st == MG_OK && (cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming) != cudaSuccess ||
-                            cudaEventRecord(r->ev, ss) != cudaSuccess))
-          st = MG_ERR_CUDA;
-      }
-      if (st != MG_OK) {
-        std::lock_guard<std::mutex> lk(mu);
-        retire(r, st);
-        cv.notify_all();
-        continue;
-      }
-      pending.push_back(r);
-    }
-    // requests whose setup finished join the running set
-    {
+      cv.notify_all();
+      // requests whose setup finished join the running set
       std::vector<Request*> still;
-      bool any_running;
-      {
-        std::lock_guard<std::mutex> lk(mu);
-        any_running = !running.empty();
-      }
-      for (size_t i = 0; i < pending.size(); ++i) {
-        Request* r = pending[i];
-        cudaError_t q = cudaEventQuery(r->ev);
-        if (q == cudaErrorNotReady && !any_running && still.empty()) q = cudaEventSynchronize(r->ev);
-        if (q == cudaErrorNotReady) {
+      for (Request* r : pending) {
+        if (cudaEventQuery(r->ev) == cudaErrorNotReady) {
           still.push_back(r);
           continue;
         }
-        int status = 0;
-        if (q == cudaSuccess) cudaMemcpy(&status, r->h->d_status, sizeof(int), cudaMemcpyDeviceToHost);
-        const mg_status st = q == cudaSuccess ? setup_status(*r->h, status) : MG_ERR_CUDA;
-        std::lock_guard<std::mutex> lk(mu);
+        const mg_status st = setup_status(*r->h, *reinterpret_cast<const int*>(r->h->h_pin + 15));
         if (st != MG_OK) {
           retire(r, st);
-          cv.notify_all();
         } else {
           r->state = 2;
           running.push_back(r);
@@ -157,81 +211,151 @@ void Server::loop() {
       }
       pending.swap(still);
     }
-    // re-form the batch when its membership changed, carrying the state over
-    std::vector<Request*> now;
+    // each idle lane starts its next step; then wait until one of them completes
+    bool any = false;
+    for (int k = 0; k < kLanes; ++k) {
+      if (!lanes[k].in_flight) start_step(lanes[k], k);
+      any = any || lanes[k].in_flight;
+    }
+    if (!any) continue;
+    // ... or until there is other work for the loop: a queued request that fits, a
+    // finished setup (its request joins an idle lane at once, not after the other
+    // lane's long step)
+    for (bool progressed = false; !progressed;) {
+      for (int k = 0; k < kLanes; ++k) {
+        Lane& ln = lanes[k];
+        if (!ln.in_flight) continue;
+        const cudaError_t q = cudaEventQuery(ln.done);
+        if (q == cudaErrorNotReady) continue;
+        finish_step(ln);
+        progressed = true;
+      }
+      if (progressed) break;
+      {
+        std::lock_guard<std::mutex> lk(mu);
+        progressed = stop;
+        for (Request* r : pending) progressed = progressed || cudaEventQuery(r->ev) != cudaErrorNotReady;
+        for (Request* r : queue) progressed = progressed || used + r->footprint <= budget;
+      }
+      if (!progressed) std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+  }
+}
+
+bool Server::start_step(Lane& ln, int lane) {
+  std::vector<Request*> now;
+  bool joiners = false, members_running = false;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    for (Request* r : running)
+      if (r->lane == lane) {
+        now.push_back(r);
+        if (std::find(ln.members.begin(), ln.members.end(), r) == ln.members.end()) joiners = true;
+      }
+    for (Request* r : ln.members) members_running = members_running || r->state == 2;
+  }
+  const bool reform = (joiners && (!members_running || Clock::now() - ln.reformed >= kReformEvery)) ||
+                      (!members_running && !ln.members.empty());
+  if (reform) {  // carry the running members' state over, release the finished ones
+    const std::vector<Request*> old = ln.members;
+    if (ln.batch) {
+      std::vector<ProblemState> carried;
+      batch_read(*ln.batch, carried, ln.stream);
+      for (size_t i = 0; i < old.size(); ++i)
+        if (old[i]->state == 2) old[i]->ps = carried[i];
+      batch_destroy(ln.batch);
+      ln.batch = nullptr;
+    }
     {
       std::lock_guard<std::mutex> lk(mu);
-      now = running;
-    }
-    if (now.empty()) continue;
-    if (now != members) {
-      std::vector<ProblemState> carried;
-      if (batch) {
-        batch_read(*batch, carried, stream);
-        for (size_t i = 0; i < members.size(); ++i) members[i]->ps = carried[i];
-        batch_destroy(batch);
-        batch = nullptr;
-      }
-      std::vector<Hier*> hs;
-      std::vector<double*> us;
-      std::vector<const double*> bs;
-      std::vector<ProblemState> init;
-      std::vector<int> fresh;
-      for (Request* r : now) {
-        hs.push_back(r->h);
-        us.push_back(r->u);
-        bs.push_back(r->b);
-        const bool is_new = std::find(members.begin(), members.end(), r) == members.end();
-        ProblemState ps = r->ps;
-        ps.tol = r->tol;
-        ps.max_cycles = r->max_cycles;
-        init.push_back(ps);
-        fresh.push_back(is_new ? 1 : 0);
-      }
-      mg_status st = batch_create(hs, &batch);
-      if (st == MG_OK) batch_set_graph(batch, false);
-      if (st == MG_OK) st = batch_begin(*batch, us.data(), bs.data(), init, fresh, stream);
-      if (st != MG_OK) {
-        std::lock_guard<std::mutex> lk(mu);
-        error = std::string("server batch: ") + mg_last_error();
-        for (Request* r : now) retire(r, st);
-        running.clear();
-        members.clear();
-        if (batch) {
-          batch_destroy(batch);
-          batch = nullptr;
+      for (Request* r : old)
+        if (r->zombie) {
+          release(r);
+          if (r->abandoned) delete r;
         }
-        cv.notify_all();
-        continue;
-      }
-      members = now;
+      cv.notify_all();
     }
-    int n_active = 0;
-    mg_status st = batch_run(*batch, 1, stream, &n_active);
-    std::vector<ProblemState> state;
-    if (st == MG_OK) st = batch_read(*batch, state, stream);
-    std::lock_guard<std::mutex> lk(mu);
-    bool changed = false;
-    for (size_t i = 0; i < members.size(); ++i) {
-      Request* r = members[i];
-      if (st != MG_OK) {
-        retire(r, st);
-        changed = true;
-        continue;
-      }
-      r->ps = state[i];
-      if (!state[i].active) {
-        retire(r, status_of(state[i].status));
-        changed = true;
-      }
+    ln.members.clear();
+    ln.reformed = Clock::now();
+    if (now.empty()) return false;
+    std::vector<Hier*> hs;
+    std::vector<double*> us;
+    std::vector<const double*> bs;
+    std::vector<ProblemState> init;
+    std::vector<int> fresh;
+    for (Request* r : now) {
+      hs.push_back(r->h);
+      us.push_back(r->u);
+      bs.push_back(r->b);
+      ProblemState ps = r->ps;
+      ps.tol = r->tol;
+      ps.max_cycles = r->max_cycles;
+      init.push_back(ps);
+      fresh.push_back(std::find(old.begin(), old.end(), r) == old.end() ? 1 : 0);
     }
-    if (changed) {
+    mg_status st = batch_create(hs, &ln.batch, prio[&ln == &lanes[0] ? 0 : 1]);
+    if (st == MG_OK) batch_set_graph(ln.batch, false);
+    if (st == MG_OK) st = batch_begin(*ln.batch, us.data(), bs.data(), init, fresh, ln.stream);
+    if (st != MG_OK) {
+      std::lock_guard<std::mutex> lk(mu);
+      error = std::string("server batch: ") + mg_last_error();
+      for (Request* r : now) retire(r, st);
       std::vector<Request*> keep;
       for (Request* r : running)
         if (r->state == 2) keep.push_back(r);
       running.swap(keep);
+      if (ln.batch) {
+        batch_destroy(ln.batch);
+        ln.batch = nullptr;
+      }
       cv.notify_all();
+      return false;
     }
+    ln.members = now;
+  } else if (!members_running) {
+    return false;
+  }
+  if (batch_step_enqueue(*ln.batch, ln.stream) != MG_OK || cudaEventRecord(ln.done, ln.stream) != cudaSuccess) {
+    std::lock_guard<std::mutex> lk(mu);
+    for (Request* r : ln.members)
+      if (r->state == 2) retire(r, MG_ERR_CUDA, false);
+    std::vector<Request*> keep;
+    for (Request* r : running)
+      if (r->state == 2) keep.push_back(r);
+    running.swap(keep);
+    cv.notify_all();
+    return false;
+  }
+  ln.in_flight = true;
+  return true;
+}
+
+void Server::finish_step(Lane& ln) {
+  ln.in_flight = false;
+  std::vector<ProblemState> state;
+  const mg_status st = batch_read(*ln.batch, state, ln.stream);
+  std::lock_guard<std::mutex> lk(mu);
+  bool changed = false;
+  for (size_t i = 0; i < ln.members.size(); ++i) {
+    Request* r = ln.members[i];
+    if (r->state != 2) continue;  // finished at an earlier step, waiting for the re-form
+    if (st != MG_OK) {
+      retire(r, st, false);
+      changed = true;
+      continue;
+    }
+    r->ps = state[i];
+    if (!state[i].active) {
+      retire(r, status_of(state[i].status), false);
+      changed = true;
+    }
+  }
+  if (changed) {
+    std::vector<Request*> keep;
+    for (Request* r : running)
+      if (r->state == 2) keep.push_back(r);
+    running.swap(keep);
+    cv.notify_all();
   }
 }
 
@@ -258,9 +382,18 @@ mg_status mg_server_create(size_t hbm_budget_bytes, const mg_options* opt, mg_se
   else
     mg_default_options(&sv->opt);
   cudaGetDevice(&sv->device);
+  int prio_low = 0, prio_high = 0;
+  cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high);
+  sv->prio[0] = prio_high;
+  sv->prio[1] = prio_low;
   bool ok = cudaStreamCreateWithFlags(&sv->stream, cudaStreamNonBlocking) == cudaSuccess;
-  for (int i = 0; i < Server::kSetupStreams && ok; ++i)
-    ok = cudaStreamCreateWithFlags(&sv->setup_streams[i], cudaStreamNonBlocking) == cudaSuccess;
+  for (int k = 0; k < Server::kLanes && ok; ++k) {
+    const int prio = k == 0 ? prio_high : prio_low;
+    ok = cudaStreamCreateWithPriority(&sv->lanes[k].stream, cudaStreamNonBlocking, prio) == cudaSuccess &&
+         cudaEventCreateWithFlags(&sv->lanes[k].done, cudaEventDisableTiming) == cudaSuccess;
+    for (int i = 0; i < Server::kSetupStreams && ok; ++i)
+      ok = cudaStreamCreateWithPriority(&sv->setup_streams[k][i], cudaStreamNonBlocking, prio) == cudaSuccess;
+  }
   if (!ok) {
     delete sv;
     set_error("mg_server_create: cudaStreamCreate failed");
@@ -268,7 +401,18 @@ mg_status mg_server_create(size_t hbm_budget_bytes, const mg_options* opt, mg_se
   }
   try {
     sv->th = std::thread([sv] { sv->loop(); });
+    for (int k = 0; k < 2; ++k)
+      for (int w = 0; w < Server::kWorkers[k]; ++w) sv->workers[k][w] = std::thread([sv, k] { sv->worker(k); });
   } catch (...) {
+    {
+      std::lock_guard<std::mutex> lk(sv->mu);
+      sv->stop = true;
+      sv->cv.notify_all();
+    }
+    if (sv->th.joinable()) sv->th.join();
+    for (int k = 0; k < 2; ++k)
+      for (auto& t : sv->workers[k])
+        if (t.joinable()) t.join();
     cudaStreamDestroy(sv->stream);
     delete sv;
     set_error("mg_server_create: thread start failed");
@@ -302,6 +446,7 @@ mg_status mg_server_submit(mg_server* server, const mg_request* req, uint64_t* t
   r->tol = req->rel_tol;
   r->max_cycles = req->max_cycles;
   r->footprint = hier_footprint(*g, sv->opt);
+  r->lane = g->levels[g->L].n_dofs >= Server::kLargeDofs ? 1 : 0;
   if (r->footprint > sv->budget) {
     delete r;
     set_error("mg_server_submit: the request's hierarchy (" + std::to_string(hier_footprint(*g, sv->opt)) +
@@ -344,7 +489,10 @@ mg_status mg_server_poll(mg_server* server, uint64_t ticket, int wait, int* done
   }
   const mg_status st = r->status;
   sv->all.erase(it);
-  delete r;
+  if (r->zombie)
+    r->abandoned = true;  // still a batch member: the server deletes it at the re-form
+  else
+    delete r;
   if (st != MG_OK) set_error("mg_server_poll: the request did not converge");
   return st;
 }
@@ -371,17 +519,30 @@ void mg_server_destroy(mg_server* server) {
     sv->cv.notify_all();
   }
   if (sv->th.joinable()) sv->th.join();
+  for (int k = 0; k < 2; ++k)
+    for (auto& t : sv->workers[k])
+      if (t.joinable()) t.join();
   cudaSetDevice(sv->device);
-  if (sv->batch) batch_destroy(sv->batch);
   cudaDeviceSynchronize();
+  for (int k = 0; k < Server::kLanes; ++k) {
+    for (Request* r : sv->lanes[k].members)
+      if (r->zombie && r->abandoned) {
+        sv->release(r);
+        delete r;
+      }
+    if (sv->lanes[k].batch) batch_destroy(sv->lanes[k].batch);
+    if (sv->lanes[k].done) cudaEventDestroy(sv->lanes[k].done);
+    if (sv->lanes[k].stream) cudaStreamDestroy(sv->lanes[k].stream);
+  }
   for (auto& kv : sv->all) {
     if (kv.second->h) mg_destroy_hier(reinterpret_cast<mg_hier*>(kv.second->h));
     if (kv.second->ev) cudaEventDestroy(kv.second->ev);
     delete kv.second;
   }
   cudaStreamDestroy(sv->stream);
-  for (int i = 0; i < Server::kSetupStreams; ++i)
-    if (sv->setup_streams[i]) cudaStreamDestroy(sv->setup_streams[i]);
+  for (int k = 0; k < Server::kLanes; ++k)
+    for (int i = 0; i < Server::kSetupStreams; ++i)
+      if (sv->setup_streams[k][i]) cudaStreamDestroy(sv->setup_streams[k][i]);
   delete sv;
 }
 

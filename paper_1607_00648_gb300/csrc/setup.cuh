@@ -241,6 +241,12 @@ __global__ void __launch_bounds__(kBlock) k_jacobi_dinv(LevelDesc L, const doubl
 template <int DIM>
 constexpr int rap_tpv() { return DIM == 2 ? 32 : 128; }
 
+// dynamic shared memory of k_rap<DIM, PMODE> (the staged P_hat planes)
+template <int DIM, int PMODE>
+constexpr size_t rap_dyn_smem() {
+  return PMODE == 1 ? static_cast<size_t>(128 / rap_tpv<DIM>()) * cpow(3, DIM) * cpow(5, DIM) * sizeof(double) : 0;
+}
+
 template <int DIM, int PMODE>
 __global__ void __launch_bounds__(128) k_rap(LevelDesc Lc, LevelDesc Lf, const double* eps_f, const double* ahat_f,
                                                const double* eps_c, const double* phat_c, double* ahat_c) {
@@ -251,6 +257,7 @@ __global__ void __launch_bounds__(128) k_rap(LevelDesc Lc, LevelDesc Lf, const d
   __shared__ double part[VPB][N3][WPV];
   __shared__ double plin[N5];          // d-linear weights by 5^d offset
   __shared__ double sst[128][N3];      // P(f,V) * fine stencil of f, per thread
+  extern __shared__ double pst[];      // P_hat of the 3^d coarse neighbours W (PMODE 1): [VPB][N3][N5]
   const int sub = threadIdx.x / TPV, j = threadIdx.x % TPV;
   const int64_t cs = blockIdx.x * static_cast<int64_t>(VPB) + sub;
   int V[DIM];
@@ -265,15 +272,19 @@ __global__ void __launch_bounds__(128) k_rap(LevelDesc Lc, LevelDesc Lf, const d
     }
     plin[k] = w;
   }
-  if (vdof && j < N3) {
-    int W[DIM], jj = j;
+  if (j < N3) {  // every entry is written (-1 unless W is a DoF): the staging below reads them all
+    int64_t pb = -1;
+    if (vdof) {
+      int W[DIM], jj = j;
 #pragma unroll
-    for (int i = 0; i < DIM; ++i) {
-      W[i] = V[i] + jj % 3 - 1;
-      jj /= 3;
+      for (int i = 0; i < DIM; ++i) {
+        W[i] = V[i] + jj % 3 - 1;
+        jj /= 3;
+      }
+      const int64_t ws = slot_of<DIM>(Lc, W);
+      if (ws >= 0 && is_dof(Lc.vflags[ws])) pb = plane_index(Lc, ws, 0, N5);
     }
-    const int64_t ws = slot_of<DIM>(Lc, W);
-    pbase[sub][j] = (ws >= 0 && is_dof(Lc.vflags[ws])) ? plane_index(Lc, ws, 0, N5) : -1;
+    pbase[sub][j] = pb;
   }
   if (vdof && j == 0) {
     double sr[N3];
@@ -312,6 +323,15 @@ __global__ void __launch_bounds__(128) k_rap(LevelDesc Lc, LevelDesc Lf, const d
     }
   }
   __syncthreads();
+  if constexpr (PMODE == 1) {
+    // stage the neighbours' P_hat planes: every load in flight at once instead of one
+    // dependent, scattered load per term of the product below
+    for (int idx = threadIdx.x; idx < VPB * N3 * N5; idx += blockDim.x) {
+      const int64_t pb = pbase[idx / (N3 * N5)][(idx / N5) % N3];
+      pst[idx] = pb >= 0 ? phat_c[pb + (idx % N5) * static_cast<int64_t>(Lc.S)] : 0.0;
+    }
+    __syncthreads();
+  }
 
   // c[q] = sum over stencil neighbours g of f with |g - 3W| <= 2 (W = V + o_q) of
   // P(f,V) A_f(f,g) P(g,W); per axis the admissible g offsets form a range
@@ -319,11 +339,9 @@ __global__ void __launch_bounds__(128) k_rap(LevelDesc Lc, LevelDesc Lf, const d
 #pragma unroll
   for (int q = 0; q < N3; ++q) c[q] = 0.0;
   if (gdof) {
-    const int64_t Sc = Lc.S;
 #pragma unroll
     for (int q = 0; q < N3; ++q) {
-      const int64_t pb = pbase[sub][q];
-      if (pb < 0) continue;
+      if (pbase[sub][q] < 0) continue;
       int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0}, qq = q;
 #pragma unroll
       for (int i = 0; i < DIM; ++i) {
@@ -342,7 +360,7 @@ __global__ void __launch_bounds__(128) k_rap(LevelDesc Lc, LevelDesc Lf, const d
             int k5 = (d[0] + ex - 3 * (q % 3 - 1)) + 2 + 5 * ((d[1] + ey - 3 * ((q / 3) % 3 - 1)) + 2);
             if (DIM == 3) k5 += 25 * ((d[2] + ez - 3 * (q / 9 - 1)) + 2);
             double p = plin[k5];
-            if constexpr (PMODE == 1) p += phat_c[pb + k5 * Sc];
+            if constexpr (PMODE == 1) p += pst[(sub * N3 + q) * N5 + k5];
             acc = fma(sst[threadIdx.x][e], p, acc);
           }
       c[q] = acc;

@@ -7,6 +7,7 @@
 #include <type_traits>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -318,19 +319,76 @@ static mg_status last_launch(const char* what) {
   return MG_OK;
 }
 
+// ---- pooled device memory and pinned slots ----
+
+namespace {
+std::mutex g_pool_mu;
+cudaMemPool_t g_pools[64] = {};
+std::vector<void*> g_pinned_free;
+}  // namespace
+
+cudaError_t pool_alloc(void** p, size_t bytes, cudaStream_t s) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  cudaMemPool_t pool;
+  {
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!g_pools[dev]) {
+      cudaMemPoolProps props{};
+      props.allocType = cudaMemAllocationTypePinned;
+      props.location.type = cudaMemLocationTypeDevice;
+      props.location.id = dev;
+      e = cudaMemPoolCreate(&g_pools[dev], &props);
+      if (e != cudaSuccess) return e;
+      uint64_t keep = ~0ull;
+      e = cudaMemPoolSetAttribute(g_pools[dev], cudaMemPoolAttrReleaseThreshold, &keep);
+      if (e != cudaSuccess) return e;
+    }
+    pool = g_pools[dev];
+  }
+  return cudaMallocFromPoolAsync(p, bytes, pool, s);
+}
+
+void pool_free(void* p, cudaStream_t s) {
+  if (p) cudaFreeAsync(p, s);
+}
+
+void* pinned_slot() {
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  if (g_pinned_free.empty()) {
+    constexpr size_t kSlot = 128, kSlab = 512;
+    char* slab = nullptr;
+    if (cudaMallocHost(&slab, kSlot * kSlab) != cudaSuccess) return nullptr;
+    for (size_t i = 0; i < kSlab; ++i) g_pinned_free.push_back(slab + i * kSlot);
+  }
+  void* p = g_pinned_free.back();
+  g_pinned_free.pop_back();
+  std::memset(p, 0, 128);
+  return p;
+}
+
+void pinned_release(void* p) {
+  if (!p) return;
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  g_pinned_free.push_back(p);
+}
+
 template <typename T>
 static mg_status dalloc(Hier& H, T** p, size_t n) {
   *p = nullptr;
   if (n == 0) return MG_OK;
   void* q = nullptr;
-  const cudaError_t e = cudaMalloc(&q, n * sizeof(T));
+  const cudaError_t e = pool_alloc(&q, n * sizeof(T), H.own);
   if (e != cudaSuccess) {
     cudaGetLastError();
-    set_error(std::string("cudaMalloc of ") + std::to_string(n * sizeof(T)) + " bytes: " + cudaGetErrorString(e));
+    set_error(std::string("device allocation of ") + std::to_string(n * sizeof(T)) + " bytes: " +
+              cudaGetErrorString(e));
     return e == cudaErrorMemoryAllocation ? MG_ERR_OOM : MG_ERR_CUDA;
   }
   H.allocs.push_back(q);
-  MG_TRY_CUDA(cudaMemset(q, 0, n * sizeof(T)));
+  MG_TRY_CUDA(cudaMemsetAsync(q, 0, n * sizeof(T), H.own));
   *p = static_cast<T*>(q);
   return MG_OK;
 }
@@ -338,27 +396,32 @@ static mg_status dalloc(Hier& H, T** p, size_t n) {
 template <typename T>
 static mg_status upload(Hier& H, T** p, const std::vector<T>& v) {
   MG_CHECK(dalloc(H, p, v.size()));
-  if (!v.empty()) MG_TRY_CUDA(cudaMemcpy(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+  if (!v.empty()) MG_TRY_CUDA(cudaMemcpyAsync(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, H.own));
   return MG_OK;
 }
 
-static void free_hier(Hier* H) {
+// device_sync: wait for all device work first (public destroy: a hierarchy may still be
+// in use on any stream, as cudaFree would have waited for); the server passes false
+static void free_hier(Hier* H, bool device_sync) {
   if (!H) return;
+  if (device_sync) cudaDeviceSynchronize();
   H->g_cycle64.reset();
   H->g_outer.reset();
   H->g_inner.reset();
   H->g_comp64.reset();
   H->g_comp_outer.reset();
   H->g_comp_inner.reset();
-  for (void* p : H->allocs) cudaFree(p);
-  if (H->h_pin) cudaFreeHost(H->h_pin);
+  for (void* p : H->allocs) pool_free(p, H->own);
+  pinned_release(H->h_pin);
   if (H->own) cudaStreamDestroy(H->own);
   delete H;
 }
 
+void hier_release(Hier* H) { free_hier(H, false); }
+
 static inline unsigned nblk(int64_t n) { return static_cast<unsigned>((n + kBlock - 1) / kBlock); }
 
-static mg_status create(const Grid* g, const mg_options& o, Hier** out) {
+static mg_status create(const Grid* g, const mg_options& o, Hier** out, int priority) {
   Hier* H = new (std::nothrow) Hier();
   if (!H) {
     set_error("mg_hier_create: out of host memory");
@@ -376,9 +439,13 @@ static mg_status create(const Grid* g, const mg_options& o, Hier** out) {
   H->mixed = o.precision != MG_PREC_FP64;
   H->fmt = o.precision == MG_PREC_MIXED_FP16 ? 2 : 1;
   auto fail = [&](mg_status s) {
-    free_hier(H);
+    free_hier(H, true);
     return s;
   };
+  if (cudaStreamCreateWithPriority(&H->own, cudaStreamNonBlocking, priority) != cudaSuccess) {
+    set_error("mg_hier_create: cudaStreamCreate failed");
+    return fail(MG_ERR_CUDA);
+  }
   const int d = g->dim;
   const int n3 = ipow(3, d), n5 = ipow(5, d);
   H->lv.resize(H->L + 1);
@@ -391,7 +458,7 @@ static mg_status create(const Grid* g, const mg_options& o, Hier** out) {
     if ((st = upload(*H, &D.brick_rank, hl.brick_rank)) != MG_OK) return fail(st);
     if ((st = upload(*H, &D.vflags, hl.vflags)) != MG_OK) return fail(st);
     if ((st = upload(*H, &D.cflags, hl.cflags)) != MG_OK) return fail(st);
-    if (l > 0) {
+    if (l > 0 && hl.n_hanging > 0) {  // levels without hanging vertices need no interpolation tables
       if ((st = upload(*H, &D.hang_idx, hl.hang_idx)) != MG_OK) return fail(st);
       if ((st = upload(*H, &D.hang_w, hl.hang_w)) != MG_OK) return fail(st);
     }
@@ -498,16 +565,50 @@ static mg_status create(const Grid* g, const mg_options& o, Hier** out) {
     if ((st = dalloc(*H, &ps, std::max(sizeof(PSolve<double>), sizeof(PSolve<float>)))) != MG_OK) return fail(st);
     H->d_psolve = ps;
   }
-  if (cudaMallocHost(&H->h_pin, 16 * sizeof(double)) != cudaSuccess) {
-    set_error("mg_hier_create: cudaMallocHost failed");
+  H->h_pin = static_cast<double*>(pinned_slot());
+  if (!H->h_pin) {
+    set_error("mg_hier_create: pinned host memory unavailable");
     return fail(MG_ERR_OOM);
   }
-  if (cudaStreamCreate(&H->own) != cudaSuccess) {
-    set_error("mg_hier_create: cudaStreamCreate failed");
+  // the buffers were allocated, zeroed and filled in order on H->own: complete that
+  // before any other stream uses them
+  if (cudaStreamSynchronize(H->own) != cudaSuccess) {
+    set_error(std::string("mg_hier_create: ") + cudaGetErrorString(cudaGetLastError()));
     return fail(MG_ERR_CUDA);
   }
   *out = H;
   return MG_OK;
+}
+
+// options and grid checks of mg_hier_create, then create() with the hierarchy's own
+// stream at the given priority (the server gives small requests the highest)
+mg_status hier_create(const Grid* g, const mg_options& o, int priority, Hier** out) {
+  *out = nullptr;
+  if (o.coarsest_level < 1 || o.coarsest_level >= g->L || o.nu1 < 0 || o.nu2 < 0 || !(o.omega > 0.0) ||
+      o.transfer < 0 || o.transfer > 1 || o.coarse < 0 || o.coarse > 1 || o.precision < 0 || o.precision > 2) {
+    set_error("mg_hier_create: invalid options");
+    return MG_ERR_INVALID_ARG;
+  }
+  if (!g->uniform) {
+    // composite solve: levels 0 .. L - 2 present and refined everywhere, so level
+    // L - 1 is complete and only its refinement towards level L is partial
+    for (int l = 0; l + 1 < g->L; ++l)
+      for (size_t c = 0; c < g->cells[l].size(); ++c)
+        if (!g->cells[l][c] || !g->refined[l][c]) {
+          set_error("mg_hier_create: adaptive grids must be complete up to level max_level - 1");
+          return MG_ERR_UNSUPPORTED;
+        }
+    if (o.coarsest_level >= g->L - 1) {
+      set_error("mg_hier_create: the coarsest level must lie below the finest complete level");
+      return MG_ERR_INVALID_ARG;
+    }
+  }
+  try {
+    return create(g, o, out, priority);
+  } catch (const std::bad_alloc&) {
+    set_error("mg_hier_create: out of host memory");
+    return MG_ERR_OOM;
+  }
 }
 
 // device bytes mg_hier_create allocates for a grid and options (admission by HBM footprint)
@@ -521,7 +622,7 @@ size_t hier_footprint(const Grid& g, const mg_options& o) {
   for (int l = o.coarsest_level; l <= g.L; ++l) {
     const HostLevel& hl = g.levels[l];
     const size_t ns = static_cast<size_t>(hl.n_slots), nb = static_cast<size_t>(hl.n_bricks);
-    bytes += nb * n3 * 4 + nb * d * 4 + hl.brick_rank.size() * 4 + 2 * ns + ns * full * 12;
+    bytes += nb * n3 * 4 + nb * d * 4 + hl.brick_rank.size() * 4 + 2 * ns + (hl.n_hanging > 0 ? ns * full * 12 : 0);
     bytes += 3 * ns * 8 + nb * hl.B * 8 + 4 + (mixed ? 0 : ns * 8);
     if (l < g.L) bytes += 2 * ns * 8;
     if (l < top) bytes += (galerkin ? ns * n3 * 8 : 0) + (boxmg ? ns * n5 * 8 : 0);
@@ -701,15 +802,20 @@ static mg_status run_setup(Hier& H, const double* eps_in, cudaStream_t s, bool c
     if (H.galerkin) {
       // 128-thread CTAs: 4 coarse vertices (2D) or 1 (3D) per CTA
       const unsigned gr = static_cast<unsigned>((C.d.n_slots + (128 / rap_tpv<2>()) - 1) / (128 / rap_tpv<2>()));
+      static const bool smem_opt_in = [] {  // the 3D kernel stages 27 KB of P_hat
+        return cudaFuncSetAttribute(k_rap<3, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    static_cast<int>(rap_dyn_smem<3, 1>())) == cudaSuccess;
+      }();
+      (void)smem_opt_in;
       if (d == 2) {
         if (H.boxmg)
-          k_rap<2, 1><<<gr, 128, 0, s>>>(C.d, F.d, F.eps, ahat_f, C.eps, C.phat, C.ahat);
+          k_rap<2, 1><<<gr, 128, rap_dyn_smem<2, 1>(), s>>>(C.d, F.d, F.eps, ahat_f, C.eps, C.phat, C.ahat);
         else
           k_rap<2, 0><<<gr, 128, 0, s>>>(C.d, F.d, F.eps, ahat_f, C.eps, C.phat, C.ahat);
       } else {
         const unsigned g3 = static_cast<unsigned>(C.d.n_slots);
         if (H.boxmg)
-          k_rap<3, 1><<<g3, 128, 0, s>>>(C.d, F.d, F.eps, ahat_f, C.eps, C.phat, C.ahat);
+          k_rap<3, 1><<<g3, 128, rap_dyn_smem<3, 1>(), s>>>(C.d, F.d, F.eps, ahat_f, C.eps, C.phat, C.ahat);
         else
           k_rap<3, 0><<<g3, 128, 0, s>>>(C.d, F.d, F.eps, ahat_f, C.eps, C.phat, C.ahat);
       }
@@ -1370,36 +1476,7 @@ mg_status mg_hier_create(const mg_grid* grid, const mg_options* opt, mg_hier** o
     o = *opt;
   else
     mg_default_options(&o);
-  const Grid* g = reinterpret_cast<const Grid*>(grid);
-  if (o.coarsest_level < 1 || o.coarsest_level >= g->L || o.nu1 < 0 || o.nu2 < 0 || !(o.omega > 0.0) ||
-      o.transfer < 0 || o.transfer > 1 || o.coarse < 0 || o.coarse > 1 || o.precision < 0 || o.precision > 2) {
-    set_error("mg_hier_create: invalid options");
-    return MG_ERR_INVALID_ARG;
-  }
-  if (!g->uniform) {
-    // composite solve: levels 0 .. L - 2 present and refined everywhere, so level
-    // L - 1 is complete and only its refinement towards level L is partial
-    for (int l = 0; l + 1 < g->L; ++l)
-      for (size_t c = 0; c < g->cells[l].size(); ++c)
-        if (!g->cells[l][c] || !g->refined[l][c]) {
-          set_error("mg_hier_create: adaptive grids must be complete up to level max_level - 1");
-          return MG_ERR_UNSUPPORTED;
-        }
-    if (o.coarsest_level >= g->L - 1) {
-      set_error("mg_hier_create: the coarsest level must lie below the finest complete level");
-      return MG_ERR_INVALID_ARG;
-    }
-  }
-  try {
-    Hier* H = nullptr;
-    const mg_status st = create(g, o, &H);
-    if (st != MG_OK) return st;
-    *out = reinterpret_cast<mg_hier*>(H);
-  } catch (const std::bad_alloc&) {
-    set_error("mg_hier_create: out of host memory");
-    return MG_ERR_OOM;
-  }
-  return MG_OK;
+  return hier_create(reinterpret_cast<const Grid*>(grid), o, 0, reinterpret_cast<Hier**>(out));
 }
 
 mg_status mg_hier_footprint(const mg_grid* grid, const mg_options* opt, size_t* bytes) {
@@ -1685,6 +1762,6 @@ mg_status mg_encode_deltas(int64_t n, int k, const double* delta, int fmt, uint1
   return last_launch("mg_encode_deltas");
 }
 
-void mg_destroy_hier(mg_hier* h) { free_hier(H_(h)); }
+void mg_destroy_hier(mg_hier* h) { free_hier(H_(h), true); }
 
 }  // extern "C"
