@@ -342,7 +342,7 @@ void emit_mixed_step(Batch& bt, const BatchState& st, cudaStream_t s) {
 }
 
 mg_status build_batch(Batch& bt) {
-  if (cudaStreamCreateWithPriority(&bt.own, cudaStreamNonBlocking, bt.priority) != cudaSuccess) {
+  if (cudaStreamCreateWithPriority(&bt.own, cudaStreamDefault, bt.priority) != cudaSuccess) {
     set_error("mg_batch_create: cudaStreamCreate failed");
     return MG_ERR_CUDA;
   }

@@ -241,10 +241,10 @@ __global__ void __launch_bounds__(kBlock) k_jacobi_dinv(LevelDesc L, const doubl
 template <int DIM>
 constexpr int rap_tpv() { return DIM == 2 ? 32 : 128; }
 
-// dynamic shared memory of k_rap<DIM, PMODE> (the staged P_hat planes)
+// dynamic shared memory of k_rap<DIM, PMODE> (the staged P of the coarse neighbours)
 template <int DIM, int PMODE>
 constexpr size_t rap_dyn_smem() {
-  return PMODE == 1 ? static_cast<size_t>(128 / rap_tpv<DIM>()) * cpow(3, DIM) * cpow(5, DIM) * sizeof(double) : 0;
+  return static_cast<size_t>(128 / rap_tpv<DIM>()) * cpow(3, DIM) * cpow(5, DIM) * sizeof(double);
 }
 
 template <int DIM, int PMODE>
@@ -256,8 +256,7 @@ __global__ void __launch_bounds__(128) k_rap(LevelDesc Lc, LevelDesc Lf, const d
   __shared__ double sred[VPB][N3];     // A_redisc(V, V + o)
   __shared__ double part[VPB][N3][WPV];
   __shared__ double plin[N5];          // d-linear weights by 5^d offset
-  __shared__ double sst[128][N3];      // P(f,V) * fine stencil of f, per thread
-  extern __shared__ double pst[];      // P_hat of the 3^d coarse neighbours W (PMODE 1): [VPB][N3][N5]
+  extern __shared__ double pfull[];    // P(W, .) = d-linear + P_hat of the 3^d coarse neighbours: [VPB][N3][N5]
   const int sub = threadIdx.x / TPV, j = threadIdx.x % TPV;
   const int64_t cs = blockIdx.x * static_cast<int64_t>(VPB) + sub;
   int V[DIM];
@@ -292,9 +291,11 @@ __global__ void __launch_bounds__(128) k_rap(LevelDesc Lc, LevelDesc Lf, const d
 #pragma unroll
     for (int q = 0; q < N3; ++q) sred[sub][q] = sr[q];
   }
-  // this thread's fine vertex f = 3V + d and which of its stencil neighbours are DoFs
+  // this thread's fine vertex f = 3V + d, P(f,V) times its fine stencil, and which of
+  // its stencil neighbours are DoFs
   int d[DIM];
   uint32_t gdof = 0;
+  double st[N3];
   {
     int f[DIM], jj = j;
 #pragma unroll
@@ -306,7 +307,6 @@ __global__ void __launch_bounds__(128) k_rap(LevelDesc Lc, LevelDesc Lf, const d
     const int64_t fs = (vdof && j < N5) ? slot_of<DIM>(Lf, f) : -1;
     if (fs >= 0 && is_dof(Lf.vflags[fs])) {
       const double pV = p_entry_d<DIM, PMODE>(Lc, phat_c, cs, d);
-      double st[N3];
       full_stencil<DIM>(Lf, eps_f, ahat_f, f, fs, st);
 #pragma unroll
       for (int e = 0; e < N3; ++e) {
@@ -318,52 +318,54 @@ __global__ void __launch_bounds__(128) k_rap(LevelDesc Lc, LevelDesc Lf, const d
         }
         const int64_t gs = slot_of<DIM>(Lf, g);
         if (gs >= 0 && is_dof(Lf.vflags[gs])) gdof |= 1u << e;
-        sst[threadIdx.x][e] = pV * st[e];
+        st[e] *= pV;
       }
     }
   }
   __syncthreads();
-  if constexpr (PMODE == 1) {
-    // stage the neighbours' P_hat planes: every load in flight at once instead of one
-    // dependent, scattered load per term of the product below
-    for (int idx = threadIdx.x; idx < VPB * N3 * N5; idx += blockDim.x) {
-      const int64_t pb = pbase[idx / (N3 * N5)][(idx / N5) % N3];
-      pst[idx] = pb >= 0 ? phat_c[pb + (idx % N5) * static_cast<int64_t>(Lc.S)] : 0.0;
+  // stage P(W, .) of the neighbours once per CTA: the loads all in flight together, and
+  // the d-linear part added here rather than once per term below (FP64 units are scarce)
+  for (int idx = threadIdx.x; idx < VPB * N3 * N5; idx += blockDim.x) {
+    const int64_t pb = pbase[idx / (N3 * N5)][(idx / N5) % N3];
+    double p = 0.0;
+    if (pb >= 0) {
+      p = plin[idx % N5];
+      if constexpr (PMODE == 1) p += phat_c[pb + (idx % N5) * static_cast<int64_t>(Lc.S)];
     }
-    __syncthreads();
+    pfull[idx] = p;
   }
+  __syncthreads();
 
   // c[q] = sum over stencil neighbours g of f with |g - 3W| <= 2 (W = V + o_q) of
-  // P(f,V) A_f(f,g) P(g,W); per axis the admissible g offsets form a range
+  // P(f,V) A_f(f,g) P(g,W).  Outer loop over g (not unrolled: a compact body), inner over
+  // the 3^d targets W with per-axis admissibility masks of the offset g - 3W
   double c[N3];
 #pragma unroll
   for (int q = 0; q < N3; ++q) c[q] = 0.0;
   if (gdof) {
-#pragma unroll
-    for (int q = 0; q < N3; ++q) {
-      if (pbase[sub][q] < 0) continue;
-      int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0}, qq = q;
+    const double* pf = pfull + sub * N3 * N5;
+#pragma unroll 1
+    for (int e = 0; e < N3; ++e) {
+      if (!((gdof >> e) & 1u)) continue;
+      const double a = st[e];
+      int sg[3] = {0, 0, 0}, ee = e;
 #pragma unroll
       for (int i = 0; i < DIM; ++i) {
-        const int o3 = 3 * (qq % 3 - 1);
-        qq /= 3;
-        lo[i] = max(-1, o3 - 2 - d[i]);
-        hi[i] = min(1, o3 + 2 - d[i]);
+        sg[i] = d[i] + ee % 3 - 1;  // g - 3V per axis, in [-3, 3]
+        ee /= 3;
       }
-      double acc = 0.0;
-      for (int ez = lo[2]; ez <= hi[2]; ++ez)
-        for (int ey = lo[1]; ey <= hi[1]; ++ey)
-          for (int ex = lo[0]; ex <= hi[0]; ++ex) {
-            const int e = DIM == 2 ? (ex + 1) + 3 * (ey + 1) : (ex + 1) + 3 * (ey + 1) + 9 * (ez + 1);
-            if (!((gdof >> e) & 1u)) continue;
-            // offset of g from 3W, per axis d + e - 3 o in [-2, 2]
-            int k5 = (d[0] + ex - 3 * (q % 3 - 1)) + 2 + 5 * ((d[1] + ey - 3 * ((q / 3) % 3 - 1)) + 2);
-            if (DIM == 3) k5 += 25 * ((d[2] + ez - 3 * (q / 9 - 1)) + 2);
-            double p = plin[k5];
-            if constexpr (PMODE == 1) p += pst[(sub * N3 + q) * N5 + k5];
-            acc = fma(sst[threadIdx.x][e], p, acc);
-          }
-      c[q] = acc;
+      bool ok[3][3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int o = -1; o <= 1; ++o) ok[i][o + 1] = i < DIM ? abs(sg[i] - 3 * o) <= 2 : o == 0;
+      const int base = (sg[0] + 2) + 5 * (sg[1] + 2) + (DIM == 3 ? 25 * (sg[2] + 2) : 0);
+#pragma unroll
+      for (int q = 0; q < N3; ++q) {
+        const int ox = q % 3 - 1, oy = (q / 3) % 3 - 1, oz = DIM == 3 ? q / 9 - 1 : 0;
+        if (ok[0][ox + 1] && ok[1][oy + 1] && ok[2][oz + 1])
+          c[q] = fma(a, pf[q * N5 + base - 3 * (ox + 5 * oy + 25 * oz)], c[q]);
+      }
     }
   }
   // fixed-order reduction over the group: shuffles within each warp, then warps in order

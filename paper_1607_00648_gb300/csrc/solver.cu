@@ -442,7 +442,9 @@ static mg_status create(const Grid* g, const mg_options& o, Hier** out, int prio
     free_hier(H, true);
     return s;
   };
-  if (cudaStreamCreateWithPriority(&H->own, cudaStreamNonBlocking, priority) != cudaSuccess) {
+  // a blocking stream: work given stream NULL runs here, ordered with the legacy
+  // default stream as the stream convention of the interface promises
+  if (cudaStreamCreateWithPriority(&H->own, cudaStreamDefault, priority) != cudaSuccess) {
     set_error("mg_hier_create: cudaStreamCreate failed");
     return fail(MG_ERR_CUDA);
   }
@@ -802,22 +804,24 @@ static mg_status run_setup(Hier& H, const double* eps_in, cudaStream_t s, bool c
     if (H.galerkin) {
       // 128-thread CTAs: 4 coarse vertices (2D) or 1 (3D) per CTA
       const unsigned gr = static_cast<unsigned>((C.d.n_slots + (128 / rap_tpv<2>()) - 1) / (128 / rap_tpv<2>()));
-      static const bool smem_opt_in = [] {  // the 3D kernel stages 27 KB of P_hat
+      static const bool smem_opt_in = [] {  // the 3D kernel stages 27 KB of P
         return cudaFuncSetAttribute(k_rap<3, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    static_cast<int>(rap_dyn_smem<3, 1>())) == cudaSuccess;
+                                    static_cast<int>(rap_dyn_smem<3, 1>())) == cudaSuccess &&
+               cudaFuncSetAttribute(k_rap<3, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    static_cast<int>(rap_dyn_smem<3, 0>())) == cudaSuccess;
       }();
       (void)smem_opt_in;
       if (d == 2) {
         if (H.boxmg)
           k_rap<2, 1><<<gr, 128, rap_dyn_smem<2, 1>(), s>>>(C.d, F.d, F.eps, ahat_f, C.eps, C.phat, C.ahat);
         else
-          k_rap<2, 0><<<gr, 128, 0, s>>>(C.d, F.d, F.eps, ahat_f, C.eps, C.phat, C.ahat);
+          k_rap<2, 0><<<gr, 128, rap_dyn_smem<2, 0>(), s>>>(C.d, F.d, F.eps, ahat_f, C.eps, C.phat, C.ahat);
       } else {
         const unsigned g3 = static_cast<unsigned>(C.d.n_slots);
         if (H.boxmg)
           k_rap<3, 1><<<g3, 128, rap_dyn_smem<3, 1>(), s>>>(C.d, F.d, F.eps, ahat_f, C.eps, C.phat, C.ahat);
         else
-          k_rap<3, 0><<<g3, 128, 0, s>>>(C.d, F.d, F.eps, ahat_f, C.eps, C.phat, C.ahat);
+          k_rap<3, 0><<<g3, 128, rap_dyn_smem<3, 0>(), s>>>(C.d, F.d, F.eps, ahat_f, C.eps, C.phat, C.ahat);
       }
     }
     MG_CHECK(last_launch("setup: BoxMG / Galerkin"));
