@@ -66,6 +66,10 @@ FP64_PEAK_TFLOPS = 1.25  # nominal dense FP64 of a GB300 (2 FMA / clock / SM at 
 # counts 2 flops): 4 + 14 + 3 + 1 + 1 + 2
 FLOPS_PER_DOF_SWEEP_2D = 25
 BYTES_PER_DOF_SWEEP_FP64 = 40  # u, b, eps, omega/diag read + u' written, 8 B each
+# DRAM bytes per DoF of that sweep from ncu (dram__bytes_read.sum + dram__bytes_write.sum)
+# on the 2D level-7 case (python bench.py --sweep-level 7 --sweep-dim 2 --sweep-prec fp64),
+# whose vectors exceed L2; the level-6 launch is scaled by its DoFs
+TRAFFIC_PER_DOF_SWEEP_FP64_2D = 38.2
 BYTES_PER_DOF_SWEEP_FP32 = 16
 
 
@@ -458,7 +462,8 @@ def run_ours(args):
                                    "peak": hbm_peak, "unit": "GB/s",
                                    "frac": BYTES_PER_DOF_SWEEP_FP64 * n_dofs / sweep_s / 1e9 / hbm_peak,
                                    "peak_source": peak_src},
-                "traffic": None}
+                "traffic": TRAFFIC_PER_DOF_SWEEP_FP64_2D * n_dofs,
+                "traffic_note": "bytes per launch, ncu DRAM bytes/DoF of the level-7 capture x DoFs"}
 
     # end to end through the public API with host buffers
     eps_h = torch.from_numpy(eps_cat).pin_memory()
