@@ -6,6 +6,7 @@
 
 #include "kernels.cuh"
 #include "persist.cuh"
+#include "sweep_fast.cuh"
 
 namespace mg {
 
@@ -70,6 +71,39 @@ __global__ void __launch_bounds__(kBlock) k_bsweep(BatchArgs<T> ba, const int4* 
   }
 }
 
+// FP32 at the fine brick edges (2D 27, 3D 9): the column kernels, 128 threads
+template <int DIM, typename T, int AMC, int OP>
+__global__ void __launch_bounds__(128, 6) k_bsweep_col(BatchArgs<T> ba, const int4* items, int part_off, int src,
+                                                         int dst) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int4 it = items[blockIdx.x];
+  const int p = it.x, l = it.y;
+  if (!ba.active[p]) return;
+  const PLevel<T>& P = ba.lv[p * kMaxLevels + l];
+  const bool finest = l == ba.Lp[p];
+  SweepArgs<T> a{};
+  a.L = P.d;
+  a.u = bvec(ba, P, p, l, src);
+  a.b = finest ? ba.bfin[p] : P.b;
+  a.out = bvec(ba, P, p, l, dst);
+  a.eps = P.eps;
+  a.ahat = P.ahat;
+  a.ascale = P.ascale;
+  a.omega = ba.omega;
+  a.R = P.R;
+  double part;
+  if (finest)
+    part = sweep_col_item<DIM, T, 0, OP>(a, it.z, it.w, smem);
+  else
+    part = sweep_col_item<DIM, T, AMC, OP>(a, it.z, it.w, smem);
+  if constexpr (OP == kJacobiNorm || OP == kResidual) {
+    if (ba.partial) {
+      const double s = block_sum(part);
+      if (threadIdx.x == 0) ba.partial[part_off + blockIdx.x] = s;
+    }
+  }
+}
+
 // item = (problem, coarse level, chunk of kBlock coarse slots); also zeroes the
 // coarse iterate (the coarse-grid correction starts from 0)
 template <int DIM, typename T, int PM, int BC, int BF>
@@ -122,11 +156,18 @@ void blaunch_transfer(const BatchArgs<T>& ba, const BatchGroup& g, bool restrict
 template <int DIM, typename T, int B>
 static void bsweep_b(const BatchArgs<T>& ba, const BatchGroup& g, int op, int amc, int src, int dst, cudaStream_t s) {
   constexpr int VOL = DIM == 2 ? B * B : B * B * B;
+  constexpr bool col = std::is_same<T, float>::value && ((DIM == 2 && B == 27) || (DIM == 3 && B == 9));
   int threads = ((VOL + 31) / 32) * 32;
   if (threads > kBlock) threads = kBlock;
-  const size_t smem = sweep_tile_bytes<DIM, T>(B, B);
+  const size_t smem = col ? (DIM == 2 ? 0 : sweep_tile_bytes<DIM, T>(B, B, true)) : sweep_tile_bytes<DIM, T>(B, B);
   const unsigned grid = static_cast<unsigned>(g.count);
-#define MG_BS(AM, OP) k_bsweep<DIM, T, AM, OP, B><<<grid, threads, smem, s>>>(ba, g.items, g.part_off, src, dst)
+#define MG_BS(AM, OP)                                                                                 \
+  do {                                                                                                \
+    if constexpr (col)                                                                                \
+      k_bsweep_col<DIM, T, AM, OP><<<grid, 128, smem, s>>>(ba, g.items, g.part_off, src, dst);         \
+    else                                                                                              \
+      k_bsweep<DIM, T, AM, OP, B><<<grid, threads, smem, s>>>(ba, g.items, g.part_off, src, dst);      \
+  } while (0)
 #define MG_BS_OPS(AM)                          \
   do {                                         \
     if (op == kJacobi) MG_BS(AM, kJacobi);     \

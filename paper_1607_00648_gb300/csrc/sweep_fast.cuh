@@ -46,14 +46,15 @@ __device__ __forceinline__ void stencil2(T sw, T se, T nw, T ne, T um_l, T um, T
 // vertices are fetched into registers meanwhile; after one barrier each thread
 // applies the stencil to its vertices from shared memory.
 template <typename T, int AMODE, int OP, int R>
-__global__ void __launch_bounds__(128) k_sweep2c(SweepArgs<T> a) {
+__device__ __forceinline__ double sweep2c_item(const SweepArgs<T>& a, int64_t brick, int slab) {
   constexpr int B = 27, Bu = B + 2, Be = B + 1, NR = (R + 3) / 4;
   __shared__ __align__(16) T su[(R + 2) * Bu];
   __shared__ __align__(16) T se[(R + 1) * Be];
   const LevelDesc& L = a.L;
   const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
-  const int64_t brick = blockIdx.x, base = brick * L.S;
-  const int z0 = blockIdx.y * R;
+  const int64_t base = brick * L.S;
+  const int z0 = slab * R;
+  __syncthreads();  // the tile may still be read by a previous item of this CTA
   const int32_t* bn = L.brick_nbr + brick * 9;
   const int x = lane - 1;
   // this thread's vertices: rows zl = g + 4 k of the slab, column x in [0, 27)
@@ -125,6 +126,12 @@ __global__ void __launch_bounds__(128) k_sweep2c(SweepArgs<T> a) {
       a.out[slot] = res;
     }
   }
+  return part;
+}
+
+template <typename T, int AMODE, int OP, int R>
+__global__ void __launch_bounds__(128) k_sweep2c(SweepArgs<T> a) {
+  const double part = sweep2c_item<T, AMODE, OP, R>(a, blockIdx.x, blockIdx.y);
   if constexpr (OP == kResidual) {
     if (a.partial) store_partial_and_finish(part, a.partial, a.counter, a.norm2);
   }
@@ -138,12 +145,13 @@ __global__ void __launch_bounds__(128) k_sweep2c(SweepArgs<T> a) {
 // below / at the vertex carried in registers.  Vertex formula as in sweep_item:
 //   (A u)_v = h/12 (5 sC u_v - sum_c q_c + sum_axis nbr n  S_n u_n).
 template <typename T, int AMODE, int OP, int R>
-__global__ void __launch_bounds__(128, 8) k_sweep3c(SweepArgs<T> a) {
+__device__ __forceinline__ double sweep3c_item(const SweepArgs<T>& a, int64_t brick, int slab,
+                                               unsigned char* smem_raw) {
   constexpr int B = 9, Bu = 11, Be = 10, UPL = Bu * Bu, EPL = Be * Be, PL = B * B, N3 = 27;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   const LevelDesc& L = a.L;
-  const int z0 = blockIdx.y * R;
-  const int64_t brick = blockIdx.x, base = brick * L.S;
+  const int z0 = slab * R;
+  const int64_t base = brick * L.S;
+  __syncthreads();  // the tile may still be read by a previous item of this CTA
   const int32_t* bn = L.brick_nbr + brick * N3;
   T* su = reinterpret_cast<T*>(smem_raw);
   T* se = su + UPL * (R + 2);
@@ -255,8 +263,36 @@ __global__ void __launch_bounds__(128, 8) k_sweep3c(SweepArgs<T> a) {
       u0 = ua;
     }
   }
+  return part;
+}
+
+template <typename T, int AMODE, int OP, int R>
+__global__ void __launch_bounds__(128, 8) k_sweep3c(SweepArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const double part = sweep3c_item<T, AMODE, OP, R>(a, blockIdx.x, blockIdx.y, smem_raw);
   if constexpr (OP == kResidual) {
     if (a.partial) store_partial_and_finish(part, a.partial, a.counter, a.norm2);
+  }
+}
+
+// FP32 column kernels for a runtime slab depth (batched sweeps: items of one launch
+// may come from levels with different slabs)
+template <int DIM, typename T, int AMODE, int OP>
+__device__ __forceinline__ double sweep_col_item(const SweepArgs<T>& a, int64_t brick, int slab,
+                                                 unsigned char* smem_raw) {
+  if constexpr (DIM == 2) {
+    switch (a.R) {
+      case 1: return sweep2c_item<T, AMODE, OP, 1>(a, brick, slab);
+      case 3: return sweep2c_item<T, AMODE, OP, 3>(a, brick, slab);
+      case 9: return sweep2c_item<T, AMODE, OP, 9>(a, brick, slab);
+      default: return sweep2c_item<T, AMODE, OP, 27>(a, brick, slab);
+    }
+  } else {
+    switch (a.R) {
+      case 1: return sweep3c_item<T, AMODE, OP, 1>(a, brick, slab, smem_raw);
+      case 3: return sweep3c_item<T, AMODE, OP, 3>(a, brick, slab, smem_raw);
+      default: return sweep3c_item<T, AMODE, OP, 9>(a, brick, slab, smem_raw);
+    }
   }
 }
 
