@@ -724,25 +724,44 @@ mg_status mg_batch_setup(mg_batch* batch, const double* const* eps, void* stream
     return MG_ERR_INVALID_ARG;
   }
   cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : bt->own;
-  for (int p = 0; p < bt->n; ++p) {
+  for (int p = 0; p < bt->n; ++p)
     if (!eps[p]) {
       set_error("mg_batch_setup: NULL coefficients");
       return MG_ERR_INVALID_ARG;
     }
-    const mg_status st = setup_enqueue(*bt->H[p], eps[p], s);
-    if (st != MG_OK) return st;
+  // fork: every problem's setup on its hierarchy's own stream, after the work already on
+  // s (the coefficients); the small setups of many problems then overlap on the GPU.
+  // Each status word comes back into the hierarchy's pinned slot; join on s.
+  std::vector<cudaEvent_t> ev(static_cast<size_t>(bt->n) + 1, nullptr);
+  auto release = [&] {
+    for (cudaEvent_t e : ev)
+      if (e) cudaEventDestroy(e);
+  };
+  mg_status st = MG_OK;
+  bool ok = true;
+  for (size_t i = 0; i < ev.size() && ok; ++i) ok = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming) == cudaSuccess;
+  ok = ok && cudaEventRecord(ev[bt->n], s) == cudaSuccess;
+  for (int p = 0; p < bt->n && ok && st == MG_OK; ++p) {
+    Hier& H = *bt->H[p];
+    ok = cudaStreamWaitEvent(H.own, ev[bt->n], 0) == cudaSuccess;
+    if (ok) st = setup_enqueue(H, eps[p], H.own);
+    ok = ok && cudaMemcpyAsync(reinterpret_cast<int*>(H.h_pin + 15), H.d_status, sizeof(int),
+                               cudaMemcpyDeviceToHost, H.own) == cudaSuccess &&
+         cudaEventRecord(ev[p], H.own) == cudaSuccess && cudaStreamWaitEvent(s, ev[p], 0) == cudaSuccess;
   }
-  if (cudaStreamSynchronize(s) != cudaSuccess) {
+  if (st != MG_OK) {
+    cudaStreamSynchronize(s);
+    release();
+    return st;
+  }
+  if (!ok || cudaStreamSynchronize(s) != cudaSuccess) {
+    release();
     set_error(std::string("mg_batch_setup: ") + cudaGetErrorString(cudaGetLastError()));
     return MG_ERR_CUDA;
   }
+  release();
   for (int p = 0; p < bt->n; ++p) {
-    int status = 0;
-    if (cudaMemcpy(&status, bt->H[p]->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
-      set_error("mg_batch_setup: status read failed");
-      return MG_ERR_CUDA;
-    }
-    const mg_status st = setup_status(*bt->H[p], status);
+    st = setup_status(*bt->H[p], *reinterpret_cast<const int*>(bt->H[p]->h_pin + 15));
     if (st != MG_OK) return st;
   }
   return MG_OK;
