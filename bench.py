@@ -222,6 +222,11 @@ def run_adaptive(args):
 
     Hmx = mg.Hierarchy(grid, precision="mixed_bf16")
     H64 = mg.Hierarchy(grid, precision="fp64")
+    tiles = {}
+    if not args.no_autotune:
+        for name, H in (("mixed", Hmx), ("fp64", H64)):
+            H.setup(eps_dev)
+            tiles[name] = {str(k): v for k, v in H.autotune().items()}
     do64, domx = args.precision in ("both", "fp64"), args.precision in ("both", "mixed")
     with Clocks(torch.cuda.current_device()) as clk:
         if domx:
@@ -287,7 +292,8 @@ def run_adaptive(args):
         "config": {"workload": args.workload, "description": w["desc"], "dofs": n_dofs,
                    "level5_dofs": int(nd_L), "inner_cycles": rmx["cycles"], "outer_steps": rmx["outer_steps"],
                    "rel_residual": rmx["rel_residual"], "parallelism": "replicas1",
-                   "l2": "flushed (512 MB write) before every timed step", "setup_included": True},
+                   "l2": "flushed (512 MB write) before every timed step", "setup_included": True,
+                   "tiles": tiles or "default rule"},
         "fp64": None if not (do64 and domx) else {
             "value": value64, "unit": "DoF/s", "ms_per_step": t64 / args.steps, "cycles": r64["cycles"],
             "rel_residual": r64["rel_residual"], "mixed_speedup": value / value64},
@@ -424,6 +430,11 @@ def run_ours(args):
 
     H64 = mg.Hierarchy(grid, transfer=w["transfer"], coarse=w["coarse"], precision="fp64")
     Hmx = mg.Hierarchy(grid, transfer=w["transfer"], coarse=w["coarse"], precision="mixed_bf16")
+    tiles = {}
+    if not args.no_autotune:  # slab depths by measurement, once, outside the timed region
+        for name, H in (("fp64", H64), ("mixed", Hmx)):
+            H.setup(eps_dev)
+            tiles[name] = {str(k): v for k, v in H.autotune().items()}
     do64, domx = args.precision in ("both", "fp64"), args.precision in ("both", "mixed")
     with Clocks(torch.cuda.current_device()) as clk:
         if do64:
@@ -503,7 +514,8 @@ def run_ours(args):
             "dtype": "f64" if do64 else "f32 cycles + f64 refinement, bf16 deltas", "data": "synthetic",
             "config": {"workload": args.workload, "description": w["desc"], "dofs": n_dofs,
                        "cycles_per_solve": st64[-1]["cycles"], "parallelism": f"replicas{world}",
-                       "l2": "flushed (512 MB write) before every timed step", "setup_included": True},
+                       "l2": "flushed (512 MB write) before every timed step", "setup_included": True,
+                       "tiles": tiles or "default rule"},
             "mixed": None if not (domx and do64) else {
                 "value": value_mx, "unit": "DoF/s", "dtype": "f32 cycles + f64 refinement, bf16 deltas",
                 "ms_per_step": tmx / args.steps, "inner_cycles": stmx[-1]["cycles"],
@@ -770,6 +782,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="checker2d-l6", choices=sorted(WORKLOADS) + sorted(ADAPTIVE))
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline leg")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default slab depths (no mg_autotune)")
     ap.add_argument("--precision", default="both", choices=("both", "fp64", "mixed"),
                     help="which solve forms to time (profiling runs; the default times both)")
     ap.add_argument("--batched", action="store_true", help="task config 4: batched mixed vs FP64 solves")

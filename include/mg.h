@@ -226,6 +226,15 @@ mg_status mg_vcycle_f32(mg_hier* h, float* u, const float* b, void* stream); /* 
 mg_status mg_residual_norm_noalloc(mg_hier* h, int level, const double* u, const double* b, double* r,
                                    double* norm2, void* stream);
 
+/* Tile autotuner (A13): for every level, time the smoother with each slab depth R
+ * dividing the brick edge (B, B/3, ..., 1 planes per CTA) on the level's own buffers
+ * and keep the fastest for later sweeps of this hierarchy (FP64 sweeps; FP32 sweeps on
+ * a mixed hierarchy).  Results are unchanged by the choice (every vertex is computed by
+ * the same arithmetic); only the split of work over CTAs differs.  chosen (host,
+ * nullable, 2 * (max_level + 1) ints): [2l] the FP64 and [2l+1] the FP32 depth of
+ * level l (0 where not tuned).  Call after mg_setup; synchronises stream. */
+mg_status mg_autotune(mg_hier* h, int32_t* chosen, void* stream);
+
 /* ---------------------------------------------------------------- A12 cycles */
 
 /* One V(nu1, nu2) cycle on the finest level (correction scheme; on uniform

@@ -197,6 +197,14 @@ class Hierarchy:
         check(load().mg_interpolate_hanging(self._h, level, _dptr(u_coarse), _dptr(u_fine), _stream_ptr(stream)),
               "mg_interpolate_hanging")
 
+    def autotune(self, stream=None) -> dict:
+        """Time each level's smoother per slab depth and keep the fastest (mg_autotune);
+        returns {level: (fp64 depth, fp32 depth)} with 0 where a type was not tuned."""
+        L = self.grid.max_level
+        chosen = (C.c_int32 * (2 * (L + 1)))()
+        check(load().mg_autotune(self._h, chosen, _stream_ptr(stream)), "mg_autotune")
+        return {lv: (chosen[2 * lv], chosen[2 * lv + 1]) for lv in range(self.options.coarsest_level, L + 1)}
+
     def vcycle(self, u, b, stream=None):
         check(load().mg_vcycle(self._h, _dptr(u), _dptr(b), _stream_ptr(stream)), "mg_vcycle")
 

@@ -76,6 +76,7 @@ _SIGS = {
     "mg_prolong": (C.c_int, [_P, C.c_int, _P, _P, _P]),
     "mg_interpolate_hanging": (C.c_int, [_P, C.c_int, _P, _P, _P]),
     "mg_vcycle": (C.c_int, [_P, _P, _P, _P]),
+    "mg_autotune": (C.c_int, [_P, C.POINTER(C.c_int32), _P]),
     "mg_solve": (C.c_int, [_P, _P, _P, C.c_double, C.c_int, C.POINTER(SolveStats), _P]),
     "mg_get_stencils": (C.c_int, [_P, C.c_int, _P, _P]),
     "mg_get_deltas": (C.c_int, [_P, C.c_int, _P, _P, _P]),

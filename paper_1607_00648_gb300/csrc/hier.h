@@ -32,6 +32,7 @@ struct DevLevel {
   double *u = nullptr, *b = nullptr, *r = nullptr, *t = nullptr;
   float *u32 = nullptr, *b32 = nullptr, *r32 = nullptr, *t32 = nullptr;
   double* dinv = nullptr;  // FP64 hierarchies: omega / diag(A) for the Jacobi sweeps
+  int R64 = 0, R32 = 0;    // slab depths picked by mg_autotune (0: the default rule)
   double* partial = nullptr;
   unsigned* counter = nullptr;
   int64_t n_dofs = 0;

@@ -652,7 +652,8 @@ static SweepArgs<T> sweep_args(const Hier& H, int l, const T* u, const T* b, T* 
   a.b = b;
   a.out = out;
   a.omega = static_cast<T>(H.opt.omega);
-  a.R = sweep_slab<T>(H.dim, D.d.B, D.d.n_bricks);
+  const int tuned = std::is_same<T, double>::value ? D.R64 : D.R32;
+  a.R = tuned > 0 ? tuned : sweep_slab<T>(H.dim, D.d.B, D.d.n_bricks);
   *amode = 0;
   if constexpr (std::is_same<T, double>::value) {
     a.eps = D.eps;
@@ -905,6 +906,45 @@ mg_status setup_enqueue(Hier& H, const double* eps, cudaStream_t s) { return run
 
 static cudaStream_t pick(Hier& H, void* stream) {
   return stream ? static_cast<cudaStream_t>(stream) : H.own;
+}
+
+// Slab depth per level and sweep type by measurement: every divisor R of the brick edge
+// (B, B/3, ..., 1) is timed on the level's own buffers (Jacobi sweeps, CUDA events on
+// s) and the fastest kept.  The sweeps compute the same values for every R; only the
+// work split over CTAs changes.
+template <typename T>
+static mg_status tune_level(Hier& H, int l, cudaStream_t s, int* best_out) {
+  DevLevel& D = H.lv[l];
+  T* u = lvec<T>(H, l, 2);
+  T* out = lvec<T>(H, l, 3);
+  const T* b = std::is_same<T, double>::value ? reinterpret_cast<const T*>(D.eps) : reinterpret_cast<const T*>(D.eps32);
+  cudaEvent_t e0, e1;
+  MG_TRY_CUDA(cudaEventCreate(&e0));
+  MG_TRY_CUDA(cudaEventCreate(&e1));
+  int best = 0;
+  float best_ms = 0.0f;
+  for (int R = D.d.B; R >= 1; R /= 3) {
+    int amode = 0;
+    SweepArgs<T> a = sweep_args<T>(H, l, u, b, out, &amode);
+    a.R = R;
+    for (int k = 0; k < 2; ++k) launch<T>(H, a, kJacobi, amode, s);
+    cudaEventRecord(e0, s);
+    constexpr int reps = 5;
+    for (int k = 0; k < reps; ++k) launch<T>(H, a, kJacobi, amode, s);
+    cudaEventRecord(e1, s);
+    if (cudaEventSynchronize(e1) != cudaSuccess) break;
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (best == 0 || ms < best_ms) {
+      best = R;
+      best_ms = ms;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  MG_CHECK(last_launch("mg_autotune"));
+  *best_out = best;
+  return MG_OK;
 }
 
 // capture fn() on stream s into g (re-captured when the key pointers change)
@@ -1634,6 +1674,32 @@ mg_status mg_interpolate_hanging(mg_hier* h, int level, const double* u_coarse, 
     k_hanging<3, double><<<nblk(F.d.n_slots), kBlock, 0, s>>>(F.d, F.hang_idx, F.hang_w, u_coarse, u_fine,
                                                               nullptr, 0);
   return last_launch("mg_interpolate_hanging");
+}
+
+mg_status mg_autotune(mg_hier* h, int32_t* chosen, void* stream) {
+  Hier* H = H_(h);
+  MG_CHECK(check_level(H, H ? H->L : 0, true));
+  cudaStream_t s = pick(*H, stream);
+  for (int l = H->c; l <= H->L; ++l) {
+    DevLevel& D = H->lv[l];
+    int r64 = 0, r32 = 0;
+    if (D.dinv || l == H->L) MG_CHECK(tune_level<double>(*H, l, s, &r64));  // FP64 sweeps of this hierarchy
+    if (H->mixed) MG_CHECK(tune_level<float>(*H, l, s, &r32));
+    D.R64 = r64;
+    D.R32 = r32;
+    if (chosen) {
+      chosen[2 * l] = r64;
+      chosen[2 * l + 1] = r32;
+    }
+  }
+  // captured cycles carry the old launch shapes
+  H->g_cycle64.reset();
+  H->g_outer.reset();
+  H->g_inner.reset();
+  H->g_comp64.reset();
+  H->g_comp_outer.reset();
+  H->g_comp_inner.reset();
+  return MG_OK;
 }
 
 mg_status mg_vcycle(mg_hier* h, double* u, const double* b, void* stream) {

@@ -247,6 +247,33 @@ def test_full_size_config2_sampled_parity():
         assert err.max() < TOL
 
 
+@pytest.mark.parametrize("dim,L,precision", [(2, 6, "fp64"), (2, 6, "mixed_bf16"), (3, 4, "mixed_bf16")])
+def test_autotune_changes_launch_shapes_not_results(dim, L, precision):
+    # the slab depth only splits the same per-vertex arithmetic over CTAs: a V-cycle
+    # before and after tuning gives bit-identical iterates; chosen depths divide B
+    c = Case(dim, L, "checker", precision=precision, oracle=False)
+    torch = c.torch
+    u0 = c.random_vec(L, 4)
+    ua = c.dev(u0)
+    c.H.vcycle(ua, c.b_dev)
+    if precision != "fp64":
+        fa = torch.from_numpy(u0.astype(np.float32)).cuda()
+        c.H.vcycle_f32(fa, c.b_dev.float())
+    chosen = c.H.autotune()
+    for lv, (r64, r32) in chosen.items():
+        B = c.grid.info(lv).brick_edge
+        for r in (r64, r32):
+            assert r == 0 or (r in (1, 3, 9, 27) and B % r == 0)
+    assert any(r > 0 for pair in chosen.values() for r in pair)
+    ub = c.dev(u0)
+    c.H.vcycle(ub, c.b_dev)
+    assert torch.equal(ua, ub)
+    if precision != "fp64":
+        fb = torch.from_numpy(u0.astype(np.float32)).cuda()
+        c.H.vcycle_f32(fb, c.b_dev.float())
+        assert torch.equal(fa, fb)
+
+
 def test_edge_cases():
     mg = lib()
     import torch
