@@ -26,6 +26,32 @@ struct LevelDesc {
 
 __host__ __device__ constexpr int cpow(int b, int e) { return e == 0 ? 1 : b * cpow(b, e - 1); }
 
+// Programmatic dependent launch: the kernels of a cycle are launched with programmatic
+// stream serialization (launch_pdl), so a kernel's CTAs are scheduled while its
+// predecessor still runs; pdl_enter makes each wait for the predecessor's results and
+// then lets its own successor start launching.  Without the launch attribute both are
+// no-ops.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;\n" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+inline void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Args... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // FEM element matrix of -div(eps grad u) for d-linear elements on a unit cube, by
 // Hamming distance of the two corners (Sect. 4): 2D 2/3, -1/6, -1/3; 3D 1/3, 0,
 // -1/12, -1/12 (times h in 3D, applied by the caller).

@@ -322,6 +322,7 @@ __device__ __forceinline__ double sweep_item(const SweepArgs<T>& a, int64_t bric
 template <int DIM, typename T, int AMODE, int OP, int B>
 __global__ void __launch_bounds__(kBlock) k_sweep(SweepArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  pdl_enter();
   const double part = sweep_item<DIM, T, AMODE, OP, B>(a, blockIdx.x, blockIdx.y, smem_raw);
   if constexpr (OP == kResidual) {
     if (a.partial) store_partial_and_finish(part, a.partial, a.counter, a.norm2);
@@ -444,6 +445,7 @@ __global__ void __launch_bounds__(32 * kRestrictWarps)
   __shared__ T wtab[N5];  // d-linear weights by tap, formed once per CTA (FP64 units are scarce)
   for (int k = threadIdx.x; k < N5; k += blockDim.x) wtab[k] = dlin_weight<DIM, T>(k);
   __syncthreads();
+  pdl_enter();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t i = blockIdx.x * 32LL + lane;
   const int64_t cs = list ? (i < n_list ? list[i] : -1) : (i < Lc.n_slots ? i : -1);
@@ -530,6 +532,7 @@ __global__ void __launch_bounds__(kBlock) k_prolong(LevelDesc Lc, LevelDesc Lf, 
   __shared__ T wtab[N5];  // d-linear weights by offset, formed once per CTA
   for (int k = threadIdx.x; k < N5; k += blockDim.x) wtab[k] = dlin_weight<DIM, T>(k);
   __syncthreads();
+  pdl_enter();
   const int64_t i = blockIdx.x * static_cast<int64_t>(kBlock) + threadIdx.x;
   if (list) {
     if (i < n_list) prolong_one<DIM, T, PMODE, BC, BF>(Lc, Lf, ec, uf, phat, pscale, list[i], wtab);

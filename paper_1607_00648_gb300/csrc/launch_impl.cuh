@@ -21,8 +21,8 @@ static void sweep_b(SweepArgs<T> a, int op, int amode, cudaStream_t s) {
     const size_t sm = DIM == 2 ? 0 : sweep_tile_bytes<DIM, T>(B, R, true);
 #define MG_SWR(AM, OP, RR)                                                                \
   do {                                                                                    \
-    if constexpr (DIM == 2) k_sweep2c<T, AM, OP, RR><<<grid, 128, 0, s>>>(a);               \
-    else k_sweep3c<T, AM, OP, (RR > 9 ? 9 : RR)><<<grid, 128, sm, s>>>(a);                  \
+    if constexpr (DIM == 2) launch_pdl(k_sweep2c<T, AM, OP, RR>, grid, 128, 0, s, a);        \
+    else launch_pdl(k_sweep3c<T, AM, OP, (RR > 9 ? 9 : RR)>, grid, 128, sm, s, a);           \
   } while (0)
 #define MG_SW(AM, OP)                                                    \
   do {                                                                   \
@@ -42,7 +42,7 @@ static void sweep_b(SweepArgs<T> a, int op, int amode, cudaStream_t s) {
     const dim3 grid(static_cast<unsigned>(a.L.n_bricks), static_cast<unsigned>(B / R));
     int threads = ((R * PLANE + 31) / 32) * 32;
     if (threads > kBlock) threads = kBlock;
-#define MG_SW(AM, OP) k_sweep<DIM, T, AM, OP, B><<<grid, threads, smem, s>>>(a)
+#define MG_SW(AM, OP) launch_pdl(k_sweep<DIM, T, AM, OP, B>, grid, threads, smem, s, a)
     if constexpr (std::is_same<T, double>::value) {
       if (op == kJacobi) {
         if (amode == 1) MG_SW(1, kJacobi); else MG_SW(0, kJacobi);
@@ -71,9 +71,9 @@ static void transfer_b(const LevelDesc& Lc, const LevelDesc& Lf, bool restrict_o
 #define MG_TR(PM)                                                                                   \
   do {                                                                                              \
     if (restrict_op)                                                                                \
-      k_restrict<DIM, T, PM, BC, BF><<<gc, 32 * kRestrictWarps, 0, s>>>(Lc, Lf, in, out, ph, ps, li, nl, zc); \
+      launch_pdl(k_restrict<DIM, T, PM, BC, BF>, gc, 32 * kRestrictWarps, 0, s, Lc, Lf, in, out, ph, ps, li, nl, zc); \
     else                                                                                            \
-      k_prolong<DIM, T, PM, BC, BF><<<gf, kBlock, 0, s>>>(Lc, Lf, in, out, ph, ps, li, nl);         \
+      launch_pdl(k_prolong<DIM, T, PM, BC, BF>, gf, kBlock, 0, s, Lc, Lf, in, out, ph, ps, li, nl);   \
   } while (0)
   if constexpr (std::is_same<T, double>::value) {
     if (pmode == 1) MG_TR(1); else MG_TR(0);

@@ -258,6 +258,7 @@ template <typename T>
 __global__ void __launch_bounds__(kBlock) k_coarse_solve(const double* Lm, int n, const int32_t* c_slots, const T* b,
                                                            T* u) {
   extern __shared__ double y[];
+  pdl_enter();
   for (int i = threadIdx.x; i < n; i += kBlock) y[i] = static_cast<double>(b[c_slots[i]]);
   __syncthreads();
   for (int k = 0; k < n; ++k) {  // L y = b
@@ -278,6 +279,7 @@ __global__ void __launch_bounds__(kBlock) k_coarse_solve(const double* Lm, int n
 // the same for at most 32 unknowns: one thread, no barriers
 template <typename T>
 __global__ void k_coarse_solve_small(const double* Lm, int n, const int32_t* c_slots, const T* b, T* u) {
+  pdl_enter();
   if (threadIdx.x != 0) return;
   double y[32];
   for (int i = 0; i < n; ++i) {
@@ -720,9 +722,11 @@ static void transfer(const Hier& H, int fine, bool restrict_op, const T* in, T* 
 template <typename T>
 static void coarse_solve(const Hier& H, const T* b, T* u, cudaStream_t s) {
   if (H.n_c <= 32)
-    k_coarse_solve_small<T><<<1, 32, 0, s>>>(H.c_mat, H.n_c, H.c_slots, b, u);
+    launch_pdl(k_coarse_solve_small<T>, 1, 32, 0, s, static_cast<const double*>(H.c_mat), H.n_c,
+               static_cast<const int32_t*>(H.c_slots), b, u);
   else
-    k_coarse_solve<T><<<1, kBlock, H.n_c * sizeof(double), s>>>(H.c_mat, H.n_c, H.c_slots, b, u);
+    launch_pdl(k_coarse_solve<T>, 1, kBlock, H.n_c * sizeof(double), s, static_cast<const double*>(H.c_mat),
+               H.n_c, static_cast<const int32_t*>(H.c_slots), b, u);
 }
 
 // nu damped Jacobi sweeps, ping-pong through tmp, result in u

@@ -131,6 +131,7 @@ __device__ __forceinline__ double sweep2c_item(const SweepArgs<T>& a, int64_t br
 
 template <typename T, int AMODE, int OP, int R>
 __global__ void __launch_bounds__(128) k_sweep2c(SweepArgs<T> a) {
+  pdl_enter();
   const double part = sweep2c_item<T, AMODE, OP, R>(a, blockIdx.x, blockIdx.y);
   if constexpr (OP == kResidual) {
     if (a.partial) store_partial_and_finish(part, a.partial, a.counter, a.norm2);
@@ -269,6 +270,7 @@ __device__ __forceinline__ double sweep3c_item(const SweepArgs<T>& a, int64_t br
 template <typename T, int AMODE, int OP, int R>
 __global__ void __launch_bounds__(128, 8) k_sweep3c(SweepArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  pdl_enter();
   const double part = sweep3c_item<T, AMODE, OP, R>(a, blockIdx.x, blockIdx.y, smem_raw);
   if constexpr (OP == kResidual) {
     if (a.partial) store_partial_and_finish(part, a.partial, a.counter, a.norm2);
