@@ -189,6 +189,7 @@ struct Batch {
   BatchState state{};
   cudaStream_t own = nullptr;
   int priority = 0;
+  bool blocking = true;
   ~Batch() {  // the caller has made sure no work of the batch is pending
     graph.reset();
     for (void* p : allocs) pool_free(p, own);
@@ -342,7 +343,8 @@ void emit_mixed_step(Batch& bt, const BatchState& st, cudaStream_t s) {
 }
 
 mg_status build_batch(Batch& bt) {
-  if (cudaStreamCreateWithPriority(&bt.own, cudaStreamDefault, bt.priority) != cudaSuccess) {
+  if (cudaStreamCreateWithPriority(&bt.own, bt.blocking ? cudaStreamDefault : cudaStreamNonBlocking, bt.priority) !=
+      cudaSuccess) {
     set_error("mg_batch_create: cudaStreamCreate failed");
     return MG_ERR_CUDA;
   }
@@ -486,7 +488,7 @@ mg_status status_of(int st) {
 
 void batch_set_graph(Batch* bt, bool use_graph) { bt->use_graph = use_graph; }
 
-mg_status batch_create(const std::vector<Hier*>& hs, Batch** out, int priority) {
+mg_status batch_create(const std::vector<Hier*>& hs, Batch** out, int priority, bool blocking) {
   *out = nullptr;
   if (hs.empty()) {
     set_error("batch: no problems");
@@ -500,6 +502,7 @@ mg_status batch_create(const std::vector<Hier*>& hs, Batch** out, int priority) 
   bt->n = static_cast<int>(hs.size());
   bt->H = hs;
   bt->priority = priority;
+  bt->blocking = blocking;
   const mg_status st = build_batch(*bt);
   if (st != MG_OK) {
     delete bt;

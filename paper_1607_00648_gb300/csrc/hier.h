@@ -94,8 +94,9 @@ void* pinned_slot();
 void pinned_release(void* p);
 // destroy a hierarchy whose work is known to be complete (no device synchronisation)
 void hier_release(Hier* H);
-// mg_hier_create with the hierarchy's stream at a given priority
-mg_status hier_create(const Grid* g, const mg_options& o, int priority, Hier** out);
+// mg_hier_create with the hierarchy's stream at a given priority; blocking false gives it
+// a non-blocking stream (for hierarchies that only ever run on explicit streams)
+mg_status hier_create(const Grid* g, const mg_options& o, int priority, Hier** out, bool blocking = true);
 
 // enqueue a hierarchy's setup without synchronising; setup_status interprets d_status
 mg_status setup_enqueue(Hier& H, const double* eps, cudaStream_t s);
@@ -108,7 +109,8 @@ struct ProblemState {
   double r0, rel, sigma, tol;
   int max_cycles;
 };
-mg_status batch_create(const std::vector<Hier*>& hs, Batch** out, int priority = 0);  // priority: of its own stream
+mg_status batch_create(const std::vector<Hier*>& hs, Batch** out, int priority = 0,
+                       bool blocking = true);  // priority / blocking: of its own stream
 void batch_destroy(Batch* bt);
 void batch_set_graph(Batch* bt, bool use_graph);
 mg_status batch_begin(Batch& bt, double* const* u, const double* const* b, const std::vector<ProblemState>& init,

@@ -149,7 +149,7 @@ void Server::worker(int lane) {
       ++creating;
     }
     Hier* h = nullptr;
-    mg_status st = hier_create(r->grid, opt, prio[lane], &h);
+    mg_status st = hier_create(r->grid, opt, prio[lane], &h, false);
     if (st == MG_OK) {
       r->h = h;
       cudaStream_t ss = setup_streams[lane][next_setup[lane]++ % kSetupStreams];
@@ -293,7 +293,7 @@ bool Server::start_step(Lane& ln, int lane) {
       init.push_back(ps);
       fresh.push_back(std::find(old.begin(), old.end(), r) == old.end() ? 1 : 0);
     }
-    mg_status st = batch_create(hs, &ln.batch, prio[&ln == &lanes[0] ? 0 : 1]);
+    mg_status st = batch_create(hs, &ln.batch, prio[&ln == &lanes[0] ? 0 : 1], false);
     if (st == MG_OK) batch_set_graph(ln.batch, false);
     if (st == MG_OK) st = batch_begin(*ln.batch, us.data(), bs.data(), init, fresh, ln.stream);
     if (st != MG_OK) {

@@ -423,7 +423,7 @@ void hier_release(Hier* H) { free_hier(H, false); }
 
 static inline unsigned nblk(int64_t n) { return static_cast<unsigned>((n + kBlock - 1) / kBlock); }
 
-static mg_status create(const Grid* g, const mg_options& o, Hier** out, int priority) {
+static mg_status create(const Grid* g, const mg_options& o, Hier** out, int priority, bool blocking) {
   Hier* H = new (std::nothrow) Hier();
   if (!H) {
     set_error("mg_hier_create: out of host memory");
@@ -444,9 +444,12 @@ static mg_status create(const Grid* g, const mg_options& o, Hier** out, int prio
     free_hier(H, true);
     return s;
   };
-  // a blocking stream: work given stream NULL runs here, ordered with the legacy
-  // default stream as the stream convention of the interface promises
-  if (cudaStreamCreateWithPriority(&H->own, cudaStreamDefault, priority) != cudaSuccess) {
+  // public hierarchies: a blocking stream, so that work given stream NULL runs here
+  // ordered with the legacy default stream as the interface's stream convention
+  // promises; the server's hierarchies (only ever used on its own streams) take a
+  // non-blocking one, so that their creation does not wait on unrelated work
+  if (cudaStreamCreateWithPriority(&H->own, blocking ? cudaStreamDefault : cudaStreamNonBlocking, priority) !=
+      cudaSuccess) {
     set_error("mg_hier_create: cudaStreamCreate failed");
     return fail(MG_ERR_CUDA);
   }
@@ -586,7 +589,7 @@ static mg_status create(const Grid* g, const mg_options& o, Hier** out, int prio
 
 // options and grid checks of mg_hier_create, then create() with the hierarchy's own
 // stream at the given priority (the server gives small requests the highest)
-mg_status hier_create(const Grid* g, const mg_options& o, int priority, Hier** out) {
+mg_status hier_create(const Grid* g, const mg_options& o, int priority, Hier** out, bool blocking) {
   *out = nullptr;
   if (o.coarsest_level < 1 || o.coarsest_level >= g->L || o.nu1 < 0 || o.nu2 < 0 || !(o.omega > 0.0) ||
       o.transfer < 0 || o.transfer > 1 || o.coarse < 0 || o.coarse > 1 || o.precision < 0 || o.precision > 2) {
@@ -608,7 +611,7 @@ mg_status hier_create(const Grid* g, const mg_options& o, int priority, Hier** o
     }
   }
   try {
-    return create(g, o, out, priority);
+    return create(g, o, out, priority, blocking);
   } catch (const std::bad_alloc&) {
     set_error("mg_hier_create: out of host memory");
     return MG_ERR_OOM;
