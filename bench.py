@@ -360,6 +360,22 @@ def run_breakdown(args):
     print(json.dumps(out))
 
 
+def max_over_ranks(ms, dist=None, device=None):
+    """The slowest rank's time (replicas: the job ends when the last one does)."""
+    if dist is None:
+        return ms
+    import torch
+
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(units_per_rank, steps, world, slowest_ms):
+    """Whole-job rate of N independent replicas: every rank's units over the slowest time."""
+    return units_per_rank * steps * world / (slowest_ms / 1e3)
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -422,11 +438,7 @@ def run_ours(args):
             o = H.options
             launches += kernel_count(L, o.coarsest_level, o.nu1, o.nu2, w["transfer"], w["coarse"], prec,
                                      res["cycles"], res["outer_steps"], o.inner_cycles)
-        if dist:
-            t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total_ms = float(t.item())
-        return total_ms, launches, stats
+        return max_over_ranks(total_ms, dist, dev), launches, stats
 
     H64 = mg.Hierarchy(grid, transfer=w["transfer"], coarse=w["coarse"], precision="fp64")
     Hmx = mg.Hierarchy(grid, transfer=w["transfer"], coarse=w["coarse"], precision="mixed_bf16")
@@ -444,8 +456,8 @@ def run_ours(args):
     clocks = clk.summary()
     if not do64:  # mixed only (profiling runs): the line reports the mixed solve
         t64, launches64, st64 = tmx, 0, stmx
-    value = n_dofs * args.steps * world / (t64 / 1e3)
-    value_mx = n_dofs * args.steps * world / (tmx / 1e3) if domx else None
+    value = replica_throughput(n_dofs, args.steps, world, t64)
+    value_mx = replica_throughput(n_dofs, args.steps, world, tmx) if domx else None
 
     # dominant kernel: finest-level FP64 in-situ Jacobi sweep (two sweeps per call, no copy)
     H64.setup(eps_dev)
@@ -493,11 +505,8 @@ def run_ours(args):
         torch.cuda.synchronize()
         if i >= args.warmup:
             e2e_ms += (time.perf_counter() - t0) * 1e3
-    if dist:
-        t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e = {"value": n_dofs * args.steps * world / (e2e_ms / 1e3), "unit": "DoF/s",
+    e2e_ms = max_over_ranks(e2e_ms, dist, dev)
+    e2e = {"value": replica_throughput(n_dofs, args.steps, world, e2e_ms), "unit": "DoF/s",
            "h2d_bytes_per_step": int(eps_h.numel() * 8 + b_h.numel() * 8),
            "d2h_bytes_per_step": int(u_h.numel() * 8)}
 
