@@ -70,7 +70,6 @@ struct Server {
   bool stop = false;
   std::string error;
   std::thread th;
-  cudaStream_t stream = nullptr;
   // setup streams per lane; the small lane's streams (setups and steps) run at the
   // device's highest priority so that their short kernels are not queued behind the
   // large problems' long ones
@@ -386,7 +385,7 @@ mg_status mg_server_create(size_t hbm_budget_bytes, const mg_options* opt, mg_se
   cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high);
   sv->prio[0] = prio_high;
   sv->prio[1] = prio_low;
-  bool ok = cudaStreamCreateWithFlags(&sv->stream, cudaStreamNonBlocking) == cudaSuccess;
+  bool ok = true;
   for (int k = 0; k < Server::kLanes && ok; ++k) {
     const int prio = k == 0 ? prio_high : prio_low;
     ok = cudaStreamCreateWithPriority(&sv->lanes[k].stream, cudaStreamNonBlocking, prio) == cudaSuccess &&
@@ -413,7 +412,6 @@ mg_status mg_server_create(size_t hbm_budget_bytes, const mg_options* opt, mg_se
     for (int k = 0; k < 2; ++k)
       for (auto& t : sv->workers[k])
         if (t.joinable()) t.join();
-    cudaStreamDestroy(sv->stream);
     delete sv;
     set_error("mg_server_create: thread start failed");
     return MG_ERR_OOM;
@@ -539,7 +537,6 @@ void mg_server_destroy(mg_server* server) {
     if (kv.second->ev) cudaEventDestroy(kv.second->ev);
     delete kv.second;
   }
-  cudaStreamDestroy(sv->stream);
   for (int k = 0; k < Server::kLanes; ++k)
     for (int i = 0; i < Server::kSetupStreams; ++i)
       if (sv->setup_streams[k][i]) cudaStreamDestroy(sv->setup_streams[k][i]);

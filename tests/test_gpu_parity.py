@@ -302,3 +302,22 @@ def test_edge_cases():
         c.H.smooth(7, v, c.b_dev, 1)
     with pytest.raises(mg.MgError):
         mg.Hierarchy(c.grid, coarsest_level=2)
+
+
+def test_sin_benchmark_config1():
+    # the paper's `sin` benchmark as the 2D level-4 workload: eps = 1, geometric V(2,2)
+    # (d-linear transfers, rediscretised coarse operators), solved to a 1e-8 drop.  The
+    # GPU takes the oracle's cycles and iterate, and the discrete solution is within
+    # the O(h^2) discretisation error of prod sin(pi x_i)
+    import synthetic as syn
+
+    c = Case(2, 4, "const", "dlinear", "redisc", load="sin")
+    u = c.torch.zeros_like(c.b_dev)
+    res = c.H.solve(u, c.b_dev, rel_tol=1e-8, max_cycles=200)
+    ref, hist = c.O.solve(c.b, 1e-8, 200)
+    assert res["cycles"] == len(hist) - 1
+    got = c.host(u)
+    assert rel_inf(got, ref) < 10 * TOL
+    exact = c.grid.to_slots(4, syn.sin_solution(4, 2))
+    err = np.abs(got - exact)[c.dof(4)].max()
+    assert err < 4.0 / 81**2  # O(h^2) with h = 1/81 (the oracle's discrete solution: 3.8e-4 = 2.5 h^2)
