@@ -43,6 +43,10 @@ WORKLOADS = {
                          coarse="galerkin", tol=1e-10, max_cycles=3000,
                          desc="2D level 6 (729^2 cells, 529,984 DoFs), 9x9 seeded checkerboard {1,1e-4}, "
                               "BoxMG + Galerkin, V(2,2) omega 0.6, to 1e-10"),
+    "jump2d-l6": dict(dim=2, L=6, eps="jump", eps_seed=0, load_seed="unit", transfer="boxmg",
+                      coarse="galerkin", tol=1e-10, max_cycles=3000,
+                      desc="2D level 6, the paper's jump benchmark (eps 1 / 0.1 across x_1 = 0.5, f = 1), "
+                           "BoxMG + Galerkin, V(2,2), to 1e-10"),
     "sin2d-l4": dict(dim=2, L=4, eps="const", eps_seed=0, load_seed=None, transfer="dlinear",
                      coarse="redisc", tol=1e-8, max_cycles=200,
                      desc="2D level 4 (81^2 cells, 6,400 DoFs), sin benchmark, geometric V(2,2), to 1e-8"),
@@ -77,9 +81,14 @@ def inputs(w):
     L, d = w["L"], w["dim"]
     if w["eps"] == "checker":
         eps = syn.checkerboard_eps(L, d, seed=w["eps_seed"])
+    elif w["eps"] == "jump":
+        eps = syn.jump_eps(L, d)
     else:
         eps = syn.constant_eps(L, d)
-    bf = syn.uniform_load(L, d, w["load_seed"]) if w["load_seed"] is not None else syn.sin_load(L, d)
+    if w["load_seed"] == "unit":
+        bf = syn.unit_load(L, d)
+    else:
+        bf = syn.uniform_load(L, d, w["load_seed"]) if w["load_seed"] is not None else syn.sin_load(L, d)
     return eps, bf
 
 

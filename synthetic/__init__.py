@@ -23,6 +23,8 @@ __all__ = [
     "uniform_load",
     "checkerboard_eps",
     "constant_eps",
+    "jump_eps",
+    "unit_load",
     "lognormal_grf_eps",
     "sphere_shell_mask",
     "sphere_eps",
@@ -63,6 +65,22 @@ def uniform_load(level: int, dim: int, seed: int) -> np.ndarray:
 
 def constant_eps(level: int, dim: int, value: float = 1.0) -> np.ndarray:
     return np.full((3**level,) * dim, float(value))
+
+
+def jump_eps(level: int, dim: int, low: float = 1.0, high: float = 0.1) -> np.ndarray:
+    """The paper's `jump` coefficient: `low` where the cell centre has x_1 < 0.5, else `high`."""
+    n = 3**level
+    xc = (np.arange(n) + 0.5) / n
+    col = np.where(xc < 0.5, low, high)
+    shape = [1] * dim
+    shape[0] = n
+    return np.broadcast_to(col.reshape(shape), (n,) * dim).astype(np.float64).copy()
+
+
+def unit_load(level: int, dim: int) -> np.ndarray:
+    """Lumped load b_v = h^d f with f = 1 (the paper's `jump` and `checkerboard` right-hand side)."""
+    n = 3**level + 1
+    return np.full((n,) * dim, (3.0**-level) ** dim)
 
 
 def checkerboard_eps(level: int, dim: int, seed=0, tiles: int = 9,

@@ -29,6 +29,8 @@ def eps_field(kind: str, L: int, dim: int, seed: int = 0) -> np.ndarray:
         return syn.checkerboard_eps(L, dim, seed=seed, tiles=3)
     if kind == "sphere":
         return syn.sphere_eps(L, dim)
+    if kind == "jump":
+        return syn.jump_eps(L, dim)
     if kind == "grf":
         return syn.lognormal_grf_eps(L, dim, sigma=2.0, seed=1000 + seed)
     raise ValueError(kind)
@@ -57,6 +59,8 @@ class Case:
                                       nu1=nu1, nu2=nu2) if oracle else None)
         if load == "sin":
             bf = syn.sin_load(L, dim)
+        elif load == "unit":
+            bf = syn.unit_load(L, dim)
         else:
             bf = syn.uniform_load(L, dim, seed + 1)
         self.b = self.grid.to_slots(L, bf)

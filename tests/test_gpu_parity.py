@@ -321,3 +321,15 @@ def test_sin_benchmark_config1():
     exact = c.grid.to_slots(4, syn.sin_solution(4, 2))
     err = np.abs(got - exact)[c.dof(4)].max()
     assert err < 4.0 / 81**2  # O(h^2) with h = 1/81 (the oracle's discrete solution: 3.8e-4 = 2.5 h^2)
+
+
+@pytest.mark.parametrize("dim,L", [(2, 4), (3, 3)])
+def test_jump_benchmark(dim, L):
+    # the paper's `jump` benchmark (eps 1 left of x_1 = 0.5, 0.1 right of it, f = 1) with
+    # BoxMG + Galerkin: the oracle's cycles and iterate at a 1e-10 drop
+    c = Case(dim, L, "jump", "boxmg", "galerkin", load="unit")
+    u = c.torch.zeros_like(c.b_dev)
+    res = c.H.solve(u, c.b_dev, rel_tol=1e-10, max_cycles=300)
+    ref, hist = c.O.solve(c.b, 1e-10, 300)
+    assert res["cycles"] == len(hist) - 1
+    assert rel_inf(c.host(u), ref) < 10 * TOL * c.amplification()

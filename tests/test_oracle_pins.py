@@ -390,3 +390,14 @@ def test_codec_roundtrip_error_bound():
         m = np.abs(d).max(axis=1, keepdims=True)
         assert np.all(np.abs(back - d) <= (u + 2.0**-23) * 1.01 * m + 1e-300)
         assert np.all(back[3] == 0) and s[3] == 0
+
+
+def test_jump_coefficient_recipe():
+    # eps by cell centre: 1 for x_1 < 0.5, 0.1 beyond; on 3^L cells the jump falls inside
+    # the middle column, which takes the value of its centre (x_1 = 0.5 exactly: 0.1)
+    import synthetic as syn
+
+    e = syn.jump_eps(2, 2)
+    assert e.shape == (9, 9)
+    assert np.all(e[:4] == 1.0) and np.all(e[4:] == 0.1)
+    assert np.all(syn.unit_load(2, 2) == 1.0 / 81)
