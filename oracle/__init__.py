@@ -16,4 +16,5 @@ cited by section, equation, algorithm or appendix:
 * ``galerkin``   -- Galerkin coarse operators A_{l-1} = R A_l P and hierarchical deltas (Sect. 4.3, Sect. 5)
 * ``multigrid``  -- damped Jacobi, residual, transfers, V-cycle, solve (Sect. 4.1, Alg. 1)
 * ``codec``      -- the BF16/FP16 + per-vertex FP32 scale storage of the deltas (Sect. 5, as a dtype)
+* ``bpa``        -- the paper's own byte codec of the deltas, f_bpa = m 2^e with a per-operator bpa (Sect. 5)
 """
