@@ -548,6 +548,80 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_codecs(args):
+    """Mixed solves with the deltas in BF16 + FP32 scale against the paper's bpa codec
+    (Sect. 5) at eps_mf = 1e-2, 1e-4, 1e-8: DoF/s, cycles and stored delta bytes."""
+    import torch
+
+    import paper_1607_00648_gb300 as mg
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    w = WORKLOADS[args.workload]
+    L, d = w["L"], w["dim"]
+    eps, bf = inputs(w)
+    grid = mg.Grid(d, L)
+    n_dofs = grid.info(L).n_dofs
+    eps_dev = torch.from_numpy(grid.cells_to_concat({L: eps})).to(dev)
+    b_dev = torch.from_numpy(grid.to_slots(L, bf)).to(dev)
+    u_dev = torch.zeros_like(b_dev)
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    n3, n5 = 3 ** d, 5 ** d
+    out = {}
+    with Clocks(0) as clk:
+        for name, kw in (("bf16", {"precision": "mixed_bf16"}),
+                         ("bpa_1e-2", {"precision": "mixed_bpa", "eps_mf": 1e-2}),
+                         ("bpa_1e-4", {"precision": "mixed_bpa", "eps_mf": 1e-4}),
+                         ("bpa_1e-8", {"precision": "mixed_bpa", "eps_mf": 1e-8})):
+            H = mg.Hierarchy(grid, transfer=w["transfer"], coarse=w["coarse"], **kw)
+            for _ in range(args.warmup):
+                H.setup(eps_dev)
+                H.solve(u_dev, b_dev, rel_tol=w["tol"], max_cycles=w["max_cycles"])
+            ms, res = 0.0, None
+            for _ in range(args.steps):
+                flush.zero_()
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                H.setup(eps_dev)
+                res = H.solve(u_dev, b_dev, rel_tol=w["tol"], max_cycles=w["max_cycles"])
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms += e0.elapsed_time(e1)
+            coarse_slots = coarse_dofs = stored = 0
+            hist = {}
+            for lv in range(H.options.coarsest_level, L):
+                inf = grid.info(lv)
+                coarse_slots += inf.n_slots
+                coarse_dofs += inf.n_dofs
+                if kw["precision"] == "mixed_bf16":
+                    stored += inf.n_slots * ((n3 + n5) * 2 + 8)
+                else:
+                    ar = torch.empty(inf.n_slots, dtype=torch.int64, device=dev)
+                    pr = torch.empty(inf.n_slots, dtype=torch.int64, device=dev)
+                    na, npb = H.get_bpa(lv, a_rec=ar, p_rec=pr)
+                    stored += na + npb + inf.n_slots * 16
+                    for r in (ar, pr):
+                        vals, cnt = np.unique((r.cpu().numpy().view(np.uint64) & np.uint64(15)).astype(int),
+                                              return_counts=True)
+                        for v, c in zip(vals, cnt):
+                            hist[int(v)] = hist.get(int(v), 0) + int(c)
+            out[name] = {"dofs_per_s": n_dofs * args.steps / (ms / 1e3), "ms_per_step": ms / args.steps,
+                         "inner_cycles": res["cycles"], "outer_steps": res["outer_steps"],
+                         "rel_residual": res["rel_residual"], "delta_bytes": stored,
+                         "delta_bytes_per_coarse_dof": stored / max(coarse_dofs, 1),
+                         "bpa_histogram": hist or None}
+            del H
+    line = {"metric": "DoF/s to 1e-10 residual drop, mixed path by delta codec", "unit": "DoF/s",
+            "value": out["bpa_1e-4"]["dofs_per_s"], "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "dtype": "f32 cycles + f64 refinement", "data": "synthetic",
+            "config": {"workload": args.workload, "description": w["desc"], "dofs": n_dofs,
+                       "l2": "flushed (512 MB write) before every timed step", "setup_included": True},
+            "codecs": out, "clocks": clk.summary()}
+    print(json.dumps(line))
+
+
 def run_sweeps(args):
     """Finest-level in-situ Jacobi sweeps alone on a uniform checkerboard grid of level
     args.sweep_level and dimension args.sweep_dim (2D level 8: 6561^2 cells, 43M DoFs;
@@ -803,6 +877,8 @@ def main():
     ap.add_argument("--no-autotune", action="store_true", help="keep the default slab depths (no mg_autotune)")
     ap.add_argument("--precision", default="both", choices=("both", "fp64", "mixed"),
                     help="which solve forms to time (profiling runs; the default times both)")
+    ap.add_argument("--codecs", action="store_true",
+                    help="mixed solves with BF16 deltas against the bpa codec at eps_mf 1e-2 / 1e-4 / 1e-8")
     ap.add_argument("--batched", action="store_true", help="task config 4: batched mixed vs FP64 solves")
     ap.add_argument("--serve", action="store_true", help="task config 5: served 3D requests, p50 / p99 latency")
     ap.add_argument("--serve-requests", type=int, default=300)
@@ -821,6 +897,8 @@ def main():
         run_serve(args)
     elif args.batched:
         run_batched(args)
+    elif args.codecs:
+        run_codecs(args)
     elif args.sweep_level:
         run_sweeps(args)
     elif args.workload in ADAPTIVE:

@@ -131,7 +131,11 @@ typedef enum mg_coarse_op { MG_COARSE_REDISC = 0, MG_COARSE_GALERKIN = 1 } mg_co
 typedef enum mg_precision {
   MG_PREC_FP64 = 0,       /* everything in FP64, deltas stored in FP64 */
   MG_PREC_MIXED_BF16 = 1, /* FP64 iterative refinement around FP32 V-cycles, deltas BF16 + FP32 scale */
-  MG_PREC_MIXED_FP16 = 2  /* same with FP16 codes */
+  MG_PREC_MIXED_FP16 = 2, /* same with FP16 codes */
+  MG_PREC_MIXED_BPA = 3   /* same with the deltas in the paper's bpa byte codec (Sect. 5):
+                             per vertex and operator bpa in {0, 2..8} bytes per entry, chosen
+                             against mg_options.eps_mf; single hierarchies only (not in
+                             batches, the server or the persistent solve) */
 } mg_precision;
 
 typedef struct mg_options {
@@ -146,9 +150,11 @@ typedef struct mg_options {
   int32_t persistent;     /* 1: whole solve in one cooperative persistent launch;
                              0: host-stepped, CUDA-graph-captured cycles (default: on GB300 a
                              dependent graph kernel costs ~0.6 us, a grid-wide barrier ~1.2 us) */
+  double eps_mf;          /* MG_PREC_MIXED_BPA: absolute bound on |f_bpa(x) - x| per delta entry
+                             (Sect. 5 uses 1e-2, 1e-4, 1e-8); default 1e-4 */
 } mg_options;
 
-void mg_default_options(mg_options* opt); /* BoxMG, Galerkin, FP64, V(2,2), omega 0.6, coarsest 1 */
+void mg_default_options(mg_options* opt); /* BoxMG, Galerkin, FP64, V(2,2), omega 0.6, coarsest 1, eps_mf 1e-4 */
 
 /* ---------------------------------------------------------------- hierarchy */
 
@@ -172,10 +178,11 @@ mg_status mg_hier_footprint(const mg_grid* grid, const mg_options* opt, size_t* 
  * compute coarse coefficients (mean of the 3^d children), BoxMG P per coarse
  * vertex (App. C: one C(s) p = f solve per patch corner), Galerkin A_{l-1} =
  * R A_l P with R = P^T (Sect. 4.3), the hierarchical deltas A_hat, P_hat
- * (Sect. 5), their BF16/FP16 codes for the mixed path, and the FP64 Cholesky
- * factor of the coarsest operator.  Enqueued on stream.
+ * (Sect. 5), their BF16/FP16 codes or bpa byte streams for the mixed path, and the
+ * FP64 Cholesky factor of the coarsest operator.  Enqueued on stream.
  * Errors: MG_ERR_INDEFINITE_COARSE if a coarse stencil has a non-positive
- * diagonal or the coarsest Cholesky fails (Sect. 4.3 definiteness check). */
+ * diagonal or the coarsest Cholesky fails (Sect. 4.3 definiteness check);
+ * MG_ERR_NONFINITE if a delta cannot be stored in the bpa codec. */
 mg_status mg_setup(mg_hier* h, const double* eps, void* stream);
 
 /* ---------------------------------------------------------------- A3-A7 steps (FP64) */
@@ -362,6 +369,34 @@ mg_status mg_get_codes(mg_hier* h, int level, uint16_t* a_codes, float* a_scale,
  * fmt (1 = BF16, 2 = FP16) of delta / scale formed in FP64 (device outputs). */
 mg_status mg_encode_deltas(int64_t n, int k, const double* delta, int fmt, uint16_t* codes, float* scale,
                            void* stream);
+
+/* The bpa byte codec of Sect. 5 on caller buffers (NEXT row: the paper's delta storage).
+ * Each of n rows of k FP64 entries (device, row-major x[i*k + j]) is one operator: it is
+ * dropped (bpa = 0) if every |entry| <= eps_mf, else stored with the smallest bpa in
+ * {2, ..., 8} for which every entry's f_bpa = (-1)^s m 2^e satisfies |f_bpa - x| <= eps_mf.
+ * An entry takes bpa bytes: e (int8), then the bpa - 1 bytes of m little-endian, whose top
+ * bit is the sign s and whose other 8 (bpa - 1) - 1 bits hold |m|; e is the smallest
+ * exponent for which |m| = rint(|x| 2^-e) fits those bits (clamped below at -128).
+ * Outputs (device): rec[i] = (byte offset of row i << 4) | bpa_i, rows one after the
+ * other in `bytes` (capacity n * k * 8 bytes, the worst case), *total_bytes = the
+ * stream's length, *status (nullable) = 0, or 1 if an entry is not finite, 2 if an entry
+ * is beyond every bpa's exponent range (those rows are recorded with bpa 0).
+ * Enqueued on stream (three launches); k in 1..125. */
+mg_status mg_bpa_encode(int64_t n, int32_t k, const double* x, double eps_mf, uint64_t* rec, uint8_t* bytes,
+                        uint64_t* total_bytes, int32_t* status, void* stream);
+
+/* Decode rows written by mg_bpa_encode (device buffers): out[i*k + j] = f_bpa of entry j
+ * of row i, in FP64 (fp32 = 0, exact) or FP32 (fp32 = 1: |m| rounded once to FP32 and
+ * scaled by 2^e, as the FP32 cycle kernels decode). */
+mg_status mg_bpa_decode(int64_t n, int32_t k, const uint64_t* rec, const uint8_t* bytes, int32_t fp32, void* out,
+                        void* stream);
+
+/* A MG_PREC_MIXED_BPA hierarchy's codec on a coarse level: copies (device, nullable) of
+ * the per-slot records and byte streams of A_hat (3^d entries per vertex, plane order)
+ * and P_hat (5^d); a_bytes / p_bytes (host, nullable) receive the streams' lengths.
+ * Buffers hold n_slots records and n_slots * 3^d * 8 (5^d * 8) bytes.  Synchronises. */
+mg_status mg_get_bpa(mg_hier* h, int level, uint64_t* a_rec, uint8_t* a_stream, uint64_t* p_rec, uint8_t* p_stream,
+                     uint64_t* a_bytes, uint64_t* p_bytes, void* stream);
 
 void mg_destroy_hier(mg_hier* h);
 

@@ -13,11 +13,12 @@ import numpy as np
 from . import _lib
 from ._lib import MgError, Options, SolveStats, check, load
 
-__all__ = ["Batch", "Server", "Grid", "Hierarchy", "MgError", "default_options", "encode_deltas", "load"]
+__all__ = ["Batch", "Server", "Grid", "Hierarchy", "MgError", "bpa_decode", "bpa_encode", "default_options",
+           "encode_deltas", "load"]
 
 TRANSFER = {"dlinear": 0, "boxmg": 1}
 COARSE = {"redisc": 0, "galerkin": 1}
-PRECISION = {"fp64": 0, "mixed_bf16": 1, "mixed_fp16": 2}
+PRECISION = {"fp64": 0, "mixed_bf16": 1, "mixed_fp16": 2, "mixed_bpa": 3}
 
 
 def _stream_ptr(stream) -> C.c_void_p:
@@ -235,6 +236,16 @@ class Hierarchy:
                                   _stream_ptr(stream)), "mg_get_codes")
 
 
+    def get_bpa(self, level, a_rec=None, a_stream=None, p_rec=None, p_stream=None, stream=None):
+        """Copies of a bpa hierarchy's records / byte streams of a coarse level; returns the
+        streams' lengths (a_bytes, p_bytes).  Synchronises."""
+        f = lambda t: _dptr(t) if t is not None else None
+        ab, pb = C.c_uint64(), C.c_uint64()
+        check(load().mg_get_bpa(self._h, level, f(a_rec), f(a_stream), f(p_rec), f(p_stream), C.byref(ab),
+                                C.byref(pb), _stream_ptr(stream)), "mg_get_bpa")
+        return ab.value, pb.value
+
+
 class Batch:
     """Many set-up hierarchies solved together (mg_batch_create / mg_batch_solve)."""
 
@@ -314,3 +325,20 @@ def encode_deltas(delta, codes, scale, fmt: int, stream=None):
     n, k = delta.shape
     check(load().mg_encode_deltas(n, k, _dptr(delta), fmt, _dptr(codes), _dptr(scale), _stream_ptr(stream)),
           "mg_encode_deltas")
+
+
+def bpa_encode(x, eps_mf: float, rec, stream_bytes, total, status=None, stream=None):
+    """Rows of x (n, k) FP64 -> records rec (n,) int64 view of uint64, bytes (n*k*8,) uint8,
+    total (1,) int64: the stream length; status (1,) int32, nullable."""
+    n, k = x.shape
+    check(load().mg_bpa_encode(n, k, _dptr(x), float(eps_mf), _dptr(rec), _dptr(stream_bytes), _dptr(total),
+                               _dptr(status) if status is not None else None, _stream_ptr(stream)),
+          "mg_bpa_encode")
+
+
+def bpa_decode(rec, stream_bytes, out, stream=None):
+    """Decode into out (n, k): FP64 (exact) or FP32 (as the FP32 cycle kernels decode)."""
+    n, k = out.shape
+    fp32 = 1 if out.element_size() == 4 else 0
+    check(load().mg_bpa_decode(n, k, _dptr(rec), _dptr(stream_bytes), fp32, _dptr(out), _stream_ptr(stream)),
+          "mg_bpa_decode")

@@ -37,7 +37,7 @@ class Options(C.Structure):
     _fields_ = [("transfer", C.c_int32), ("coarse", C.c_int32), ("precision", C.c_int32),
                 ("nu1", C.c_int32), ("nu2", C.c_int32), ("omega", C.c_double),
                 ("coarsest_level", C.c_int32), ("inner_cycles", C.c_int32), ("use_graphs", C.c_int32),
-                ("persistent", C.c_int32)]
+                ("persistent", C.c_int32), ("eps_mf", C.c_double)]
 
 
 class SolveStats(C.Structure):
@@ -82,6 +82,9 @@ _SIGS = {
     "mg_get_deltas": (C.c_int, [_P, C.c_int, _P, _P, _P]),
     "mg_get_codes": (C.c_int, [_P, C.c_int, _P, _P, _P, _P, _P]),
     "mg_encode_deltas": (C.c_int, [C.c_int64, C.c_int, _P, C.c_int, _P, _P, _P]),
+    "mg_bpa_encode": (C.c_int, [C.c_int64, C.c_int32, _P, C.c_double, _P, _P, _P, _P, _P]),
+    "mg_bpa_decode": (C.c_int, [C.c_int64, C.c_int32, _P, _P, C.c_int32, _P, _P]),
+    "mg_get_bpa": (C.c_int, [_P, C.c_int, _P, _P, _P, _P, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64), _P]),
     "mg_batch_create": (C.c_int, [C.c_int, C.POINTER(_P), C.POINTER(_P)]),
     "mg_batch_solve": (C.c_int, [_P, C.POINTER(_P), C.POINTER(_P), C.c_double, C.c_int, C.POINTER(SolveStats), _P]),
     "mg_batch_setup": (C.c_int, [_P, C.POINTER(_P), _P]),

@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <type_traits>
 
 #include "../../include/mg.h"
 
@@ -107,7 +108,8 @@ __device__ __forceinline__ int64_t plane_index(const LevelDesc& L, int64_t slot,
 }
 
 // ---- delta storage ---------------------------------------------------------
-// DMODE 0: none, 1: FP64 values, 2: BF16 codes x FP32 scale, 3: FP16 codes x FP32 scale
+// DMODE 0: none, 1: FP64 values, 2: BF16 codes x FP32 scale, 3: FP16 codes x FP32 scale,
+// 4: the bpa byte codec
 __device__ __forceinline__ float bf16_bits_to_float(uint16_t q) {
   return __uint_as_float(static_cast<uint32_t>(q) << 16);
 }
@@ -117,14 +119,45 @@ __device__ __forceinline__ float fp16_bits_to_float(uint16_t q) {
   return __half2float(__half(hr));
 }
 
+// bpa codec (Sect. 5): an operator of a vertex is either dropped (bpa = 0) or stored
+// entry by entry as bpa bytes: a signed exponent byte e, then bpa - 1 bytes of m
+// little-endian, whose top bit is the sign and whose other M = 8 (bpa - 1) - 1 bits
+// hold |m|; the value is (-1)^sign |m| 2^e.  rec = (byte offset << 4) | bpa locates the
+// operator in its byte stream; entry k sits k * bpa bytes further.  The FP32 value is
+// |m| rounded once to FP32 then scaled by 2^e (exact scaling), i.e. the FP32 rounding of
+// the stored value wherever that is a normal number.
+template <typename T>
+__device__ __forceinline__ T bpa_decode(const uint8_t* bytes, uint64_t rec, int k) {
+  const int bpa = static_cast<int>(rec & 15u);
+  if (bpa == 0) return T(0);
+  const uint8_t* p = bytes + (rec >> 4) + static_cast<int64_t>(k) * bpa;
+  const int e = static_cast<int>(static_cast<int8_t>(p[0]));
+  uint64_t w = 0;
+#pragma unroll
+  for (int i = 1; i < 8; ++i)
+    if (i < bpa) w |= static_cast<uint64_t>(p[i]) << (8 * (i - 1));
+  const int M = 8 * (bpa - 1) - 1;
+  const uint64_t m = w & ((1ull << M) - 1ull);
+  T v;
+  if constexpr (std::is_same<T, double>::value) v = ldexp(__ull2double_rn(m), e);
+  else v = ldexpf(__ull2float_rn(m), e);
+  return ((w >> M) & 1u) ? -v : v;
+}
+
+// delta entry k of the vertex in slot `slot`; idx = its position in the 16-bit or FP64
+// planes.  aux: per-vertex FP32 scales (DMODE 2, 3) or bpa records (DMODE 4).
 template <int DMODE, typename T>
-__device__ __forceinline__ T load_delta(const void* p, const float* scale, int64_t idx, int64_t slot) {
+__device__ __forceinline__ T load_delta(const void* p, const void* aux, int64_t idx, int64_t slot, int k = 0) {
   if constexpr (DMODE == 1) {
     return static_cast<T>(static_cast<const double*>(p)[idx]);
   } else if constexpr (DMODE == 2) {
-    return static_cast<T>(bf16_bits_to_float(static_cast<const uint16_t*>(p)[idx]) * scale[slot]);
+    return static_cast<T>(bf16_bits_to_float(static_cast<const uint16_t*>(p)[idx]) *
+                          static_cast<const float*>(aux)[slot]);
   } else if constexpr (DMODE == 3) {
-    return static_cast<T>(fp16_bits_to_float(static_cast<const uint16_t*>(p)[idx]) * scale[slot]);
+    return static_cast<T>(fp16_bits_to_float(static_cast<const uint16_t*>(p)[idx]) *
+                          static_cast<const float*>(aux)[slot]);
+  } else if constexpr (DMODE == 4) {
+    return bpa_decode<T>(static_cast<const uint8_t*>(p), static_cast<const uint64_t*>(aux)[slot], k);
   } else {
     return T(0);
   }

@@ -29,6 +29,10 @@ struct DevLevel {
   double* phat = nullptr;
   uint16_t* p16 = nullptr;
   float* pscale = nullptr;
+  uint64_t* abpa_rec = nullptr;  // bpa codec: per-slot records and byte streams of A_hat, P_hat
+  uint8_t* abpa = nullptr;
+  uint64_t* pbpa_rec = nullptr;
+  uint8_t* pbpa = nullptr;
   double *u = nullptr, *b = nullptr, *r = nullptr, *t = nullptr;
   float *u32 = nullptr, *b32 = nullptr, *r32 = nullptr, *t32 = nullptr;
   double* dinv = nullptr;  // FP64 hierarchies: omega / diag(A) for the Jacobi sweeps
@@ -63,7 +67,8 @@ struct Hier {
   int32_t *ref_top = nullptr, *dof_L = nullptr, *hang_L = nullptr;
   int64_t n_ref_top = 0, n_dof_L = 0, n_hang_L = 0;
   bool galerkin = false, boxmg = false, mixed = false;
-  int fmt = 1;  // 1 bf16, 2 fp16
+  int fmt = 1;  // 1 bf16, 2 fp16, 4 bpa codec
+  uint64_t* bpa_used = nullptr;  // bpa codec: stream lengths per level, [2 l] A_hat, [2 l + 1] P_hat
   std::vector<DevLevel> lv;
   std::vector<void*> allocs;
   int n_c = 0;

@@ -19,7 +19,7 @@ struct SweepArgs {
   T* out;
   const T* eps;         // cell coefficients (cell slots)
   const void* ahat;     // A_hat planes (3^d per vertex) or nullptr
-  const float* ascale;  // per-vertex scale of 16-bit codes
+  const void* ascale;   // per-vertex aux of A_hat: FP32 scales (16-bit codes) or bpa records
   T omega;
   double* partial;      // per-CTA partial sums of r^2 (residual op), nullable
   unsigned* counter;    // completion counter for the fused final sum, nullable
@@ -291,7 +291,7 @@ __device__ __forceinline__ double sweep_item(const SweepArgs<T>& a, int64_t bric
             kk /= 3;
             m *= Bu;
           }
-          const T d = load_delta<AMODE, T>(a.ahat, a.ascale, (brick * N3 + k) * L.S + s, slot);
+          const T d = load_delta<AMODE, T>(a.ahat, a.ascale, (brick * N3 + k) * L.S + s, slot, k);
           if (k == N3 / 2)
             D += d;
           else
@@ -385,7 +385,7 @@ __device__ __forceinline__ bool coords_of_b(const LevelDesc& L, int64_t slot, in
 // unrolled so the d-linear weights are compile-time constants.
 template <int DIM, typename T, int PMODE, int BC, int BF>
 __device__ __forceinline__ void restrict_one(const LevelDesc& Lc, const LevelDesc& Lf, const T* rf, T* bc,
-                                             const void* phat, const float* pscale, int64_t cs) {
+                                             const void* phat, const void* pscale, int64_t cs) {
   constexpr int N5 = cpow(5, DIM);
   int X[DIM];
   if (!coords_of_b<DIM, BC>(Lc, cs, X) || !is_dof(Lc.vflags[cs])) {
@@ -409,7 +409,7 @@ __device__ __forceinline__ void restrict_one(const LevelDesc& Lc, const LevelDes
     const int64_t fs = slot_of_b<DIM, BF>(Lf, y);
     if (fs < 0) continue;
     T p = static_cast<T>(w);
-    if constexpr (PMODE != 0) p += load_delta<PMODE, T>(phat, pscale, (cb * N5 + k) * Lc.S + cl, cs);
+    if constexpr (PMODE != 0) p += load_delta<PMODE, T>(phat, pscale, (cb * N5 + k) * Lc.S + cl, cs, k);
     acc = fma(p, rf[fs], acc);
   }
   bc[cs] = acc;
@@ -438,7 +438,7 @@ constexpr int kRestrictWarps = 8;
 
 template <int DIM, typename T, int PMODE, int BC, int BF>
 __global__ void __launch_bounds__(32 * kRestrictWarps)
-    k_restrict(LevelDesc Lc, LevelDesc Lf, const T* rf, T* bc, const void* phat, const float* pscale,
+    k_restrict(LevelDesc Lc, LevelDesc Lf, const T* rf, T* bc, const void* phat, const void* pscale,
                const int32_t* list, int64_t n_list, T* zero_c) {
   constexpr int N5 = cpow(5, DIM);
   __shared__ T part[kRestrictWarps][32];
@@ -465,7 +465,7 @@ __global__ void __launch_bounds__(32 * kRestrictWarps)
       const int64_t fs = slot_of_b<DIM, BF>(Lf, y);
       if (fs < 0) continue;
       T p = wtab[k];
-      if constexpr (PMODE != 0) p += load_delta<PMODE, T>(phat, pscale, (cb * N5 + k) * Lc.S + cl, cs);
+      if constexpr (PMODE != 0) p += load_delta<PMODE, T>(phat, pscale, (cb * N5 + k) * Lc.S + cl, cs, k);
       acc = fma(p, rf[fs], acc);
     }
   }
@@ -484,7 +484,7 @@ __global__ void __launch_bounds__(32 * kRestrictWarps)
 // correction of Alg. 1).  One thread per fine slot; non-DoF slots untouched.
 template <int DIM, typename T, int PMODE, int BC, int BF>
 __device__ __forceinline__ void prolong_one(const LevelDesc& Lc, const LevelDesc& Lf, const T* ec, T* uf,
-                                            const void* phat, const float* pscale, int64_t fs,
+                                            const void* phat, const void* pscale, int64_t fs,
                                             const T* wtab = nullptr) {
   constexpr int N5 = cpow(5, DIM);
   int x[DIM];
@@ -516,7 +516,7 @@ __device__ __forceinline__ void prolong_one(const LevelDesc& Lc, const LevelDesc
     T p = wtab ? wtab[k] : dlin_weight<DIM, T>(k);
     if constexpr (PMODE != 0) {
       const int64_t cb = cs / Lc.S;
-      p += load_delta<PMODE, T>(phat, pscale, (cb * N5 + k) * Lc.S + (cs - cb * Lc.S), cs);
+      p += load_delta<PMODE, T>(phat, pscale, (cb * N5 + k) * Lc.S + (cs - cb * Lc.S), cs, k);
     }
     acc = fma(p, ec[cs], acc);
   }
@@ -526,7 +526,7 @@ __device__ __forceinline__ void prolong_one(const LevelDesc& Lc, const LevelDesc
 // (list: fine DoF slots to serve, thread i -> list[i]; nullptr: every fine slot)
 template <int DIM, typename T, int PMODE, int BC, int BF>
 __global__ void __launch_bounds__(kBlock) k_prolong(LevelDesc Lc, LevelDesc Lf, const T* ec, T* uf,
-                                                      const void* phat, const float* pscale,
+                                                      const void* phat, const void* pscale,
                                                       const int32_t* list, int64_t n_list) {
   constexpr int N5 = cpow(5, DIM);
   __shared__ T wtab[N5];  // d-linear weights by offset, formed once per CTA
@@ -583,7 +583,7 @@ void launch_sweep(SweepArgs<T> a, int op, int amode, cudaStream_t s);
 // nullptr serves every slot of the target level
 template <int DIM, typename T>
 void launch_transfer(const LevelDesc& Lc, const LevelDesc& Lf, bool restrict_op, int pmode, const T* in, T* out,
-                     const void* phat, const float* pscale, cudaStream_t s, const int32_t* list = nullptr,
+                     const void* phat, const void* pscale, cudaStream_t s, const int32_t* list = nullptr,
                      int64_t n_list = 0, T* zero_c = nullptr);
 
 }  // namespace mg

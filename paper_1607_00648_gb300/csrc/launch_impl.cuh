@@ -32,9 +32,11 @@ static void sweep_b(SweepArgs<T> a, int op, int amode, cudaStream_t s) {
     else MG_SWR(AM, OP, 27);                                             \
   } while (0)
     if (op == kJacobi) {
-      if (amode == 2) MG_SW(2, kJacobi); else if (amode == 3) MG_SW(3, kJacobi); else MG_SW(0, kJacobi);
+      if (amode == 2) MG_SW(2, kJacobi); else if (amode == 3) MG_SW(3, kJacobi);
+      else if (amode == 4) MG_SW(4, kJacobi); else MG_SW(0, kJacobi);
     } else {
-      if (amode == 2) MG_SW(2, kResidual); else if (amode == 3) MG_SW(3, kResidual); else MG_SW(0, kResidual);
+      if (amode == 2) MG_SW(2, kResidual); else if (amode == 3) MG_SW(3, kResidual);
+      else if (amode == 4) MG_SW(4, kResidual); else MG_SW(0, kResidual);
     }
 #undef MG_SW
 #undef MG_SWR
@@ -51,9 +53,11 @@ static void sweep_b(SweepArgs<T> a, int op, int amode, cudaStream_t s) {
       }
     } else {
       if (op == kJacobi) {
-        if (amode == 2) MG_SW(2, kJacobi); else if (amode == 3) MG_SW(3, kJacobi); else MG_SW(0, kJacobi);
+        if (amode == 2) MG_SW(2, kJacobi); else if (amode == 3) MG_SW(3, kJacobi);
+        else if (amode == 4) MG_SW(4, kJacobi); else MG_SW(0, kJacobi);
       } else {
-        if (amode == 2) MG_SW(2, kResidual); else if (amode == 3) MG_SW(3, kResidual); else MG_SW(0, kResidual);
+        if (amode == 2) MG_SW(2, kResidual); else if (amode == 3) MG_SW(3, kResidual);
+        else if (amode == 4) MG_SW(4, kResidual); else MG_SW(0, kResidual);
       }
     }
 #undef MG_SW
@@ -62,7 +66,7 @@ static void sweep_b(SweepArgs<T> a, int op, int amode, cudaStream_t s) {
 
 template <int DIM, typename T, int BC, int BF>
 static void transfer_b(const LevelDesc& Lc, const LevelDesc& Lf, bool restrict_op, int pmode, const T* in, T* out,
-                       const void* ph, const float* ps, cudaStream_t s, const int32_t* li, int64_t nl,
+                       const void* ph, const void* ps, cudaStream_t s, const int32_t* li, int64_t nl,
                        T* zc) {
   const int64_t nc = li ? nl : Lc.n_slots, nf = li ? nl : Lf.n_slots;
   const unsigned gc = static_cast<unsigned>((nc + 31) / 32);
@@ -78,7 +82,7 @@ static void transfer_b(const LevelDesc& Lc, const LevelDesc& Lf, bool restrict_o
   if constexpr (std::is_same<T, double>::value) {
     if (pmode == 1) MG_TR(1); else MG_TR(0);
   } else {
-    if (pmode == 2) MG_TR(2); else if (pmode == 3) MG_TR(3); else MG_TR(0);
+    if (pmode == 2) MG_TR(2); else if (pmode == 3) MG_TR(3); else if (pmode == 4) MG_TR(4); else MG_TR(0);
   }
 #undef MG_TR
 }
@@ -97,7 +101,7 @@ static void transfer_b(const LevelDesc& Lc, const LevelDesc& Lf, bool restrict_o
   }                                                                                                         \
   template <>                                                                                               \
   void launch_transfer<DIM, T>(const LevelDesc& Lc, const LevelDesc& Lf, bool r, int pmode, const T* in,     \
-                               T* out, const void* ph, const float* ps, cudaStream_t s, const int32_t* li,  \
+                               T* out, const void* ph, const void* ps, cudaStream_t s, const int32_t* li,  \
                                int64_t nl, T* zc) {                                                         \
     if (Lc.B == 3 && Lf.B == 9) transfer_b<DIM, T, 3, 9>(Lc, Lf, r, pmode, in, out, ph, ps, s, li, nl, zc);  \
     else if (Lc.B == 9 && Lf.B == 9) transfer_b<DIM, T, 9, 9>(Lc, Lf, r, pmode, in, out, ph, ps, s, li, nl, zc); \

@@ -369,6 +369,10 @@ mg_status mg_server_create(size_t hbm_budget_bytes, const mg_options* opt, mg_se
     set_error("mg_server_create: invalid argument");
     return MG_ERR_INVALID_ARG;
   }
+  if (opt && opt->precision == MG_PREC_MIXED_BPA) {
+    set_error("mg_server_create: the server runs batches, which take no bpa-coded hierarchies");
+    return MG_ERR_UNSUPPORTED;
+  }
   *out = nullptr;
   Server* sv = new (std::nothrow) Server();
   if (!sv) {

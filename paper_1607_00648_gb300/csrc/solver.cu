@@ -12,6 +12,7 @@
 #include <string>
 #include <vector>
 
+#include "bpa.cuh"
 #include "hier.h"
 #include "internal.h"
 #include "kernels.cuh"
@@ -439,7 +440,7 @@ static mg_status create(const Grid* g, const mg_options& o, Hier** out, int prio
   H->galerkin = o.coarse == MG_COARSE_GALERKIN;
   H->boxmg = o.transfer == MG_TRANSFER_BOXMG;
   H->mixed = o.precision != MG_PREC_FP64;
-  H->fmt = o.precision == MG_PREC_MIXED_FP16 ? 2 : 1;
+  H->fmt = o.precision == MG_PREC_MIXED_FP16 ? 2 : (o.precision == MG_PREC_MIXED_BPA ? 4 : 1);
   auto fail = [&](mg_status s) {
     free_hier(H, true);
     return s;
@@ -493,7 +494,16 @@ static mg_status create(const Grid* g, const mg_options& o, Hier** out, int prio
       if ((st = dalloc(*H, &D.b32, ns)) != MG_OK) return fail(st);
       if ((st = dalloc(*H, &D.r32, ns)) != MG_OK) return fail(st);
       if ((st = dalloc(*H, &D.t32, ns)) != MG_OK) return fail(st);
-      if (l < H->top) {
+      if (l < H->top && H->fmt == 4) {  // bpa streams at their worst case (8 bytes per entry)
+        if (H->galerkin) {
+          if ((st = dalloc(*H, &D.abpa_rec, ns)) != MG_OK) return fail(st);
+          if ((st = dalloc(*H, &D.abpa, ns * n3 * 8)) != MG_OK) return fail(st);
+        }
+        if (H->boxmg) {
+          if ((st = dalloc(*H, &D.pbpa_rec, ns)) != MG_OK) return fail(st);
+          if ((st = dalloc(*H, &D.pbpa, ns * n5 * 8)) != MG_OK) return fail(st);
+        }
+      } else if (l < H->top) {
         if (H->galerkin) {
           if ((st = dalloc(*H, &D.a16, ns * n3)) != MG_OK) return fail(st);
           if ((st = dalloc(*H, &D.ascale, ns)) != MG_OK) return fail(st);
@@ -563,6 +573,7 @@ static mg_status create(const Grid* g, const mg_options& o, Hier** out, int prio
   if ((st = upload(*H, &H->c_map, map)) != MG_OK) return fail(st);
   if ((st = dalloc(*H, &H->c_mat, static_cast<size_t>(H->n_c) * H->n_c)) != MG_OK) return fail(st);
   if ((st = dalloc(*H, &H->d_status, 1)) != MG_OK) return fail(st);
+  if (H->fmt == 4 && (st = dalloc(*H, &H->bpa_used, 2 * (H->L + 1))) != MG_OK) return fail(st);
   if ((st = dalloc(*H, &H->d_scal, 16)) != MG_OK) return fail(st);
   if ((st = dalloc(*H, &H->d_hist, kHistCap)) != MG_OK) return fail(st);
   if ((st = dalloc(*H, &H->d_pint, 4)) != MG_OK) return fail(st);
@@ -592,7 +603,8 @@ static mg_status create(const Grid* g, const mg_options& o, Hier** out, int prio
 mg_status hier_create(const Grid* g, const mg_options& o, int priority, Hier** out, bool blocking) {
   *out = nullptr;
   if (o.coarsest_level < 1 || o.coarsest_level >= g->L || o.nu1 < 0 || o.nu2 < 0 || !(o.omega > 0.0) ||
-      o.transfer < 0 || o.transfer > 1 || o.coarse < 0 || o.coarse > 1 || o.precision < 0 || o.precision > 2) {
+      o.transfer < 0 || o.transfer > 1 || o.coarse < 0 || o.coarse > 1 || o.precision < 0 || o.precision > 3 ||
+      (o.precision == MG_PREC_MIXED_BPA && !(o.eps_mf >= 0.0 && o.eps_mf < 1e300))) {
     set_error("mg_hier_create: invalid options");
     return MG_ERR_INVALID_ARG;
   }
@@ -635,7 +647,8 @@ size_t hier_footprint(const Grid& g, const mg_options& o) {
     if (l < top) bytes += (galerkin ? ns * n3 * 8 : 0) + (boxmg ? ns * n5 * 8 : 0);
     if (mixed) {
       bytes += 5 * ns * 4;
-      if (l < top) bytes += (galerkin ? ns * n3 * 2 + ns * 4 : 0) + (boxmg ? ns * n5 * 2 + ns * 4 : 0);
+      const size_t per = o.precision == MG_PREC_MIXED_BPA ? 8 : 2, sc = o.precision == MG_PREC_MIXED_BPA ? 8 : 4;
+      if (l < top) bytes += (galerkin ? ns * n3 * per + ns * sc : 0) + (boxmg ? ns * n5 * per + ns * sc : 0);
     }
     if (l == top && top < g.L) bytes += ns * 4 + (mixed ? 2 * ns * 4 : 0);  // injection map, FP32 composite vectors
   }
@@ -669,7 +682,11 @@ static SweepArgs<T> sweep_args(const Hier& H, int l, const T* u, const T* b, T* 
     }
   } else {
     a.eps = D.eps32;
-    if (coarse) {
+    if (coarse && H.fmt == 4) {
+      *amode = 4;
+      a.ahat = D.abpa;
+      a.ascale = D.abpa_rec;
+    } else if (coarse) {
       *amode = H.fmt == 1 ? 2 : 3;
       a.ahat = D.a16;
       a.ascale = D.ascale;
@@ -705,11 +722,15 @@ static void transfer(const Hier& H, int fine, bool restrict_op, const T* in, T* 
   const DevLevel& C = H.lv[fine - 1];
   int pmode = 0;
   const void* ph = nullptr;
-  const float* ps = nullptr;
+  const void* ps = nullptr;
   if (H.boxmg && fine <= H.top) {
     if constexpr (std::is_same<T, double>::value) {
       pmode = 1;
       ph = C.phat;
+    } else if (H.fmt == 4) {
+      pmode = 4;
+      ph = C.pbpa;
+      ps = C.pbpa_rec;
     } else {
       pmode = H.fmt == 1 ? 2 : 3;
       ph = C.p16;
@@ -865,7 +886,15 @@ static mg_status run_setup(Hier& H, const double* eps_in, cudaStream_t s, bool c
     for (int l = H.c; l <= H.L; ++l) {
       DevLevel& D = H.lv[l];
       k_to_f32<<<nblk(D.d.n_slots), kBlock, 0, s>>>(D.d.n_slots, D.eps, D.eps32);
-      if (l < H.top) {
+      if (l < H.top && H.fmt == 4) {
+        const int64_t ns = D.d.n_slots;
+        if (H.galerkin)
+          bpa_encode_enqueue(BpaSrc{D.ahat, n3, true, D.d}, ns, H.opt.eps_mf, D.abpa_rec, D.abpa,
+                             H.bpa_used + 2 * l, H.d_status, 4, 5, s);
+        if (H.boxmg)
+          bpa_encode_enqueue(BpaSrc{D.phat, n5, true, D.d}, ns, H.opt.eps_mf, D.pbpa_rec, D.pbpa,
+                             H.bpa_used + 2 * l + 1, H.d_status, 4, 5, s);
+      } else if (l < H.top) {
         if (H.galerkin) {
           if (H.fmt == 1)
             k_encode_planes<1><<<nblk(D.d.n_slots), kBlock, 0, s>>>(D.d, n3, D.ahat, D.a16, D.ascale);
@@ -904,6 +933,11 @@ mg_status setup_status(Hier& H, int status) {
   if (status == 3) {
     set_error("mg_setup: the coarsest operator is not positive definite");
     return MG_ERR_INDEFINITE_COARSE;
+  }
+  if (status == 4 || status == 5) {
+    set_error(status == 4 ? "mg_setup: a hierarchical delta is not finite"
+                          : "mg_setup: a hierarchical delta is beyond the bpa codec's exponent range");
+    return MG_ERR_NONFINITE;
   }
   H.ready = true;
   return MG_OK;
@@ -1514,6 +1548,7 @@ void mg_default_options(mg_options* o) {
   o->inner_cycles = 8;
   o->use_graphs = 1;
   o->persistent = 0;
+  o->eps_mf = 1e-4;
 }
 
 mg_status mg_hier_create(const mg_grid* grid, const mg_options* opt, mg_hier** out) {
@@ -1738,7 +1773,7 @@ mg_status mg_solve(mg_hier* h, double* u, const double* b, double rel_tol, int m
   }
   cudaStream_t s = pick(*H, stream);
   const auto t0 = std::chrono::steady_clock::now();
-  const bool persistent = H->opt.persistent && !H->adaptive && H->n_c <= 64 && H->L < kMaxLevels;
+  const bool persistent = H->opt.persistent && !H->adaptive && H->fmt != 4 && H->n_c <= 64 && H->L < kMaxLevels;
   const mg_status st = H->adaptive ? (H->mixed ? solve_comp_mixed(*H, u, b, rel_tol, max_cycles, stats, s)
                                                  : solve_comp_fp64(*H, u, b, rel_tol, max_cycles, stats, s))
                        : persistent ? solve_persistent(*H, u, b, rel_tol, max_cycles, stats, s)
@@ -1837,6 +1872,58 @@ mg_status mg_encode_deltas(int64_t n, int k, const double* delta, int fmt, uint1
   else
     k_encode_rows<2><<<nblk(n), kBlock, 0, s>>>(n, k, delta, codes, scale);
   return last_launch("mg_encode_deltas");
+}
+
+mg_status mg_bpa_encode(int64_t n, int32_t k, const double* x, double eps_mf, uint64_t* rec, uint8_t* bytes,
+                        uint64_t* total_bytes, int32_t* status, void* stream) {
+  if (n < 0 || k <= 0 || k > 125 || !(eps_mf >= 0.0) || !total_bytes || (n > 0 && (!x || !rec || !bytes))) {
+    set_error("mg_bpa_encode: invalid argument");
+    return MG_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (status) MG_TRY_CUDA(cudaMemsetAsync(status, 0, sizeof(int32_t), s));
+  BpaSrc src{x, k, false, LevelDesc{}};
+  bpa_encode_enqueue(src, n, eps_mf, rec, bytes, total_bytes, status, 1, 2, s);
+  return last_launch("mg_bpa_encode");
+}
+
+mg_status mg_bpa_decode(int64_t n, int32_t k, const uint64_t* rec, const uint8_t* bytes, int32_t fp32, void* out,
+                        void* stream) {
+  if (n < 0 || k <= 0 || (n > 0 && (!rec || !bytes || !out))) {
+    set_error("mg_bpa_decode: invalid argument");
+    return MG_ERR_INVALID_ARG;
+  }
+  if (n == 0) return MG_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (fp32)
+    k_bpa_decode<float><<<nblk(n), kBlock, 0, s>>>(n, k, rec, bytes, static_cast<float*>(out));
+  else
+    k_bpa_decode<double><<<nblk(n), kBlock, 0, s>>>(n, k, rec, bytes, static_cast<double*>(out));
+  return last_launch("mg_bpa_decode");
+}
+
+mg_status mg_get_bpa(mg_hier* h, int level, uint64_t* a_rec, uint8_t* a_stream, uint64_t* p_rec, uint8_t* p_stream,
+                     uint64_t* a_bytes, uint64_t* p_bytes, void* stream) {
+  Hier* H = H_(h);
+  MG_CHECK(check_level(H, level, true));
+  if (H->fmt != 4 || level >= H->top) {
+    set_error("mg_get_bpa: no bpa streams (not a MG_PREC_MIXED_BPA hierarchy, or the finest level)");
+    return MG_ERR_INVALID_ARG;
+  }
+  DevLevel& D = H->lv[level];
+  cudaStream_t s = pick(*H, stream);
+  const size_t ns = static_cast<size_t>(D.d.n_slots);
+  const size_t n3 = ipow(3, H->dim), n5 = ipow(5, H->dim);
+  uint64_t used[2] = {0, 0};
+  MG_TRY_CUDA(cudaMemcpyAsync(used, H->bpa_used + 2 * level, sizeof(used), cudaMemcpyDeviceToHost, s));
+  if (a_rec && D.abpa_rec) MG_TRY_CUDA(cudaMemcpyAsync(a_rec, D.abpa_rec, ns * 8, cudaMemcpyDeviceToDevice, s));
+  if (a_stream && D.abpa) MG_TRY_CUDA(cudaMemcpyAsync(a_stream, D.abpa, ns * n3 * 8, cudaMemcpyDeviceToDevice, s));
+  if (p_rec && D.pbpa_rec) MG_TRY_CUDA(cudaMemcpyAsync(p_rec, D.pbpa_rec, ns * 8, cudaMemcpyDeviceToDevice, s));
+  if (p_stream && D.pbpa) MG_TRY_CUDA(cudaMemcpyAsync(p_stream, D.pbpa, ns * n5 * 8, cudaMemcpyDeviceToDevice, s));
+  MG_TRY_CUDA(cudaStreamSynchronize(s));
+  if (a_bytes) *a_bytes = D.abpa ? used[0] : 0;
+  if (p_bytes) *p_bytes = D.pbpa ? used[1] : 0;
+  return last_launch("mg_get_bpa");
 }
 
 void mg_destroy_hier(mg_hier* h) { free_hier(H_(h), true); }

@@ -109,7 +109,7 @@ __device__ __forceinline__ double sweep2c_item(const SweepArgs<T>& a, int64_t br
           const int sl = (z0 + zl) * B + x;
 #pragma unroll
           for (int q = 0; q < 9; ++q) {
-            const T d = load_delta<AMODE, T>(a.ahat, a.ascale, (brick * 9 + q) * L.S + sl, slot);
+            const T d = load_delta<AMODE, T>(a.ahat, a.ascale, (brick * 9 + q) * L.S + sl, slot, q);
             Au = fma(d, nbv[q], Au);
             if (q == 4) D += d;
           }
@@ -243,7 +243,7 @@ __device__ __forceinline__ double sweep3c_item(const SweepArgs<T>& a, int64_t br
 #pragma unroll
           for (int k = 0; k < N3; ++k) {
             const int off = (k % 3 - 1) + Bu * ((k / 3) % 3 - 1) + UPL * (k / 9 - 1);
-            const T d = load_delta<AMODE, T>(a.ahat, a.ascale, (brick * N3 + k) * L.S + s, slot);
+            const T d = load_delta<AMODE, T>(a.ahat, a.ascale, (brick * N3 + k) * L.S + s, slot, k);
             Au = fma(d, uc[off], Au);
             if (k == N3 / 2) D += d;
           }

@@ -40,7 +40,7 @@ class Case:
     """One problem on the CPU oracle and on the GPU library, same slot numbering."""
 
     def __init__(self, dim, L, eps_kind="checker", transfer="boxmg", coarse="galerkin", precision="fp64",
-                 seed=0, omega=0.6, nu1=2, nu2=2, load="uniform", oracle=True, persistent=0):
+                 seed=0, omega=0.6, nu1=2, nu2=2, load="uniform", oracle=True, persistent=0, eps_mf=None):
         import torch
 
         self.mg = lib()
@@ -48,8 +48,9 @@ class Case:
         self.dim, self.L = dim, L
         self.eps = eps_field(eps_kind, L, dim, seed)
         self.grid = self.mg.Grid(dim, L)
+        extra = {} if eps_mf is None else {"eps_mf": eps_mf}
         self.H = self.mg.Hierarchy(self.grid, transfer=transfer, coarse=coarse, precision=precision,
-                                   omega=omega, nu1=nu1, nu2=nu2, persistent=persistent)
+                                   omega=omega, nu1=nu1, nu2=nu2, persistent=persistent, **extra)
         eps_cat = self.grid.cells_to_concat({L: self.eps})
         self.eps_dev = torch.from_numpy(eps_cat).cuda()
         self.H.setup(self.eps_dev)

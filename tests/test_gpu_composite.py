@@ -133,7 +133,7 @@ def test_composite_solve_matches_oracle(comp):
     assert np.abs(g4 - d4)[comp.C.unref4].max() <= 1e-8 * ds
 
 
-@pytest.mark.parametrize("precision", ["mixed_bf16", "mixed_fp16"])
+@pytest.mark.parametrize("precision", ["mixed_bf16", "mixed_fp16", "mixed_bpa"])
 @pytest.mark.parametrize("dim,L", CASES)
 def test_composite_mixed_solve_reaches_fp64_solution(dim, L, precision):
     c = Comp(dim, L, precision=precision, eps_kind="grf", seed=5)
