@@ -47,6 +47,10 @@ WORKLOADS = {
                       coarse="galerkin", tol=1e-10, max_cycles=3000,
                       desc="2D level 6, the paper's jump benchmark (eps 1 / 0.1 across x_1 = 0.5, f = 1), "
                            "BoxMG + Galerkin, V(2,2), to 1e-10"),
+    "grf2d-l6": dict(dim=2, L=6, eps="grf", eps_seed=1000, load_seed=2000, transfer="boxmg",
+                     coarse="galerkin", tol=1e-10, max_cycles=3000,
+                     desc="2D level 6, log-normal coefficient sigma 2, lambda 0.1 (the largest problem size "
+                          "of the batched workload), BoxMG + Galerkin, V(2,2), to 1e-10"),
     "sin2d-l4": dict(dim=2, L=4, eps="const", eps_seed=0, load_seed=None, transfer="dlinear",
                      coarse="redisc", tol=1e-8, max_cycles=200,
                      desc="2D level 4 (81^2 cells, 6,400 DoFs), sin benchmark, geometric V(2,2), to 1e-8"),
@@ -83,6 +87,8 @@ def inputs(w):
         eps = syn.checkerboard_eps(L, d, seed=w["eps_seed"])
     elif w["eps"] == "jump":
         eps = syn.jump_eps(L, d)
+    elif w["eps"] == "grf":
+        eps = syn.lognormal_grf_eps(L, d, sigma=2.0, seed=w["eps_seed"])
     else:
         eps = syn.constant_eps(L, d)
     if w["load_seed"] == "unit":
@@ -343,8 +349,9 @@ def run_breakdown(args):
     bd = torch.from_numpy(b).cuda()
     u = torch.zeros_like(bd)
     out = {"workload": args.workload, "dofs": n_dofs}
-    for prec in ("fp64", "mixed_bf16"):
-        if args.precision not in ("both", prec.split("_")[0]):
+    precs = ("mixed_bf16", "mixed_bpa") if args.precision == "bpa" else ("fp64", "mixed_bf16")
+    for prec in precs:
+        if args.precision not in ("both", "bpa", prec.split("_")[0]):
             continue
         H = mg.Hierarchy(grid, precision=prec, **opts)
         H.setup(e)
@@ -875,8 +882,9 @@ def main():
     ap.add_argument("--workload", default="checker2d-l6", choices=sorted(WORKLOADS) + sorted(ADAPTIVE))
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline leg")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default slab depths (no mg_autotune)")
-    ap.add_argument("--precision", default="both", choices=("both", "fp64", "mixed"),
-                    help="which solve forms to time (profiling runs; the default times both)")
+    ap.add_argument("--precision", default="both", choices=("both", "fp64", "mixed", "bpa"),
+                    help="which solve forms to time (profiling runs; the default times both; "
+                         "bpa: --breakdown of the BF16 and bpa mixed forms)")
     ap.add_argument("--codecs", action="store_true",
                     help="mixed solves with BF16 deltas against the bpa codec at eps_mf 1e-2 / 1e-4 / 1e-8")
     ap.add_argument("--batched", action="store_true", help="task config 4: batched mixed vs FP64 solves")
@@ -891,6 +899,8 @@ def main():
     ap.add_argument("--sweep-dim", type=int, default=2, choices=(2, 3))
     ap.add_argument("--sweep-prec", default="both", choices=("both", "fp64", "fp32"))
     args = ap.parse_args()
+    if args.precision == "bpa" and not args.breakdown:
+        ap.error("--precision bpa goes with --breakdown (bench.py --codecs times the codecs)")
     if args.breakdown:
         run_breakdown(args)
     elif args.serve:

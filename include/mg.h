@@ -387,7 +387,9 @@ mg_status mg_bpa_encode(int64_t n, int32_t k, const double* x, double eps_mf, ui
 
 /* Decode rows written by mg_bpa_encode (device buffers): out[i*k + j] = f_bpa of entry j
  * of row i, in FP64 (fp32 = 0, exact) or FP32 (fp32 = 1: |m| rounded once to FP32 and
- * scaled by 2^e, as the FP32 cycle kernels decode). */
+ * scaled by 2^e, as the FP32 cycle kernels decode).  The decoder reads the stream by
+ * aligned 8-byte words: `bytes` must be 8-byte aligned and its buffer a multiple of 8
+ * bytes long (the n * k * 8 bytes mg_bpa_encode asks for are). */
 mg_status mg_bpa_decode(int64_t n, int32_t k, const uint64_t* rec, const uint8_t* bytes, int32_t fp32, void* out,
                         void* stream);
 

@@ -9,10 +9,14 @@
 
 namespace mg {
 
+__device__ __forceinline__ double pow2d(int i) {  // 2^i for i in [-1022, 1023], exact
+  return __longlong_as_double(static_cast<long long>(i + 1023) << 52);
+}
+
 // (e, |m|) of one entry at bpa >= 2 and its error | |m| 2^e - |x| | (the FP64 expression
 // of the tolerance test); false if the exponent does not fit a signed byte.  The
 // exponent is the smallest whose |m| = rint(|x| 2^-e) fits M = 8 (bpa - 1) - 1 bits,
-// clamped below at -128.
+// clamped below at -128.  Every scaling is by an exact power of two.
 __device__ __forceinline__ bool bpa_entry(double x, int bpa, int* e_out, uint64_t* m_out, double* err) {
   const double a = fabs(x);
   if (a == 0.0) {
@@ -25,19 +29,22 @@ __device__ __forceinline__ bool bpa_entry(double x, int bpa, int* e_out, uint64_
   int E;
   frexp(a, &E);  // a = f 2^E, f in [0.5, 1)
   int e = E - M;
-  uint64_t m = static_cast<uint64_t>(rint(ldexp(a, -e)));
-  if (m == (1ull << M)) {  // rounding carried into the next power of two
-    m >>= 1;
-    ++e;
-  }
+  uint64_t m;
   if (e < -128) {
+    // clamped exponent (a rounding carry from e = -129 lands on the same value)
     e = -128;
-    m = static_cast<uint64_t>(rint(ldexp(a, 128)));
+    m = static_cast<uint64_t>(rint(a * pow2d(64) * pow2d(64)));
+  } else {
+    m = static_cast<uint64_t>(rint(a * pow2d(-e)));
+    if (m == (1ull << M)) {  // rounding carried into the next power of two
+      m >>= 1;
+      ++e;
+    }
   }
   if (e > 127) return false;
   *e_out = e;
   *m_out = m;
-  *err = fabs(ldexp(__ull2double_rn(m), e) - a);
+  *err = fabs(__ull2double_rn(m) * pow2d(e) - a);
   return true;
 }
 
@@ -52,40 +59,34 @@ struct BpaSrc {
   }
 };
 
+// One thread per entry: the entry's smallest bpa (0 if |x| <= eps_mf, else the first of
+// 2..8 whose error is within eps_mf), merged into rec[row] (zeroed before) by atomicMax.
+// The error of an entry never grows with bpa (the finer grid of m 2^e contains the
+// coarser one, and FP64 rounding of the difference is monotone), so the row's smallest
+// admissible bpa is the largest of its entries' smallest ones.
 // *status <- code_nonfinite for a non-finite entry, code_unrep for an entry no bpa can store
 __global__ void k_bpa_choose(BpaSrc src, int64_t n, double eps_mf, uint64_t* rec, int* status, int code_nonfinite,
                              int code_unrep) {
-  const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
-  if (i >= n) return;
-  double amax = 0.0;
-  for (int k = 0; k < src.K; ++k) {
-    const double v = src.at(i, k);
-    if (!isfinite(v)) {
-      if (status) atomicExch(status, code_nonfinite);
-      rec[i] = 0;
+  const int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (t >= n * src.K) return;
+  const int64_t row = t / src.K;
+  const int k = static_cast<int>(t - row * src.K);
+  const double v = src.at(row, k);
+  if (!isfinite(v)) {
+    if (status) atomicExch(status, code_nonfinite);
+    return;
+  }
+  if (fabs(v) <= eps_mf) return;
+  for (int b = 2; b <= 8; ++b) {
+    int e;
+    uint64_t m;
+    double err;
+    if (bpa_entry(v, b, &e, &m, &err) && err <= eps_mf) {
+      atomicMax(reinterpret_cast<unsigned long long*>(rec + row), static_cast<unsigned long long>(b));
       return;
     }
-    amax = fmax(amax, fabs(v));
   }
-  int chosen = 0;
-  if (amax > eps_mf) {
-    chosen = -1;
-    for (int b = 2; b <= 8 && chosen < 0; ++b) {
-      bool ok = true;
-      for (int k = 0; k < src.K && ok; ++k) {
-        int e;
-        uint64_t m;
-        double err;
-        ok = bpa_entry(src.at(i, k), b, &e, &m, &err) && err <= eps_mf;
-      }
-      if (ok) chosen = b;
-    }
-    if (chosen < 0) {
-      if (status) atomicExch(status, code_unrep);
-      chosen = 0;
-    }
-  }
-  rec[i] = static_cast<uint64_t>(chosen);
+  if (status) atomicExch(status, code_unrep);
 }
 
 // one CTA: rec[i] (= bpa) -> (exclusive prefix of bpa * K) << 4 | bpa; *total = bytes
@@ -135,23 +136,25 @@ __global__ void __launch_bounds__(kScanThreads) k_bpa_scan(int64_t n, int K, uin
   if (threadIdx.x == 0) *total = carry;
 }
 
+// one thread per entry: its bpa bytes at the row's offset + k * bpa
 __global__ void k_bpa_write(BpaSrc src, int64_t n, const uint64_t* rec, uint8_t* bytes) {
-  const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
-  if (i >= n) return;
-  const int bpa = static_cast<int>(rec[i] & 15u);
+  const int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (t >= n * src.K) return;
+  const int64_t row = t / src.K;
+  const int k = static_cast<int>(t - row * src.K);
+  const uint64_t r = rec[row];
+  const int bpa = static_cast<int>(r & 15u);
   if (bpa == 0) return;
-  uint8_t* p = bytes + (rec[i] >> 4);
+  uint8_t* p = bytes + (r >> 4) + static_cast<int64_t>(k) * bpa;
+  const double v = src.at(row, k);
+  int e = 0;
+  uint64_t m = 0;
+  double err;
+  if (!isfinite(v) || !bpa_entry(v, bpa, &e, &m, &err)) e = 0, m = 0;  // flagged in k_bpa_choose
   const int M = 8 * (bpa - 1) - 1;
-  for (int k = 0; k < src.K; ++k, p += bpa) {
-    const double v = src.at(i, k);
-    int e;
-    uint64_t m;
-    double err;
-    bpa_entry(v, bpa, &e, &m, &err);  // representable: checked when bpa was chosen
-    const uint64_t word = m | (static_cast<uint64_t>(v < 0.0) << M);
-    p[0] = static_cast<uint8_t>(static_cast<int8_t>(e));
-    for (int j = 1; j < bpa; ++j) p[j] = static_cast<uint8_t>(word >> (8 * (j - 1)));
-  }
+  const uint64_t word = m | (static_cast<uint64_t>(v < 0.0) << M);
+  p[0] = static_cast<uint8_t>(static_cast<int8_t>(e));
+  for (int j = 1; j < bpa; ++j) p[j] = static_cast<uint8_t>(word >> (8 * (j - 1)));
 }
 
 template <typename T>
@@ -168,7 +171,8 @@ inline void bpa_encode_enqueue(const BpaSrc& src, int64_t n, double eps_mf, uint
     cudaMemsetAsync(total, 0, sizeof(uint64_t), s);
     return;
   }
-  const unsigned g = static_cast<unsigned>((n + 255) / 256);
+  const unsigned g = static_cast<unsigned>((n * src.K + 255) / 256);
+  cudaMemsetAsync(rec, 0, static_cast<size_t>(n) * sizeof(uint64_t), s);
   k_bpa_choose<<<g, 256, 0, s>>>(src, n, eps_mf, rec, status, code_nonfinite, code_unrep);
   k_bpa_scan<<<1, kScanThreads, 0, s>>>(n, src.K, rec, total);
   k_bpa_write<<<g, 256, 0, s>>>(src, n, rec, bytes);

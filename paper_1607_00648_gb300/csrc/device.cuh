@@ -130,24 +130,47 @@ template <typename T>
 __device__ __forceinline__ T bpa_decode(const uint8_t* bytes, uint64_t rec, int k) {
   const int bpa = static_cast<int>(rec & 15u);
   if (bpa == 0) return T(0);
-  const uint8_t* p = bytes + (rec >> 4) + static_cast<int64_t>(k) * bpa;
-  const int e = static_cast<int>(static_cast<int8_t>(p[0]));
-  uint64_t w = 0;
-#pragma unroll
-  for (int i = 1; i < 8; ++i)
-    if (i < bpa) w |= static_cast<uint64_t>(p[i]) << (8 * (i - 1));
+  // the entry's bpa bytes from the (one or two) aligned 8-byte words holding them; the
+  // stream is 8-byte aligned and its buffer a multiple of 8 bytes, so both words exist
+  const uint64_t at = (rec >> 4) + static_cast<uint64_t>(k) * bpa;
+  const uint64_t* w = reinterpret_cast<const uint64_t*>(bytes) + (at >> 3);
+  const int sh = static_cast<int>(at & 7u) * 8;
+  uint64_t v = w[0] >> sh;
+  if (sh + 8 * bpa > 64) v |= w[1] << (64 - sh);
+  const int e = static_cast<int>(static_cast<int8_t>(v & 0xffu));
+  const uint64_t word = v >> 8;
   const int M = 8 * (bpa - 1) - 1;
-  const uint64_t m = w & ((1ull << M) - 1ull);
-  T v;
-  if constexpr (std::is_same<T, double>::value) v = ldexp(__ull2double_rn(m), e);
-  else v = ldexpf(__ull2float_rn(m), e);
-  return ((w >> M) & 1u) ? -v : v;
+  const uint64_t m = word & ((1ull << M) - 1ull);
+  // 2^e built from its bit pattern (e in [-128, 127]: normal in FP64; in FP32 normal down
+  // to -126, and 2^-127, 2^-128 are FP32 subnormals), so the product is the one rounding
+  T x;
+  if constexpr (std::is_same<T, double>::value) {
+    x = __ull2double_rn(m) * __longlong_as_double(static_cast<long long>(e + 1023) << 52);
+  } else {
+    const float p2 = e >= -126 ? __int_as_float((e + 127) << 23) : __int_as_float(0x00400000 >> (-127 - e));
+    x = __fmul_rn(__ull2float_rn(m), p2);
+  }
+  return ((word >> M) & 1u) ? -x : x;
+}
+
+// per-vertex key of a delta row: the bpa record (DMODE 4), else a non-zero constant;
+// a zero key marks a dropped operator whose entries all read as zero
+template <int DMODE>
+__device__ __forceinline__ uint64_t delta_row(const void* aux, int64_t slot) {
+  if constexpr (DMODE == 4) return static_cast<const uint64_t*>(aux)[slot];
+  else return 1;
+}
+template <int DMODE>
+__device__ __forceinline__ bool delta_row_live(uint64_t key) {
+  return DMODE != 4 || (key & 15u) != 0;
 }
 
 // delta entry k of the vertex in slot `slot`; idx = its position in the 16-bit or FP64
-// planes.  aux: per-vertex FP32 scales (DMODE 2, 3) or bpa records (DMODE 4).
+// planes.  aux: per-vertex FP32 scales (DMODE 2, 3); DMODE 4 decodes from the stream p
+// with the vertex's record `key` (delta_row).
 template <int DMODE, typename T>
-__device__ __forceinline__ T load_delta(const void* p, const void* aux, int64_t idx, int64_t slot, int k = 0) {
+__device__ __forceinline__ T load_delta(const void* p, const void* aux, int64_t idx, int64_t slot, int k = 0,
+                                        uint64_t key = 0) {
   if constexpr (DMODE == 1) {
     return static_cast<T>(static_cast<const double*>(p)[idx]);
   } else if constexpr (DMODE == 2) {
@@ -157,7 +180,7 @@ __device__ __forceinline__ T load_delta(const void* p, const void* aux, int64_t 
     return static_cast<T>(fp16_bits_to_float(static_cast<const uint16_t*>(p)[idx]) *
                           static_cast<const float*>(aux)[slot]);
   } else if constexpr (DMODE == 4) {
-    return bpa_decode<T>(static_cast<const uint8_t*>(p), static_cast<const uint64_t*>(aux)[slot], k);
+    return bpa_decode<T>(static_cast<const uint8_t*>(p), key, k);
   } else {
     return T(0);
   }

@@ -281,7 +281,8 @@ __device__ __forceinline__ double sweep_item(const SweepArgs<T>& a, int64_t bric
         off *= hscale;
         D = static_cast<T>(elem_k(DIM, 0)) * es_centre * hscale;
       }
-      if constexpr (AMODE != 0) {
+      const uint64_t akey = AMODE != 0 ? delta_row<AMODE>(a.ascale, slot) : 0;
+      if (AMODE != 0 && delta_row_live<AMODE>(akey)) {
 #pragma unroll
         for (int k = 0; k < N3; ++k) {
           int uidx = cu, m = 1, kk = k;
@@ -291,7 +292,7 @@ __device__ __forceinline__ double sweep_item(const SweepArgs<T>& a, int64_t bric
             kk /= 3;
             m *= Bu;
           }
-          const T d = load_delta<AMODE, T>(a.ahat, a.ascale, (brick * N3 + k) * L.S + s, slot, k);
+          const T d = load_delta<AMODE, T>(a.ahat, a.ascale, (brick * N3 + k) * L.S + s, slot, k, akey);
           if (k == N3 / 2)
             D += d;
           else
@@ -393,6 +394,7 @@ __device__ __forceinline__ void restrict_one(const LevelDesc& Lc, const LevelDes
     return;
   }
   const int64_t cb = cs / Lc.S, cl = cs - cb * Lc.S;
+  const uint64_t pkey = PMODE != 0 ? delta_row<PMODE>(pscale, cs) : 0;
   T acc = T(0);
 #pragma unroll
   for (int k = 0; k < N5; ++k) {
@@ -409,7 +411,7 @@ __device__ __forceinline__ void restrict_one(const LevelDesc& Lc, const LevelDes
     const int64_t fs = slot_of_b<DIM, BF>(Lf, y);
     if (fs < 0) continue;
     T p = static_cast<T>(w);
-    if constexpr (PMODE != 0) p += load_delta<PMODE, T>(phat, pscale, (cb * N5 + k) * Lc.S + cl, cs, k);
+    if constexpr (PMODE != 0) p += load_delta<PMODE, T>(phat, pscale, (cb * N5 + k) * Lc.S + cl, cs, k, pkey);
     acc = fma(p, rf[fs], acc);
   }
   bc[cs] = acc;
@@ -454,6 +456,7 @@ __global__ void __launch_bounds__(32 * kRestrictWarps)
   T acc = T(0);
   if (dof) {
     const int64_t cb = cs / Lc.S, cl = cs - cb * Lc.S;
+    const uint64_t pkey = PMODE != 0 ? delta_row<PMODE>(pscale, cs) : 0;
     for (int k = warp; k < N5; k += kRestrictWarps) {
       int y[DIM];
       int kk = k;
@@ -465,7 +468,8 @@ __global__ void __launch_bounds__(32 * kRestrictWarps)
       const int64_t fs = slot_of_b<DIM, BF>(Lf, y);
       if (fs < 0) continue;
       T p = wtab[k];
-      if constexpr (PMODE != 0) p += load_delta<PMODE, T>(phat, pscale, (cb * N5 + k) * Lc.S + cl, cs, k);
+      if constexpr (PMODE != 0)
+        p += load_delta<PMODE, T>(phat, pscale, (cb * N5 + k) * Lc.S + cl, cs, k, pkey);
       acc = fma(p, rf[fs], acc);
     }
   }
@@ -516,7 +520,8 @@ __device__ __forceinline__ void prolong_one(const LevelDesc& Lc, const LevelDesc
     T p = wtab ? wtab[k] : dlin_weight<DIM, T>(k);
     if constexpr (PMODE != 0) {
       const int64_t cb = cs / Lc.S;
-      p += load_delta<PMODE, T>(phat, pscale, (cb * N5 + k) * Lc.S + (cs - cb * Lc.S), cs, k);
+      p += load_delta<PMODE, T>(phat, pscale, (cb * N5 + k) * Lc.S + (cs - cb * Lc.S), cs, k,
+                                delta_row<PMODE>(pscale, cs));
     }
     acc = fma(p, ec[cs], acc);
   }

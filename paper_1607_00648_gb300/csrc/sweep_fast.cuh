@@ -104,12 +104,13 @@ __device__ __forceinline__ double sweep2c_item(const SweepArgs<T>& a, int64_t br
         const T up_l = uc[Bu - 1], up = uc[Bu], up_r = uc[Bu + 1];
         T Au, D;
         stencil2<T>(ec[-Be - 1], ec[-Be], ec[-1], ec[0], um_l, um, um_r, u0_l, u0, u0_r, up_l, up, up_r, Au, D);
-        if constexpr (AMODE != 0) {
+        const uint64_t akey = AMODE != 0 ? delta_row<AMODE>(a.ascale, slot) : 0;
+        if (AMODE != 0 && delta_row_live<AMODE>(akey)) {
           const T nbv[9] = {um_l, um, um_r, u0_l, u0, u0_r, up_l, up, up_r};
           const int sl = (z0 + zl) * B + x;
 #pragma unroll
           for (int q = 0; q < 9; ++q) {
-            const T d = load_delta<AMODE, T>(a.ahat, a.ascale, (brick * 9 + q) * L.S + sl, slot, q);
+            const T d = load_delta<AMODE, T>(a.ahat, a.ascale, (brick * 9 + q) * L.S + sl, slot, q, akey);
             Au = fma(d, nbv[q], Au);
             if (q == 4) D += d;
           }
@@ -239,11 +240,12 @@ __device__ __forceinline__ double sweep3c_item(const SweepArgs<T>& a, int64_t br
         s1 = fma(szm, ub, s1);
         T Au = fma(T(5) * sC, u0, s1 - Q) * (hscale * static_cast<T>(1.0 / 12.0));
         T D = sC * (hscale * static_cast<T>(1.0 / 3.0));
-        if constexpr (AMODE != 0) {
+        const uint64_t akey = AMODE != 0 ? delta_row<AMODE>(a.ascale, slot) : 0;
+        if (AMODE != 0 && delta_row_live<AMODE>(akey)) {
 #pragma unroll
           for (int k = 0; k < N3; ++k) {
             const int off = (k % 3 - 1) + Bu * ((k / 3) % 3 - 1) + UPL * (k / 9 - 1);
-            const T d = load_delta<AMODE, T>(a.ahat, a.ascale, (brick * N3 + k) * L.S + s, slot, k);
+            const T d = load_delta<AMODE, T>(a.ahat, a.ascale, (brick * N3 + k) * L.S + s, slot, k, akey);
             Au = fma(d, uc[off], Au);
             if (k == N3 / 2) D += d;
           }

@@ -187,24 +187,33 @@ def test_encoder_matches_oracle_bit_exact():
         assert np.array_equal(scale.cpu().numpy().view(np.uint32), so.view(np.uint32))
 
 
-def test_mixed_codes_are_the_encoding_of_the_fp64_deltas():
+def test_mixed_codes_hold_the_oracle_deltas():
+    # the codes come from the hierarchy's own FP64 deltas, so they are checked against
+    # the oracle's deltas through the format's bound: scale = fl32(max |delta|) and
+    # |fl32(q * s) - delta| <= half a unit of the 16-bit format (relative to s) + the
+    # FP32 product's rounding + the FP64 setup tolerance
+    half_unit = {"bf16": 2.0 ** -9, "fp16": 2.0 ** -12}
     for fmt, prec in (("bf16", "mixed_bf16"), ("fp16", "mixed_fp16")):
-        c = Case(2, 4, "checker", precision=prec, oracle=False)
+        c = Case(2, 4, "grf", precision=prec)
         torch = c.torch
         for lv in range(1, 4):
             n = c.n(lv)
-            a = torch.empty(9 * n, dtype=torch.float64, device="cuda")
-            p = torch.empty(25 * n, dtype=torch.float64, device="cuda")
-            c.H.get_deltas(lv, a_hat=a, p_hat=p)
+            dof = c.dof(lv)
             ac = torch.empty(9 * n, dtype=torch.int16, device="cuda")
             pc = torch.empty(25 * n, dtype=torch.int16, device="cuda")
             asc = torch.empty(n, dtype=torch.float32, device="cuda")
             psc = torch.empty(n, dtype=torch.float32, device="cuda")
             c.H.get_codes(lv, ac, asc, pc, psc)
-            for dlt, cod, sc, K in ((a, ac, asc, 9), (p, pc, psc, 25)):
-                q, s = codec.encode(c.host(dlt).reshape(K, n).T, fmt)
-                assert np.array_equal(c.host(cod).view(np.uint16).reshape(K, n).T, q)
-                assert np.array_equal(c.host(sc).view(np.uint32), s.view(np.uint32))
+            for cod, sc, K, ref, tol in (
+                    (ac, asc, 9, c.O.ops[lv].a_hat, TOL * c.abs_scale(lv).max(axis=1)),
+                    (pc, psc, 25, c.O.ops[lv + 1].p_hat, np.full(n, TOL))):
+                q = c.host(cod).view(np.uint16).reshape(K, n).T
+                s = c.host(sc)
+                amax = np.abs(ref).max(axis=1)
+                assert np.all((np.abs(s.astype(np.float64) - amax) <= 2.0 ** -24 * amax + tol)[dof])
+                dec = codec.decode(q, s, fmt).astype(np.float64)
+                bound = (half_unit[fmt] + 2.0 ** -24) * s.astype(np.float64) + 2 * tol
+                assert np.all((np.abs(dec - ref) <= bound[:, None])[dof]), (fmt, lv, K)
 
 
 @pytest.mark.parametrize("prec", ["mixed_bf16", "mixed_fp16"])
