@@ -10,6 +10,8 @@ solved directly (dense FP64), as in the paper's exact coarse-grid variants.
 Hierarchy options:
 * transfer = 'dlinear' | 'boxmg' (Sect. 4.4)
 * coarse   = 'redisc'  | 'galerkin' (Sect. 4.3)
+* smoother = 'jacobi'  | 'block' (Sect. 4.2: block Jacobi, Gauss-Seidel sweeps on the
+  iota vertices of every 3^d patch, then damped Jacobi on the c and gamma vertices)
 """
 from __future__ import annotations
 
@@ -41,8 +43,9 @@ class Hierarchy:
 
     def __init__(self, tree: Spacetree, leaf_eps: dict[int, np.ndarray], transfer: str = "boxmg",
                  coarse: str = "galerkin", omega: float = 0.6, nu1: int = 2, nu2: int = 2,
-                 coarsest: int = 1):
+                 coarsest: int = 1, smoother: str = "jacobi", gs_sweeps: int = 1):
         self.tree, self.omega, self.nu1, self.nu2, self.coarsest = tree, omega, nu1, nu2, coarsest
+        self.smoother, self.gs_sweeps = smoother, gs_sweeps
         self.transfer, self.coarse = transfer, coarse
         L = tree.max_level
         self.L = L
@@ -75,12 +78,49 @@ class Hierarchy:
 
     # --- single steps -----------------------------------------------------
     def smooth(self, lv: int, u: np.ndarray, b: np.ndarray, nu: int) -> np.ndarray:
-        """nu omega-damped Jacobi sweeps (Alg. 1 smoothing update)."""
+        """nu smoothing steps: omega-damped Jacobi sweeps (Alg. 1 smoothing update), or
+        block Jacobi steps (Sect. 4.2) with smoother='block'."""
+        if self.smoother == "block":
+            return self.block_smooth(lv, u, b, nu)
         o = self.ops[lv]
         u = u.copy()
         for _ in range(nu):
             r = b - o.A @ u
             u = u + np.where(o.dof, self.omega * r / o.diag, 0.0)
+        return u
+
+    def iota_vertices(self, lv: int) -> np.ndarray:
+        """Slots of the iota DoFs of level lv (Sect. 4.2: vertices inside a 3^d patch, i.e.
+        inside a level lv-1 cell: no coordinate a multiple of 3), patch by patch, within a
+        patch in lexicographic order of the position (x fastest)."""
+        o = self.ops[lv]
+        c = self.tree.levels[lv].coords
+        iota = o.dof & (c[:, 0] >= 0) & np.all(c % 3 != 0, axis=1)
+        idx = np.nonzero(iota)[0]
+        key = sorted(range(len(idx)), key=lambda j: (tuple((c[idx[j]] // 3)[::-1]), tuple(c[idx[j]][::-1])))
+        return idx[key]
+
+    def block_smooth(self, lv: int, u: np.ndarray, b: np.ndarray, nu: int) -> np.ndarray:
+        """nu block Jacobi steps (Sect. 4.2).  Reading of the paper: a step first runs
+        gs_sweeps Gauss-Seidel sweeps over the iota vertices of every patch (each vertex
+        in turn: u_v += (b_v - (A u)_v) / A_vv with the current values), then one
+        omega-damped Jacobi update of the c and gamma DoFs from the values the
+        Gauss-Seidel sweeps left.  Patches share no iota vertex and no iota vertex is
+        a neighbour of another patch's, so the patch order does not matter."""
+        o = self.ops[lv]
+        A = o.A.tocsr()
+        order = self.iota_vertices(lv)
+        not_iota = o.dof.copy()
+        not_iota[order] = False
+        u = u.copy()
+        for _ in range(nu):
+            for _s in range(self.gs_sweeps):
+                for i in order:
+                    lo, hi = A.indptr[i], A.indptr[i + 1]
+                    r = b[i] - A.data[lo:hi] @ u[A.indices[lo:hi]]
+                    u[i] += r / o.diag[i]
+            r = b - A @ u
+            u = u + np.where(not_iota, self.omega * r / o.diag, 0.0)
         return u
 
     def residual(self, lv: int, u: np.ndarray, b: np.ndarray) -> np.ndarray:
