@@ -157,10 +157,11 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def kernel_count(L, c, nu1, nu2, transfer, coarse, precision, cycles, outer, chunk):
+def kernel_count(L, c, nu1, nu2, transfer, coarse, precision, cycles, outer, chunk, block=False):
     """Kernels of ours launched by one mg_setup + mg_solve (memsets / copies excluded)."""
     levels = L - c
-    per_cycle = levels * (nu1 + nu2 + 3) + 1  # sweeps, residual, restrict, prolong per level; coarse solve
+    steps = (nu1 + nu2) * (2 if block else 1)  # a block step: patch Gauss-Seidel + masked Jacobi
+    per_cycle = levels * (steps + 3) + 1  # smoothing, residual, restrict, prolong per level; coarse solve
     setup = (levels + 1) + levels + levels * ((transfer == "boxmg") + (coarse == "galerkin")) + (levels + 1) + 2
     if precision == "fp64":
         return setup + (levels + 1) + 2 + cycles * (per_cycle + 2)  # + the Jacobi factors per level
@@ -345,6 +346,8 @@ def run_breakdown(args):
         eps_cat, b = grid.cells_to_concat({w["L"]: eps}), grid.to_slots(w["L"], bf)
         n_dofs = grid.info(w["L"]).n_dofs
         opts = {"transfer": w["transfer"], "coarse": w["coarse"]}
+    if args.smoother != "jacobi":
+        opts.update(smoother=args.smoother, gs_sweeps=args.gs_sweeps)
     e = torch.from_numpy(eps_cat).cuda()
     bd = torch.from_numpy(b).cuda()
     u = torch.zeros_like(bd)
@@ -453,11 +456,12 @@ def run_ours(args):
             stats.append(res)
             o = H.options
             launches += kernel_count(L, o.coarsest_level, o.nu1, o.nu2, w["transfer"], w["coarse"], prec,
-                                     res["cycles"], res["outer_steps"], o.inner_cycles)
+                                     res["cycles"], res["outer_steps"], o.inner_cycles, block=o.smoother == 1)
         return max_over_ranks(total_ms, dist, dev), launches, stats
 
-    H64 = mg.Hierarchy(grid, transfer=w["transfer"], coarse=w["coarse"], precision="fp64")
-    Hmx = mg.Hierarchy(grid, transfer=w["transfer"], coarse=w["coarse"], precision="mixed_bf16")
+    smo = {} if args.smoother == "jacobi" else {"smoother": args.smoother, "gs_sweeps": args.gs_sweeps}
+    H64 = mg.Hierarchy(grid, transfer=w["transfer"], coarse=w["coarse"], precision="fp64", **smo)
+    Hmx = mg.Hierarchy(grid, transfer=w["transfer"], coarse=w["coarse"], precision="mixed_bf16", **smo)
     tiles = {}
     if not args.no_autotune:  # slab depths by measurement, once, outside the timed region
         for name, H in (("fp64", H64), ("mixed", Hmx)):
@@ -540,7 +544,9 @@ def run_ours(args):
             "config": {"workload": args.workload, "description": w["desc"], "dofs": n_dofs,
                        "cycles_per_solve": st64[-1]["cycles"], "parallelism": f"replicas{world}",
                        "l2": "flushed (512 MB write) before every timed step", "setup_included": True,
-                       "tiles": tiles or "default rule"},
+                       "tiles": tiles or "default rule",
+                       "smoother": "damped Jacobi" if not smo else f"block Jacobi, {args.gs_sweeps} Gauss-Seidel "
+                                                                     f"sweep(s) per patch (Sect. 4.2)"},
             "mixed": None if not (domx and do64) else {
                 "value": value_mx, "unit": "DoF/s", "dtype": "f32 cycles + f64 refinement, bf16 deltas",
                 "ms_per_step": tmx / args.steps, "inner_cycles": stmx[-1]["cycles"],
@@ -885,6 +891,9 @@ def main():
     ap.add_argument("--precision", default="both", choices=("both", "fp64", "mixed", "bpa"),
                     help="which solve forms to time (profiling runs; the default times both; "
                          "bpa: --breakdown of the BF16 and bpa mixed forms)")
+    ap.add_argument("--smoother", default="jacobi", choices=("jacobi", "block"),
+                    help="smoother of the timed solves (the workloads are defined with damped Jacobi)")
+    ap.add_argument("--gs-sweeps", type=int, default=1, help="block smoother: Gauss-Seidel sweeps per patch")
     ap.add_argument("--codecs", action="store_true",
                     help="mixed solves with BF16 deltas against the bpa codec at eps_mf 1e-2 / 1e-4 / 1e-8")
     ap.add_argument("--batched", action="store_true", help="task config 4: batched mixed vs FP64 solves")

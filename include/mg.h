@@ -138,6 +138,14 @@ typedef enum mg_precision {
                              batches, the server or the persistent solve) */
 } mg_precision;
 
+typedef enum mg_smoother {
+  MG_SMOOTH_JACOBI = 0, /* omega-damped point Jacobi (Alg. 1) */
+  MG_SMOOTH_BLOCK = 1   /* block Jacobi (Sect. 4.2): per step, gs_sweeps Gauss-Seidel sweeps over the
+                           2^d iota vertices of every 3^d patch (vertices inside a cell of the next
+                           coarser level, lexicographic within the patch), then omega-damped Jacobi
+                           on the other DoFs.  Uniform levels; single hierarchies only */
+} mg_smoother;
+
 typedef struct mg_options {
   int32_t transfer;       /* mg_transfer (Sect. 4.4: BoxMG, or d-linear) */
   int32_t coarse;         /* mg_coarse_op (Sect. 4.3: Galerkin R A P, or rediscretisation) */
@@ -152,9 +160,12 @@ typedef struct mg_options {
                              dependent graph kernel costs ~0.6 us, a grid-wide barrier ~1.2 us) */
   double eps_mf;          /* MG_PREC_MIXED_BPA: absolute bound on |f_bpa(x) - x| per delta entry
                              (Sect. 5 uses 1e-2, 1e-4, 1e-8); default 1e-4 */
+  int32_t smoother;       /* mg_smoother (default MG_SMOOTH_JACOBI); nu1, nu2 count its steps */
+  int32_t gs_sweeps;      /* MG_SMOOTH_BLOCK: Gauss-Seidel sweeps per patch and step, 1..64 (default 1) */
 } mg_options;
 
-void mg_default_options(mg_options* opt); /* BoxMG, Galerkin, FP64, V(2,2), omega 0.6, coarsest 1, eps_mf 1e-4 */
+void mg_default_options(mg_options* opt); /* BoxMG, Galerkin, FP64, V(2,2), omega 0.6, coarsest 1, eps_mf 1e-4,
+                                             Jacobi smoother */
 
 /* ---------------------------------------------------------------- hierarchy */
 

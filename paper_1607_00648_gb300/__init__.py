@@ -19,6 +19,7 @@ __all__ = ["Batch", "Server", "Grid", "Hierarchy", "MgError", "bpa_decode", "bpa
 TRANSFER = {"dlinear": 0, "boxmg": 1}
 COARSE = {"redisc": 0, "galerkin": 1}
 PRECISION = {"fp64": 0, "mixed_bf16": 1, "mixed_fp16": 2, "mixed_bpa": 3}
+SMOOTHER = {"jacobi": 0, "block": 1}
 
 
 def _stream_ptr(stream) -> C.c_void_p:
@@ -130,6 +131,8 @@ def default_options(**kw) -> Options:
             v = COARSE[v] if isinstance(v, str) else v
         elif k == "precision":
             v = PRECISION[v] if isinstance(v, str) else v
+        elif k == "smoother":
+            v = SMOOTHER[v] if isinstance(v, str) else v
         setattr(o, k, v)
     return o
 

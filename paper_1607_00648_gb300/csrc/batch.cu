@@ -366,6 +366,10 @@ mg_status build_batch(Batch& bt) {
       set_error("mg_batch_create: every hierarchy of a batch needs the same dimension and options");
       return MG_ERR_INVALID_ARG;
     }
+    if (h->opt.smoother != MG_SMOOTH_JACOBI) {
+      set_error("mg_batch_create: batches run the Jacobi smoother only");
+      return MG_ERR_UNSUPPORTED;
+    }
     if (h->fmt == 4) {
       set_error("mg_batch_create: bpa-coded hierarchies (MG_PREC_MIXED_BPA) are single-problem only");
       return MG_ERR_UNSUPPORTED;

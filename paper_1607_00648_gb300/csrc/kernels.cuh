@@ -26,7 +26,17 @@ struct SweepArgs {
   double* norm2;        // fused final sum of r^2 (written by the last CTA), nullable
   int R;                // slab thickness along the last axis (divides B)
   const T* dinv;        // Jacobi: omega / diag(A) per vertex (setup), nullable
+  int block;            // Jacobi of a block step (Sect. 4.2): iota vertices keep their value
 };
+
+// iota vertex of brick slot s (local coordinates; bricks start at multiples of 3): no
+// coordinate a multiple of 3, i.e. inside a cell of the next coarser level
+template <int DIM>
+__device__ __forceinline__ bool iota_local(int s, int B) {
+  const int x = s % B, y = (s / B) % B;
+  if constexpr (DIM == 2) return x % 3 != 0 && y % 3 != 0;
+  return x % 3 != 0 && y % 3 != 0 && (s / (B * B)) % 3 != 0;
+}
 
 // Deterministic CTA reduction of one double per thread; thread 0 returns the sum.
 __device__ __forceinline__ double block_sum(double v) {
@@ -204,12 +214,14 @@ __device__ __forceinline__ double sweep_item(const SweepArgs<T>& a, int64_t bric
     const int64_t slot = base + s;
     T res = T(0);
     const uint8_t vf = L.vflags[slot];
+    const bool keep = OP == kJacobi && a.block && iota_local<DIM>(s, B);
     if constexpr (OP == kJacobi || OP == kJacobiNorm) {
       // hanging vertices keep their value: it is the coarser level's interpolant
-      // (Sect. 3, rule 2), refreshed by the composite cycle, not a smoother unknown
-      if (vf & MG_V_HANGING) res = a.u[slot];
+      // (Sect. 3, rule 2), refreshed by the composite cycle, not a smoother unknown;
+      // so do iota vertices in the Jacobi part of a block step (Sect. 4.2)
+      if ((vf & MG_V_HANGING) || keep) res = a.u[slot];
     }
-    if (is_dof(vf)) {
+    if (is_dof(vf) && !keep) {
       const int x = s % B;
       const int y = DIM == 2 ? 0 : (s / B) % B;
       const int zl = s / PLANE - z0;
@@ -318,6 +330,145 @@ __device__ __forceinline__ double sweep_item(const SweepArgs<T>& a, int64_t bric
     a.out[slot] = res;
   }
   return part;
+}
+
+// Gauss-Seidel sweeps of a block Jacobi step (Sect. 4.2): one thread per 3^d patch (a
+// cell of the next coarser level; (B/3)^d of them per brick).  The thread loads the
+// 4^d vertex values and 3^d cell coefficients of its patch into registers, then
+// updates the 2^d iota vertices x = c + (1 or 2)^d in lexicographic order,
+// u_v += (b_v - (A u)_v) / A_vv with the current values, `sweeps` times, and writes
+// them back.  Patches share no iota vertex and no iota vertex neighbours another
+// patch's, so the in-place updates of different threads never meet.
+template <int DIM, typename T, int AMODE>
+__global__ void __launch_bounds__(DIM == 2 ? 256 : 64) k_patch_gs(SweepArgs<T> a, int sweeps) {
+  constexpr int N3 = cpow(3, DIM), N4 = cpow(4, DIM), NI = 1 << DIM;
+  const LevelDesc& L = a.L;
+  const int pb = L.B / 3;  // patches per brick axis
+  const int pp = DIM == 2 ? pb * pb : pb * pb * pb;
+  const int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (t >= static_cast<int64_t>(L.n_bricks) * pp) return;
+  const int64_t brick = t / pp;
+  int p = static_cast<int>(t - brick * pp);
+  int cl[DIM];  // brick-local corner of the patch (a multiple of 3, at most B - 3)
+#pragma unroll
+  for (int i = 0; i < DIM; ++i) {
+    cl[i] = 3 * (p % pb);
+    p /= pb;
+  }
+  // slot of corner + d, d in {0..3}^d: the same brick, or for a local coordinate of B
+  // the next brick along that axis (brick neighbour table, -1 beyond the domain)
+  const int32_t* bn = L.brick_nbr + brick * N3;
+  auto slot_at = [&](const int* d) -> int64_t {
+    int bidx = 0, m3 = 1;
+    int64_t li = 0, mb = 1;
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) {
+      int l = cl[i] + d[i];
+      const int o = l >= L.B ? 1 : 0;
+      l -= o * L.B;
+      bidx += (o + 1) * m3;
+      m3 *= 3;
+      li += l * mb;
+      mb *= L.B;
+    }
+    const int32_t nb = bn[bidx];
+    return nb < 0 ? -1 : static_cast<int64_t>(nb) * L.S + li;
+  };
+  T* u = a.out;  // the iterate, updated in place (a.u aliases it)
+  T ul[N4];      // vertex values at corner + {0..3}^d
+  T el[N3];      // cell coefficients of the patch's cells corner + {0..2}^d
+#pragma unroll
+  for (int q = 0; q < N4; ++q) {
+    int d[DIM], qq = q;
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) {
+      d[i] = qq % 4;
+      qq /= 4;
+    }
+    const int64_t w = slot_at(d);
+    ul[q] = w >= 0 ? u[w] : T(0);
+  }
+#pragma unroll
+  for (int q = 0; q < N3; ++q) {
+    int d[DIM], qq = q;
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) {
+      d[i] = qq % 3;
+      qq /= 3;
+    }
+    el[q] = a.eps[slot_at(d)];  // inside the patch's own brick
+  }
+  int64_t vs[NI];
+  T bv[NI];
+#pragma unroll
+  for (int j = 0; j < NI; ++j) {
+    int d[DIM];
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) d[i] = 1 + ((j >> i) & 1);
+    const int64_t v = slot_at(d);
+    vs[j] = (v >= 0 && is_dof(L.vflags[v])) ? v : -1;
+    bv[j] = vs[j] >= 0 ? a.b[v] : T(0);
+  }
+  const T scale = DIM == 3 ? static_cast<T>(L.h) : T(1);
+  for (int sw = 0; sw < sweeps; ++sw) {
+#pragma unroll
+    for (int j = 0; j < NI; ++j) {
+      if (vs[j] < 0) continue;
+      int q[DIM];  // local position of the vertex, in {1,2}^d
+#pragma unroll
+      for (int i = 0; i < DIM; ++i) q[i] = 1 + ((j >> i) & 1);
+      const uint64_t key = AMODE != 0 ? delta_row<AMODE>(a.ascale, vs[j]) : 0;
+      T au = T(0), diag = T(0);
+#pragma unroll
+      for (int k = 0; k < N3; ++k) {
+        int o[DIM], kk = k, ham = 0, un = 0, m4 = 1;
+#pragma unroll
+        for (int i = 0; i < DIM; ++i) {
+          o[i] = kk % 3 - 1;
+          kk /= 3;
+          ham += o[i] != 0;
+          un += (q[i] + o[i]) * m4;
+          m4 *= 4;
+        }
+        T es = T(0);  // cells holding both the vertex and its neighbour x + o
+#pragma unroll
+        for (int e = 0; e < NI; ++e) {
+          bool ok = true;
+          int cl = 0, m3 = 1;
+#pragma unroll
+          for (int i = 0; i < DIM; ++i) {
+            const int ei = (e >> i) & 1;
+            ok = ok && ei + o[i] >= 0 && ei + o[i] <= 1;
+            cl += (q[i] - ei) * m3;
+            m3 *= 3;
+          }
+          if (ok) es += el[cl];
+        }
+        T st = static_cast<T>(elem_k(DIM, ham)) * es * scale;
+        if constexpr (AMODE != 0) st += load_delta<AMODE, T>(a.ahat, a.ascale, plane_index(L, vs[j], k, N3), vs[j], k, key);
+        if (k == N3 / 2) diag = st;
+        au = fma(st, ul[un], au);
+      }
+      int ui = 0, m4 = 1;
+#pragma unroll
+      for (int i = 0; i < DIM; ++i) {
+        ui += q[i] * m4;
+        m4 *= 4;
+      }
+      ul[ui] += (bv[j] - au) / diag;
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < NI; ++j) {
+    if (vs[j] < 0) continue;
+    int ui = 0, m4 = 1;
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) {
+      ui += (1 + ((j >> i) & 1)) * m4;
+      m4 *= 4;
+    }
+    u[vs[j]] = ul[ui];
+  }
 }
 
 template <int DIM, typename T, int AMODE, int OP, int B>
@@ -583,6 +734,10 @@ inline int pick_slab(int B, int64_t n_bricks, int64_t target) {
 
 template <int DIM, typename T>
 void launch_sweep(SweepArgs<T> a, int op, int amode, cudaStream_t s);
+
+// Gauss-Seidel part of a block Jacobi step (Sect. 4.2) on a.u in place
+template <int DIM, typename T>
+void launch_patch_gs(SweepArgs<T> a, int amode, int sweeps, cudaStream_t s);
 
 // list / n_list: the coarse (restriction) or fine (prolongation) slots to serve;
 // nullptr serves every slot of the target level

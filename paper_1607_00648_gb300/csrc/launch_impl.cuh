@@ -87,6 +87,23 @@ static void transfer_b(const LevelDesc& Lc, const LevelDesc& Lf, bool restrict_o
 #undef MG_TR
 }
 
+template <int DIM, typename T>
+static void patch_gs_b(SweepArgs<T> a, int amode, int sweeps, cudaStream_t s) {
+  const int64_t pb = a.L.B / 3, pp = DIM == 2 ? pb * pb : pb * pb * pb;  // patches per brick
+  constexpr int nt = DIM == 2 ? 256 : 64;
+  const unsigned g = static_cast<unsigned>((a.L.n_bricks * pp + nt - 1) / nt);
+  if (g == 0 || sweeps <= 0) return;
+  if constexpr (std::is_same<T, double>::value) {
+    if (amode == 1) k_patch_gs<DIM, T, 1><<<g, nt, 0, s>>>(a, sweeps);
+    else k_patch_gs<DIM, T, 0><<<g, nt, 0, s>>>(a, sweeps);
+  } else {
+    if (amode == 2) k_patch_gs<DIM, T, 2><<<g, nt, 0, s>>>(a, sweeps);
+    else if (amode == 3) k_patch_gs<DIM, T, 3><<<g, nt, 0, s>>>(a, sweeps);
+    else if (amode == 4) k_patch_gs<DIM, T, 4><<<g, nt, 0, s>>>(a, sweeps);
+    else k_patch_gs<DIM, T, 0><<<g, nt, 0, s>>>(a, sweeps);
+  }
+}
+
 }  // namespace mg
 
 #define MG_INSTANTIATE_LAUNCHERS(DIM, T)                                                                    \
@@ -98,6 +115,10 @@ static void transfer_b(const LevelDesc& Lc, const LevelDesc& Lf, bool restrict_o
       case 9: sweep_b<DIM, T, 9>(a, op, amode, s); break;                                                   \
       default: MG_SWEEP_27(DIM, T) break;                                                                   \
     }                                                                                                       \
+  }                                                                                                         \
+  template <>                                                                                               \
+  void launch_patch_gs<DIM, T>(SweepArgs<T> a, int amode, int sweeps, cudaStream_t s) {                     \
+    patch_gs_b<DIM, T>(a, amode, sweeps, s);                                                                \
   }                                                                                                         \
   template <>                                                                                               \
   void launch_transfer<DIM, T>(const LevelDesc& Lc, const LevelDesc& Lf, bool r, int pmode, const T* in,     \

@@ -603,7 +603,8 @@ static mg_status create(const Grid* g, const mg_options& o, Hier** out, int prio
 mg_status hier_create(const Grid* g, const mg_options& o, int priority, Hier** out, bool blocking) {
   *out = nullptr;
   if (o.coarsest_level < 1 || o.coarsest_level >= g->L || o.nu1 < 0 || o.nu2 < 0 || !(o.omega > 0.0) ||
-      o.transfer < 0 || o.transfer > 1 || o.coarse < 0 || o.coarse > 1 || o.precision < 0 || o.precision > 3 ||
+      o.transfer < 0 || o.transfer > 1 || o.coarse < 0 || o.coarse > 1 || o.precision < 0 || o.precision > 3 || o.smoother < 0 || o.smoother > 1 ||
+      (o.smoother == MG_SMOOTH_BLOCK && (o.gs_sweeps < 1 || o.gs_sweeps > 64)) ||
       (o.precision == MG_PREC_MIXED_BPA && !(o.eps_mf >= 0.0 && o.eps_mf < 1e300))) {
     set_error("mg_hier_create: invalid options");
     return MG_ERR_INVALID_ARG;
@@ -753,13 +754,26 @@ static void coarse_solve(const Hier& H, const T* b, T* u, cudaStream_t s) {
                H.n_c, static_cast<const int32_t*>(H.c_slots), b, u);
 }
 
-// nu damped Jacobi sweeps, ping-pong through tmp, result in u
+// nu smoothing steps, ping-pong through tmp, result in u: damped Jacobi sweeps, or block
+// Jacobi steps (Sect. 4.2: Gauss-Seidel on the patches' iota vertices in place, then the
+// Jacobi sweep with the iota values kept) on the uniform levels of a block hierarchy
 template <typename T>
 static void smooth(const Hier& H, int l, T* u, const T* b, T* tmp, int nu, cudaStream_t s) {
   T* src = u;
   T* dst = tmp;
+  const bool block = H.opt.smoother == MG_SMOOTH_BLOCK && l <= H.top;
   for (int k = 0; k < nu; ++k) {
-    sweep<T>(H, l, kJacobi, src, b, dst, nullptr, s);
+    if (block) {
+      int amode = 0;
+      SweepArgs<T> g = sweep_args<T>(H, l, src, b, src, &amode);
+      const int gs = H.opt.gs_sweeps;
+      if (H.dim == 2) launch_patch_gs<2, T>(g, amode, gs, s); else launch_patch_gs<3, T>(g, amode, gs, s);
+      SweepArgs<T> a = sweep_args<T>(H, l, src, b, dst, &amode);
+      a.block = 1;
+      launch<T>(H, a, kJacobi, amode, s);
+    } else {
+      sweep<T>(H, l, kJacobi, src, b, dst, nullptr, s);
+    }
     T* t = src;
     src = dst;
     dst = t;
@@ -1549,6 +1563,8 @@ void mg_default_options(mg_options* o) {
   o->use_graphs = 1;
   o->persistent = 0;
   o->eps_mf = 1e-4;
+  o->smoother = MG_SMOOTH_JACOBI;
+  o->gs_sweeps = 1;
 }
 
 mg_status mg_hier_create(const mg_grid* grid, const mg_options* opt, mg_hier** out) {
@@ -1773,7 +1789,8 @@ mg_status mg_solve(mg_hier* h, double* u, const double* b, double rel_tol, int m
   }
   cudaStream_t s = pick(*H, stream);
   const auto t0 = std::chrono::steady_clock::now();
-  const bool persistent = H->opt.persistent && !H->adaptive && H->fmt != 4 && H->n_c <= 64 && H->L < kMaxLevels;
+  const bool persistent = H->opt.persistent && !H->adaptive && H->fmt != 4 && H->opt.smoother == MG_SMOOTH_JACOBI &&
+                          H->n_c <= 64 && H->L < kMaxLevels;
   const mg_status st = H->adaptive ? (H->mixed ? solve_comp_mixed(*H, u, b, rel_tol, max_cycles, stats, s)
                                                  : solve_comp_fp64(*H, u, b, rel_tol, max_cycles, stats, s))
                        : persistent ? solve_persistent(*H, u, b, rel_tol, max_cycles, stats, s)

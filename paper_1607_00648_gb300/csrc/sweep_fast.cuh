@@ -95,10 +95,12 @@ __device__ __forceinline__ double sweep2c_item(const SweepArgs<T>& a, int64_t br
       const T* uc = su + (zl + 1) * Bu + lane;  // tile column of x is lane
       const T* ec = se + (zl + 1) * Be + lane;  // cell with lower corner (x, y)
       T res = T(0);
+      // iota vertices keep their value in the Jacobi part of a block step (Sect. 4.2)
+      const bool keep = OP == kJacobi && a.block && x % 3 != 0 && (z0 + zl) % 3 != 0;
       if constexpr (OP == kJacobi || OP == kJacobiNorm) {
-        if (vf & MG_V_HANGING) res = uc[0];  // hanging values come from the coarser level (Sect. 3)
+        if ((vf & MG_V_HANGING) || keep) res = uc[0];  // hanging values come from the coarser level (Sect. 3)
       }
-      if (is_dof(vf)) {
+      if (is_dof(vf) && !keep) {
         const T um_l = uc[-Bu - 1], um = uc[-Bu], um_r = uc[-Bu + 1];
         const T u0_l = uc[-1], u0 = uc[0], u0_r = uc[1];
         const T up_l = uc[Bu - 1], up = uc[Bu], up_r = uc[Bu + 1];
@@ -222,10 +224,11 @@ __device__ __forceinline__ double sweep3c_item(const SweepArgs<T>& a, int64_t br
       const int64_t slot = base + s;
       const uint8_t vf = fv[zl];
       T res = T(0);
+      const bool keep = OP == kJacobi && a.block && x % 3 != 0 && y % 3 != 0 && (z0 + zl) % 3 != 0;
       if constexpr (OP == kJacobi || OP == kJacobiNorm) {
-        if (vf & MG_V_HANGING) res = u0;
+        if ((vf & MG_V_HANGING) || keep) res = u0;
       }
-      if (is_dof(vf)) {
+      if (is_dof(vf) && !keep) {
         // cell e<bx><by><bz> has lower corner v - (bx, by, bz): a = above (bz 0), b = below
         const T p00 = ea0 + eb0, p10 = ea1 + eb1, p01 = ea2 + eb2, p11 = ea3 + eb3;
         const T sxp = p00 + p01, sxm = p10 + p11, syp = p00 + p10, sym = p01 + p11;

@@ -40,7 +40,8 @@ class Case:
     """One problem on the CPU oracle and on the GPU library, same slot numbering."""
 
     def __init__(self, dim, L, eps_kind="checker", transfer="boxmg", coarse="galerkin", precision="fp64",
-                 seed=0, omega=0.6, nu1=2, nu2=2, load="uniform", oracle=True, persistent=0, eps_mf=None):
+                 seed=0, omega=0.6, nu1=2, nu2=2, load="uniform", oracle=True, persistent=0, eps_mf=None,
+                 smoother="jacobi", gs_sweeps=1):
         import torch
 
         self.mg = lib()
@@ -49,6 +50,8 @@ class Case:
         self.eps = eps_field(eps_kind, L, dim, seed)
         self.grid = self.mg.Grid(dim, L)
         extra = {} if eps_mf is None else {"eps_mf": eps_mf}
+        if smoother != "jacobi":
+            extra.update(smoother=smoother, gs_sweeps=gs_sweeps)
         self.H = self.mg.Hierarchy(self.grid, transfer=transfer, coarse=coarse, precision=precision,
                                    omega=omega, nu1=nu1, nu2=nu2, persistent=persistent, **extra)
         eps_cat = self.grid.cells_to_concat({L: self.eps})
@@ -57,7 +60,8 @@ class Case:
         torch.cuda.synchronize()
         self.tree = stt.Spacetree(dim, L) if oracle else None
         self.O = (multigrid.Hierarchy(self.tree, {L: self.eps}, transfer=transfer, coarse=coarse, omega=omega,
-                                      nu1=nu1, nu2=nu2) if oracle else None)
+                                      nu1=nu1, nu2=nu2, smoother=smoother, gs_sweeps=gs_sweeps)
+                  if oracle else None)
         if load == "sin":
             bf = syn.sin_load(L, dim)
         elif load == "unit":

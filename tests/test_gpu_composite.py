@@ -22,7 +22,7 @@ TOL = 1e-12
 
 
 class Comp:
-    def __init__(self, dim, L, precision="fp64", eps_kind="sphere", seed=0):
+    def __init__(self, dim, L, precision="fp64", eps_kind="sphere", seed=0, **hier_options):
         import torch
 
         self.torch = torch
@@ -38,7 +38,7 @@ class Comp:
             self.eps = {lv: syn.lognormal_grf_eps(lv, dim, sigma=2.0, seed=seed + lv) for lv in (L, T)}
         self.C = composite.Composite(self.tree, self.eps)
         self.grid = mg.Grid(dim, L, {T: mask})
-        self.H = mg.Hierarchy(self.grid, precision=precision)
+        self.H = mg.Hierarchy(self.grid, precision=precision, **hier_options)
         self.H.setup(torch.from_numpy(self.grid.cells_to_concat(self.eps)).cuda())
         self.oL, self.nL = self.grid.info(L).slot_offset, self.grid.info(L).n_slots
         self.oT, self.nT = self.grid.info(T).slot_offset, self.grid.info(T).n_slots

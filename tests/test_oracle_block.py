@@ -88,7 +88,7 @@ def test_many_sweeps_reach_the_exact_patch_solve():
 
 @pytest.mark.parametrize("eps_kind", ["checker", "grf"])
 def test_block_smoothing_speeds_up_convergence(eps_kind):
-    # Sect. 7 ("block smoothers can double the convergence speed"): fewer V(2,2) cycles
+    # Sect. 7 reports block smoothing up to halving the cycle count: fewer V(2,2) cycles
     dim, L = 2, 4
     eps = (syn.checkerboard_eps(L, dim, seed=0) if eps_kind == "checker"
            else syn.lognormal_grf_eps(L, dim, sigma=2.0, seed=1000))
