@@ -164,6 +164,62 @@ class Hierarchy:
             hist.append(np.linalg.norm(self.residual(self.L, u, b)))
         return u, np.array(hist)
 
+    # --- additive multigrid (Alg. 2) --------------------------------------
+    def inject(self, lv: int, u_fine: np.ndarray) -> np.ndarray:
+        """I: a level lv-1 DoF takes the level-lv value at the same position (Sect. 3, rule 1)."""
+        ch = self.tree.child_map(lv - 1)
+        ok = self.ops[lv - 1].dof & (ch >= 0)
+        out = np.zeros(ch.size)
+        out[ok] = u_fine[ch[ok]]
+        return out
+
+    def additive_traversal(self, u: dict, d: dict, b: np.ndarray) -> None:
+        """One grid traversal of the additive multigrid of Alg. 2, in place on the level
+        iterates u[l] (u[L] is the solution) and corrections d[l], levels coarsest .. L.
+
+        Coarse to fine (the descent): d_l += P d_{l-1} and u_l += P d_{l-1} (the coarse
+        corrections of the previous traversal), the hierarchical surplus
+        uh_l = u_l - P u_{l-1}, and the coarse right-hand sides cleared.  Fine to coarse
+        (the ascent): r_l = b_l - A_l u_l, rh_l = b_l - A_l uh_l, d_l = omega D_l^-1 r_l,
+        u_l += d_l, then u_{l-1} = I u_l and b_{l-1} = R rh_l.  Every level, the coarsest
+        included, is smoothed; nothing is solved exactly."""
+        L, c = self.L, self.coarsest
+        uh, bb = {}, {}
+        for lv in range(c, L + 1):
+            dof = self.ops[lv].dof
+            if lv > c:
+                pd = np.where(dof, self.prolong(lv, d[lv - 1]), 0.0)
+                d[lv] = d[lv] + pd
+                u[lv] = u[lv] + pd
+                uh[lv] = u[lv] - np.where(dof, self.prolong(lv, u[lv - 1]), 0.0)
+            else:
+                uh[lv] = u[lv].copy()
+            bb[lv] = b if lv == L else np.zeros_like(u[lv])
+        for lv in range(L, c - 1, -1):
+            o = self.ops[lv]
+            r = self.residual(lv, u[lv], bb[lv])
+            rh = self.residual(lv, uh[lv], bb[lv])
+            d[lv] = np.where(o.dof, self.omega * r / o.diag, 0.0)
+            u[lv] = u[lv] + d[lv]
+            if lv > c:
+                u[lv - 1] = self.inject(lv, u[lv])
+                bb[lv - 1] = np.where(self.ops[lv - 1].dof, self.restrict(lv, rh), 0.0)
+
+    def additive_solve(self, b: np.ndarray, rel_tol: float = 1e-10, max_cycles: int = 100):
+        """Additive traversals from u = 0 until ||b - A u_L||_2 / ||b||_2 <= rel_tol;
+        returns (u_L, history of relative residuals)."""
+        L = self.L
+        u = {lv: np.zeros(self.ops[lv].dof.size) for lv in range(self.coarsest, L + 1)}
+        d = {lv: np.zeros_like(u[lv]) for lv in u}
+        r0 = np.linalg.norm(self.residual(L, u[L], b))
+        hist = [r0]
+        for _ in range(max_cycles):
+            if hist[-1] <= rel_tol * r0:
+                break
+            self.additive_traversal(u, d, b)
+            hist.append(np.linalg.norm(self.residual(L, u[L], b)))
+        return u[L], np.array(hist)
+
     def direct(self, b: np.ndarray) -> np.ndarray:
         """Exact discrete solution of the finest level (sparse direct solve)."""
         o = self.ops[self.L]
