@@ -455,12 +455,19 @@ def run_ours(args):
             total_ms += e0.elapsed_time(e1)
             stats.append(res)
             o = H.options
-            launches += kernel_count(L, o.coarsest_level, o.nu1, o.nu2, w["transfer"], w["coarse"], prec,
-                                     res["cycles"], res["outer_steps"], o.inner_cycles, block=o.smoother == 1)
+            if o.cycle == 1:  # setup and r0 as for V-cycles; per traversal and level: 3 prolongations,
+                # negate, 2 residuals, correction, inject, restrict; the finest residual norm
+                lv = L - o.coarsest_level
+                launches += kernel_count(L, o.coarsest_level, o.nu1, o.nu2, w["transfer"], w["coarse"], prec,
+                                         0, 0, o.inner_cycles) + res["cycles"] * (9 * lv + 3 + 1)
+            else:
+                launches += kernel_count(L, o.coarsest_level, o.nu1, o.nu2, w["transfer"], w["coarse"], prec,
+                                         res["cycles"], res["outer_steps"], o.inner_cycles, block=o.smoother == 1)
         return max_over_ranks(total_ms, dist, dev), launches, stats
 
     smo = {} if args.smoother == "jacobi" else {"smoother": args.smoother, "gs_sweeps": args.gs_sweeps}
-    H64 = mg.Hierarchy(grid, transfer=w["transfer"], coarse=w["coarse"], precision="fp64", **smo)
+    cyc = {} if args.cycle == "v" else {"cycle": args.cycle}
+    H64 = mg.Hierarchy(grid, transfer=w["transfer"], coarse=w["coarse"], precision="fp64", **smo, **cyc)
     Hmx = mg.Hierarchy(grid, transfer=w["transfer"], coarse=w["coarse"], precision="mixed_bf16", **smo)
     tiles = {}
     if not args.no_autotune:  # slab depths by measurement, once, outside the timed region
@@ -468,6 +475,8 @@ def run_ours(args):
             H.setup(eps_dev)
             tiles[name] = {str(k): v for k, v in H.autotune().items()}
     do64, domx = args.precision in ("both", "fp64"), args.precision in ("both", "mixed")
+    if cyc:  # the additive cycle runs on FP64 hierarchies only
+        do64, domx = True, False
     with Clocks(torch.cuda.current_device()) as clk:
         if do64:
             t64, launches64, st64 = timed(H64, args.steps, args.warmup, "fp64")
@@ -546,7 +555,8 @@ def run_ours(args):
                        "l2": "flushed (512 MB write) before every timed step", "setup_included": True,
                        "tiles": tiles or "default rule",
                        "smoother": "damped Jacobi" if not smo else f"block Jacobi, {args.gs_sweeps} Gauss-Seidel "
-                                                                     f"sweep(s) per patch (Sect. 4.2)"},
+                                                                     f"sweep(s) per patch (Sect. 4.2)",
+                       "cycle": "V(2,2)" if not cyc else "additive (Alg. 2)"},
             "mixed": None if not (domx and do64) else {
                 "value": value_mx, "unit": "DoF/s", "dtype": "f32 cycles + f64 refinement, bf16 deltas",
                 "ms_per_step": tmx / args.steps, "inner_cycles": stmx[-1]["cycles"],
@@ -894,6 +904,8 @@ def main():
     ap.add_argument("--smoother", default="jacobi", choices=("jacobi", "block"),
                     help="smoother of the timed solves (the workloads are defined with damped Jacobi)")
     ap.add_argument("--gs-sweeps", type=int, default=1, help="block smoother: Gauss-Seidel sweeps per patch")
+    ap.add_argument("--cycle", default="v", choices=("v", "additive"),
+                    help="multigrid cycle of the timed FP64 solve (additive: Alg. 2; FP64 only)")
     ap.add_argument("--codecs", action="store_true",
                     help="mixed solves with BF16 deltas against the bpa codec at eps_mf 1e-2 / 1e-4 / 1e-8")
     ap.add_argument("--batched", action="store_true", help="task config 4: batched mixed vs FP64 solves")

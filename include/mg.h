@@ -146,6 +146,16 @@ typedef enum mg_smoother {
                            on the other DoFs.  Uniform levels; single hierarchies only */
 } mg_smoother;
 
+typedef enum mg_cycle {
+  MG_CYCLE_V = 0,        /* multiplicative V(nu1, nu2) cycles (Alg. 1) */
+  MG_CYCLE_ADDITIVE = 1  /* additive multigrid (Alg. 2): per traversal, the coarse corrections of the
+                            previous traversal prolongated down (d_l += P d_{l-1}, u_l += P d_{l-1},
+                            surplus uh_l = u_l - P u_{l-1}), then fine to coarse r_l = b_l - A_l u_l,
+                            rh_l = b_l - A_l uh_l, d_l = omega D_l^-1 r_l, u_l += d_l, u_{l-1} = I u_l,
+                            b_{l-1} = R rh_l; every level smoothed, none solved.  FP64 uniform
+                            hierarchies, single problems only; mg_solve stops on ||b - A u||_2 */
+} mg_cycle;
+
 typedef struct mg_options {
   int32_t transfer;       /* mg_transfer (Sect. 4.4: BoxMG, or d-linear) */
   int32_t coarse;         /* mg_coarse_op (Sect. 4.3: Galerkin R A P, or rediscretisation) */
@@ -162,6 +172,7 @@ typedef struct mg_options {
                              (Sect. 5 uses 1e-2, 1e-4, 1e-8); default 1e-4 */
   int32_t smoother;       /* mg_smoother (default MG_SMOOTH_JACOBI); nu1, nu2 count its steps */
   int32_t gs_sweeps;      /* MG_SMOOTH_BLOCK: Gauss-Seidel sweeps per patch and step, 1..64 (default 1) */
+  int32_t cycle;          /* mg_cycle (default MG_CYCLE_V); mg_vcycle runs one traversal of it */
 } mg_options;
 
 void mg_default_options(mg_options* opt); /* BoxMG, Galerkin, FP64, V(2,2), omega 0.6, coarsest 1, eps_mf 1e-4,

@@ -20,6 +20,7 @@ TRANSFER = {"dlinear": 0, "boxmg": 1}
 COARSE = {"redisc": 0, "galerkin": 1}
 PRECISION = {"fp64": 0, "mixed_bf16": 1, "mixed_fp16": 2, "mixed_bpa": 3}
 SMOOTHER = {"jacobi": 0, "block": 1}
+CYCLE = {"v": 0, "additive": 1}
 
 
 def _stream_ptr(stream) -> C.c_void_p:
@@ -133,6 +134,8 @@ def default_options(**kw) -> Options:
             v = PRECISION[v] if isinstance(v, str) else v
         elif k == "smoother":
             v = SMOOTHER[v] if isinstance(v, str) else v
+        elif k == "cycle":
+            v = CYCLE[v] if isinstance(v, str) else v
         setattr(o, k, v)
     return o
 

@@ -38,7 +38,7 @@ class Options(C.Structure):
                 ("nu1", C.c_int32), ("nu2", C.c_int32), ("omega", C.c_double),
                 ("coarsest_level", C.c_int32), ("inner_cycles", C.c_int32), ("use_graphs", C.c_int32),
                 ("persistent", C.c_int32), ("eps_mf", C.c_double), ("smoother", C.c_int32),
-                ("gs_sweeps", C.c_int32)]
+                ("gs_sweeps", C.c_int32), ("cycle", C.c_int32)]
 
 
 class SolveStats(C.Structure):

@@ -366,8 +366,8 @@ mg_status build_batch(Batch& bt) {
       set_error("mg_batch_create: every hierarchy of a batch needs the same dimension and options");
       return MG_ERR_INVALID_ARG;
     }
-    if (h->opt.smoother != MG_SMOOTH_JACOBI) {
-      set_error("mg_batch_create: batches run the Jacobi smoother only");
+    if (h->opt.smoother != MG_SMOOTH_JACOBI || h->opt.cycle != MG_CYCLE_V) {
+      set_error("mg_batch_create: batches run V-cycles with the Jacobi smoother only");
       return MG_ERR_UNSUPPORTED;
     }
     if (h->fmt == 4) {

@@ -36,6 +36,8 @@ struct DevLevel {
   double *u = nullptr, *b = nullptr, *r = nullptr, *t = nullptr;
   float *u32 = nullptr, *b32 = nullptr, *r32 = nullptr, *t32 = nullptr;
   double* dinv = nullptr;  // FP64 hierarchies: omega / diag(A) for the Jacobi sweeps
+  double *ad = nullptr, *ar = nullptr;  // additive cycle: correction d_l, surplus residual rh_l
+  int32_t* child = nullptr;             // additive cycle: level-(l+1) slot at position 3x (injection)
   int R64 = 0, R32 = 0;    // slab depths picked by mg_autotune (0: the default rule)
   double* partial = nullptr;
   unsigned* counter = nullptr;
@@ -84,7 +86,7 @@ struct Hier {
   void* d_psolve = nullptr;
   cudaStream_t own = nullptr;
   bool ready = false;
-  Graph g_cycle64, g_outer, g_inner, g_comp64, g_comp_outer, g_comp_inner;
+  Graph g_cycle64, g_outer, g_inner, g_comp64, g_comp_outer, g_comp_inner, g_add;
 };
 
 // ---- device memory of hierarchies and batches (solver.cu) ----

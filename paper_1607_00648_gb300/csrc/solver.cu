@@ -82,6 +82,25 @@ __global__ void k_inject(LevelDesc Lt, const int32_t* child, const T* uL, T* ut)
   if (is_dof(f) && (f & MG_V_REFINED)) ut[s] = uL[child[s]];
 }
 
+// additive cycle (Alg. 2), element-wise steps: d = omega D^-1 r on DoFs (zero elsewhere)
+// and u += d; the negated copy of a vector; injection u_c = I u_f on every coarse DoF
+__global__ void k_add_correct(LevelDesc L, const double* dinv, const double* r, double* d, double* u) {
+  const int64_t s = blockIdx.x * static_cast<int64_t>(kBlock) + threadIdx.x;
+  if (s >= L.n_slots) return;
+  const double c = is_dof(L.vflags[s]) ? dinv[s] * r[s] : 0.0;
+  d[s] = c;
+  u[s] += c;
+}
+__global__ void k_negate(int64_t n, const double* x, double* y) {
+  const int64_t s = blockIdx.x * static_cast<int64_t>(kBlock) + threadIdx.x;
+  if (s < n) y[s] = -x[s];
+}
+__global__ void k_inject_level(LevelDesc Lc, const int32_t* child, const double* uf, double* uc) {
+  const int64_t s = blockIdx.x * static_cast<int64_t>(kBlock) + threadIdx.x;
+  if (s >= Lc.n_slots) return;
+  uc[s] = (is_dof(Lc.vflags[s]) && child[s] >= 0) ? uf[child[s]] : 0.0;
+}
+
 // coarse-correction right-hand side off the refined vertices: the level-t residual
 // at unrefined DoFs, zero at non-DoFs (the restriction fills the refined DoFs)
 template <typename T>
@@ -414,6 +433,7 @@ static void free_hier(Hier* H, bool device_sync) {
   H->g_comp64.reset();
   H->g_comp_outer.reset();
   H->g_comp_inner.reset();
+  H->g_add.reset();
   for (void* p : H->allocs) pool_free(p, H->own);
   pinned_release(H->h_pin);
   if (H->own) cudaStreamDestroy(H->own);
@@ -477,6 +497,22 @@ static mg_status create(const Grid* g, const mg_options& o, Hier** out, int prio
     if ((st = dalloc(*H, &D.eps, ns)) != MG_OK) return fail(st);
     if ((st = dalloc(*H, &D.r, ns)) != MG_OK) return fail(st);
     if ((st = dalloc(*H, &D.t, ns)) != MG_OK) return fail(st);
+    if (o.cycle == MG_CYCLE_ADDITIVE) {
+      if ((st = dalloc(*H, &D.ad, ns)) != MG_OK) return fail(st);
+      if ((st = dalloc(*H, &D.ar, ns)) != MG_OK) return fail(st);
+      if (l < H->L) {  // injection map: the level-(l+1) slot at position 3x
+        const HostLevel& hf = g->levels[l + 1];
+        std::vector<int32_t> child(hl.n_slots, -1);
+        int x[3];
+        for (int64_t q = 0; q < hl.n_slots; ++q) {
+          hl.coords_of(q, x);
+          if (x[0] < 0) continue;
+          for (int i = 0; i < d; ++i) x[i] *= 3;
+          child[q] = static_cast<int32_t>(hf.slot_of(x));
+        }
+        if ((st = upload(*H, &D.child, child)) != MG_OK) return fail(st);
+      }
+    }
     if ((st = dalloc(*H, &D.partial, static_cast<size_t>(hl.n_bricks) * hl.B)) != MG_OK) return fail(st);
     if (!H->mixed && (st = dalloc(*H, &D.dinv, ns)) != MG_OK) return fail(st);
     if ((st = dalloc(*H, &D.counter, 1)) != MG_OK) return fail(st);
@@ -604,7 +640,8 @@ mg_status hier_create(const Grid* g, const mg_options& o, int priority, Hier** o
   *out = nullptr;
   if (o.coarsest_level < 1 || o.coarsest_level >= g->L || o.nu1 < 0 || o.nu2 < 0 || !(o.omega > 0.0) ||
       o.transfer < 0 || o.transfer > 1 || o.coarse < 0 || o.coarse > 1 || o.precision < 0 || o.precision > 3 || o.smoother < 0 || o.smoother > 1 ||
-      (o.smoother == MG_SMOOTH_BLOCK && (o.gs_sweeps < 1 || o.gs_sweeps > 64)) ||
+      (o.smoother == MG_SMOOTH_BLOCK && (o.gs_sweeps < 1 || o.gs_sweeps > 64)) || o.cycle < 0 || o.cycle > 1 ||
+      (o.cycle == MG_CYCLE_ADDITIVE && (o.precision != MG_PREC_FP64 || o.smoother != MG_SMOOTH_JACOBI)) ||
       (o.precision == MG_PREC_MIXED_BPA && !(o.eps_mf >= 0.0 && o.eps_mf < 1e300))) {
     set_error("mg_hier_create: invalid options");
     return MG_ERR_INVALID_ARG;
@@ -621,6 +658,10 @@ mg_status hier_create(const Grid* g, const mg_options& o, int priority, Hier** o
     if (o.coarsest_level >= g->L - 1) {
       set_error("mg_hier_create: the coarsest level must lie below the finest complete level");
       return MG_ERR_INVALID_ARG;
+    }
+    if (o.cycle != MG_CYCLE_V) {
+      set_error("mg_hier_create: adaptive grids run the composite V-cycle");
+      return MG_ERR_UNSUPPORTED;
     }
   }
   try {
@@ -645,6 +686,7 @@ size_t hier_footprint(const Grid& g, const mg_options& o) {
     bytes += nb * n3 * 4 + nb * d * 4 + hl.brick_rank.size() * 4 + 2 * ns + (hl.n_hanging > 0 ? ns * full * 12 : 0);
     bytes += 3 * ns * 8 + nb * hl.B * 8 + 4 + (mixed ? 0 : ns * 8);
     if (l < g.L) bytes += 2 * ns * 8;
+    if (o.cycle == MG_CYCLE_ADDITIVE) bytes += 2 * ns * 8 + (l < g.L ? ns * 4 : 0);
     if (l < top) bytes += (galerkin ? ns * n3 * 8 : 0) + (boxmg ? ns * n5 * 8 : 0);
     if (mixed) {
       bytes += 5 * ns * 4;
@@ -816,6 +858,8 @@ static void residual_norm(Hier& H, const T* u, const T* b, T* r, int slot, cudaS
   sweep<T>(H, H.L, kResidual, u, b, r, H.d_scal + slot, s);
 }
 
+static mg_status additive_reset(Hier& H, double* u, cudaStream_t s);
+
 static mg_status run_setup(Hier& H, const double* eps_in, cudaStream_t s, bool check_now = true) {
   const Grid& g = *H.g;
   const int d = H.dim;
@@ -925,6 +969,7 @@ static mg_status run_setup(Hier& H, const double* eps_in, cudaStream_t s, bool c
     }
     MG_CHECK(last_launch("setup: encode"));
   }
+  if (H.opt.cycle == MG_CYCLE_ADDITIVE) MG_CHECK(additive_reset(H, nullptr, s));
   if (!check_now) {  // the caller reads d_status after one synchronisation for many hierarchies
     H.ready = true;
     return MG_OK;
@@ -1055,6 +1100,104 @@ static mg_status solve_fp64(Hier& H, double* u, const double* b, double tol, int
   while (rel > tol && cycles < max_cycles) {
     MG_CHECK(graph_launch(H, H.g_cycle64, u, b, s, [&](cudaStream_t ss) {
       vcycle<double>(H, H.L, u, b, ss);
+      residual_norm<double>(H, u, b, F.r, 0, ss);
+      cudaMemcpyAsync(H.h_pin, H.d_scal, sizeof(double), cudaMemcpyDeviceToHost, ss);
+    }));
+    MG_TRY_CUDA(cudaStreamSynchronize(s));
+    ++cycles;
+    rel = std::sqrt(H.h_pin[0]) / r0;
+    if (st && st->history && st->history_len < st->history_capacity) st->history[st->history_len++] = rel;
+    if (!std::isfinite(rel)) {
+      set_error("mg_solve: non-finite residual");
+      if (st) st->cycles = cycles;
+      return MG_ERR_NONFINITE;
+    }
+    if (rel > 1e6) {
+      set_error("mg_solve: residual grew by more than 1e6 (diverged)");
+      if (st) st->cycles = cycles;
+      return MG_ERR_DIVERGED;
+    }
+  }
+  if (st) {
+    st->cycles = cycles;
+    st->outer_steps = cycles;
+    st->rel_residual = rel;
+  }
+  if (rel > tol) {
+    set_error("mg_solve: not converged within max_cycles");
+    return MG_ERR_NOT_CONVERGED;
+  }
+  return MG_OK;
+}
+
+// One traversal of the additive multigrid of Alg. 2 on level iterates u_l (u, b: the
+// finest level's), corrections d_l (D.ad) and surpluses uh_l (D.t).  Descent: d_l +=
+// P d_{l-1}, u_l += P d_{l-1}, uh_l = u_l - P u_{l-1}; ascent: r_l = b_l - A_l u_l (D.r),
+// rh_l = b_l - A_l uh_l (D.ar), d_l = omega D^-1 r_l, u_l += d_l, u_{l-1} = I u_l,
+// b_{l-1} = R rh_l.  The coarse b_l are rebuilt by the restriction every traversal.
+static void additive_traversal(Hier& H, double* u, const double* b, cudaStream_t s) {
+  auto U = [&](int l) { return l == H.L ? u : H.lv[l].u; };
+  auto Bv = [&](int l) { return l == H.L ? b : static_cast<const double*>(H.lv[l].b); };
+  for (int l = H.c; l <= H.L; ++l) {
+    DevLevel& D = H.lv[l];
+    const size_t bytes = static_cast<size_t>(D.d.n_slots) * sizeof(double);
+    if (l > H.c) {
+      DevLevel& C = H.lv[l - 1];
+      transfer<double>(H, l, false, C.ad, D.ad, s);
+      transfer<double>(H, l, false, C.ad, U(l), s);
+      cudaMemcpyAsync(D.t, U(l), bytes, cudaMemcpyDeviceToDevice, s);
+      k_negate<<<nblk(C.d.n_slots), kBlock, 0, s>>>(C.d.n_slots, C.u, C.ar);  // rh_{l-1} is formed later
+      transfer<double>(H, l, false, C.ar, D.t, s);
+    } else {
+      cudaMemcpyAsync(D.t, U(l), bytes, cudaMemcpyDeviceToDevice, s);
+    }
+  }
+  for (int l = H.L; l >= H.c; --l) {
+    DevLevel& D = H.lv[l];
+    sweep<double>(H, l, kResidual, U(l), Bv(l), D.r, nullptr, s);
+    sweep<double>(H, l, kResidual, D.t, Bv(l), D.ar, nullptr, s);
+    k_add_correct<<<nblk(D.d.n_slots), kBlock, 0, s>>>(D.d, D.dinv, D.r, D.ad, U(l));
+    if (l > H.c) {
+      DevLevel& C = H.lv[l - 1];
+      k_inject_level<<<nblk(C.d.n_slots), kBlock, 0, s>>>(C.d, C.child, U(l), C.u);
+      transfer<double>(H, l, true, D.ar, C.b, s);
+    }
+  }
+}
+
+// the level iterates and corrections of the additive cycle start from zero
+static mg_status additive_reset(Hier& H, double* u, cudaStream_t s) {
+  for (int l = H.c; l <= H.L; ++l) {
+    DevLevel& D = H.lv[l];
+    const size_t bytes = static_cast<size_t>(D.d.n_slots) * sizeof(double);
+    MG_TRY_CUDA(cudaMemsetAsync(D.ad, 0, bytes, s));
+    if (l < H.L) MG_TRY_CUDA(cudaMemsetAsync(D.u, 0, bytes, s));
+  }
+  if (u) MG_TRY_CUDA(cudaMemsetAsync(u, 0, H.lv[H.L].d.n_slots * sizeof(double), s));
+  return MG_OK;
+}
+
+static mg_status solve_additive(Hier& H, double* u, const double* b, double tol, int max_cycles,
+                                mg_solve_stats* st, cudaStream_t s) {
+  DevLevel& F = H.lv[H.L];
+  MG_CHECK(additive_reset(H, u, s));
+  residual_norm<double>(H, u, b, F.r, 0, s);
+  MG_TRY_CUDA(cudaMemcpyAsync(H.h_pin, H.d_scal, sizeof(double), cudaMemcpyDeviceToHost, s));
+  MG_TRY_CUDA(cudaStreamSynchronize(s));
+  const double r0 = std::sqrt(H.h_pin[0]);
+  if (st) {
+    st->r0_norm = r0;
+    st->history_len = 0;
+  }
+  if (!std::isfinite(r0)) {
+    set_error("mg_solve: non-finite initial residual");
+    return MG_ERR_NONFINITE;
+  }
+  double rel = r0 > 0 ? 1.0 : 0.0;
+  int cycles = 0;
+  while (rel > tol && cycles < max_cycles) {
+    MG_CHECK(graph_launch(H, H.g_add, u, b, s, [&](cudaStream_t ss) {
+      additive_traversal(H, u, b, ss);
       residual_norm<double>(H, u, b, F.r, 0, ss);
       cudaMemcpyAsync(H.h_pin, H.d_scal, sizeof(double), cudaMemcpyDeviceToHost, ss);
     }));
@@ -1565,6 +1708,7 @@ void mg_default_options(mg_options* o) {
   o->eps_mf = 1e-4;
   o->smoother = MG_SMOOTH_JACOBI;
   o->gs_sweeps = 1;
+  o->cycle = MG_CYCLE_V;
 }
 
 mg_status mg_hier_create(const mg_grid* grid, const mg_options* opt, mg_hier** out) {
@@ -1757,6 +1901,7 @@ mg_status mg_autotune(mg_hier* h, int32_t* chosen, void* stream) {
   H->g_comp64.reset();
   H->g_comp_outer.reset();
   H->g_comp_inner.reset();
+  H->g_add.reset();
   return MG_OK;
 }
 
@@ -1773,6 +1918,8 @@ mg_status mg_vcycle(mg_hier* h, double* u, const double* b, void* stream) {
     fill_hanging<double>(*H, v.ut, v.uL, s);
     composite_cycle<double>(*H, v.uL, v.bL, v.ut, v.bt, s);
     inject<double>(*H, v.uL, v.ut, s);
+  } else if (H->opt.cycle == MG_CYCLE_ADDITIVE) {
+    additive_traversal(*H, u, b, s);  // on the stored coarse iterates and corrections
   } else {
     vcycle<double>(*H, H->L, u, b, s);
   }
@@ -1790,9 +1937,11 @@ mg_status mg_solve(mg_hier* h, double* u, const double* b, double rel_tol, int m
   cudaStream_t s = pick(*H, stream);
   const auto t0 = std::chrono::steady_clock::now();
   const bool persistent = H->opt.persistent && !H->adaptive && H->fmt != 4 && H->opt.smoother == MG_SMOOTH_JACOBI &&
+                          H->opt.cycle == MG_CYCLE_V &&
                           H->n_c <= 64 && H->L < kMaxLevels;
   const mg_status st = H->adaptive ? (H->mixed ? solve_comp_mixed(*H, u, b, rel_tol, max_cycles, stats, s)
                                                  : solve_comp_fp64(*H, u, b, rel_tol, max_cycles, stats, s))
+                       : H->opt.cycle == MG_CYCLE_ADDITIVE ? solve_additive(*H, u, b, rel_tol, max_cycles, stats, s)
                        : persistent ? solve_persistent(*H, u, b, rel_tol, max_cycles, stats, s)
                        : H->mixed   ? solve_mixed(*H, u, b, rel_tol, max_cycles, stats, s)
                                     : solve_fp64(*H, u, b, rel_tol, max_cycles, stats, s);
