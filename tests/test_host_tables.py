@@ -111,3 +111,34 @@ def test_adaptive_hierarchy_shape_is_checked_before_any_device_work(mg):
     with pytest.raises(mg.MgError) as e:
         mg.Hierarchy(g2, coarsest_level=2)  # the coarsest level must lie below level L-1
     assert e.value.status == 1  # MG_ERR_INVALID_ARG
+
+
+def test_option_validation_needs_no_gpu(mg):
+    # mg_hier_create checks its options before touching the device
+    g = mg.Grid(2, 3)
+    bad = [dict(smoother="block", gs_sweeps=0), dict(smoother="block", gs_sweeps=65), dict(smoother=2),
+           dict(cycle="additive", precision="mixed_bf16"), dict(cycle="additive", smoother="block"),
+           dict(cycle=2), dict(precision=4), dict(precision="mixed_bpa", eps_mf=-1.0),
+           dict(precision="mixed_bpa", eps_mf=float("nan")), dict(coarsest_level=3), dict(omega=0.0)]
+    for kw in bad:
+        with pytest.raises(mg.MgError):
+            mg.Hierarchy(g, **kw)
+    ga = mg.Grid(2, 4, {3: syn.sphere_shell_mask(3, 2, radius=0.3, centre=(0.5, 0.5))})
+    with pytest.raises(mg.MgError):
+        mg.Hierarchy(ga, cycle="additive")
+
+
+def test_footprints_of_the_storage_modes(mg):
+    # device bytes planned per mode: the bpa streams are held at their worst case (8 bytes
+    # per entry plus an 8-byte record per slot and operator, against 2 bytes + a 4-byte
+    # scale for BF16); the additive cycle adds two vectors per level and injection maps
+    g = mg.Grid(2, 5)
+    base = mg.hier_footprint(g)
+    bf16 = mg.hier_footprint(g, precision="mixed_bf16")
+    bpa = mg.hier_footprint(g, precision="mixed_bpa")
+    coarse = sum(g.info(lv).n_slots for lv in range(1, 5))
+    assert bpa - bf16 == coarse * ((9 + 25) * 6 + 2 * 4)
+    add = mg.hier_footprint(g, cycle="additive")
+    allv = sum(g.info(lv).n_slots for lv in range(1, 6))
+    assert add - base == allv * 16 + coarse * 4
+    assert mg.hier_footprint(g, smoother="block") == base
