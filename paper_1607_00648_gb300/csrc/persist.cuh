@@ -221,7 +221,7 @@ __device__ void cycle_rest(const PSolve<T>& p, unsigned char* smem) {
 }
 
 // FP64 solve from u = 0 (the caller zeroes u): V-cycles until the relative residual
-// drops below tol (Sect. 4.1; convergence test of the survey's reading R9).
+// drops below tol (Sect. 4.1; ||r||_2 / ||r_0||_2 over the DoFs, u_0 = 0).
 template <int DIM, int AMC, int PM>
 __global__ void __launch_bounds__(kBlock) k_persist_fp64(const PSolve<double>* __restrict__ pp) {
   namespace cg = cooperative_groups;
