@@ -6,6 +6,12 @@ over the 2^d cells adjacent to its vertex (eq. "03_solver:stencils").  Here the
 element matrix is the plain definition K_ij = int_cell grad phi_i . grad phi_j,
 integrated by tensor Gauss-Legendre quadrature (exact for these polynomials),
 and level operators are assembled cell by cell into scipy sparse matrices.
+
+eps is a scalar per cell, or a diagonal tensor (eps_1, ..., eps_d) per cell (eq. (1)
+allows a diagonal diffusion tensor; the paper's `checkerboard` benchmark sets eps_i
+by the coordinate x_i): a coordinate array with a trailing axis of length d.  The
+tensor case uses the directional element matrices K^(i)_ab = int d_i phi_a d_i phi_b,
+whose sum is K.
 """
 from __future__ import annotations
 
@@ -23,11 +29,17 @@ def element_matrix(dim: int, h: float) -> np.ndarray:
     phi_e(xi) = prod_i (xi_i if e_i else 1 - xi_i) on the reference cube; the
     chain rule gives grad_x = grad_xi / h and dx = h^d dxi, so K scales as h^(d-2).
     """
+    return sum(directional_element_matrices(dim, h))
+
+
+def directional_element_matrices(dim: int, h: float) -> list[np.ndarray]:
+    """[K^(i)] with K^(i)_ab = int over a cube of side h of d_i phi_a d_i phi_b (same
+    quadrature and scaling as ``element_matrix``)."""
     gp, gw = np.polynomial.legendre.leggauss(2)
     gp = 0.5 * (gp + 1.0)
     gw = 0.5 * gw
     cs = corners(dim)
-    K = np.zeros((len(cs), len(cs)))
+    K = [np.zeros((len(cs), len(cs))) for _ in range(dim)]
     for q in itertools.product(range(2), repeat=dim):
         xi = np.array([gp[i] for i in q])
         wq = np.prod([gw[i] for i in q])
@@ -39,8 +51,9 @@ def element_matrix(dim: int, h: float) -> np.ndarray:
                     if j != i:
                         g *= xi[j] if e[j] else 1.0 - xi[j]
                 grads[a, i] = g
-        K += wq * grads @ grads.T
-    return K * h ** (dim - 2)
+        for i in range(dim):
+            K[i] += wq * np.outer(grads[:, i], grads[:, i])
+    return [k * h ** (dim - 2) for k in K]
 
 
 def coarse_eps(tree: Spacetree, leaf_eps: dict[int, np.ndarray]) -> dict[int, np.ndarray]:
@@ -51,19 +64,21 @@ def coarse_eps(tree: Spacetree, leaf_eps: dict[int, np.ndarray]) -> dict[int, np
     rediscretisation coefficient open, Sect. 4.3 / Sect. 5).
     """
     d = tree.dim
+    tail = next(iter(leaf_eps.values())).shape[d:]  # () scalar, (d,) diagonal tensor
+    ext = (slice(None),) * d + (None,) * len(tail)
     out: dict[int, np.ndarray] = {}
     for lv in range(tree.max_level, -1, -1):
         n = 3**lv
-        e = np.zeros((n,) * d)
+        e = np.zeros((n,) * d + tail)
         if lv in leaf_eps:
-            e = np.where(tree.cells[lv] & ~tree.refined[lv], leaf_eps[lv], 0.0)
+            e = np.where((tree.cells[lv] & ~tree.refined[lv])[ext], leaf_eps[lv], 0.0)
         if lv < tree.max_level:
             child = out[lv + 1]
             shape = []
             for _ in range(d):
                 shape += [n, 3]
-            mean = child.reshape(shape).mean(axis=tuple(range(1, 2 * d, 2)))
-            e = np.where(tree.refined[lv], mean, e)
+            mean = child.reshape(shape + list(tail)).mean(axis=tuple(range(1, 2 * d, 2)))
+            e = np.where(tree.refined[lv][ext], mean, e)
         out[lv] = e
     return out
 
@@ -76,7 +91,8 @@ def assemble(tree: Spacetree, level: int, eps_cells: np.ndarray) -> sp.csr_matri
     """
     lv = tree.levels[level]
     d = tree.dim
-    K = element_matrix(d, lv.h)
+    tensor = eps_cells.ndim == d + 1
+    K = directional_element_matrices(d, lv.h) if tensor else element_matrix(d, lv.h)
     rows, cols, vals = [], [], []
     cell_slots = np.nonzero((lv.cflags & CELL_EXISTS) != 0)[0]
     cv = lv.cell_vertices[cell_slots]
@@ -86,7 +102,10 @@ def assemble(tree: Spacetree, level: int, eps_cells: np.ndarray) -> sp.csr_matri
             ok = (cv[:, a] >= 0) & (cv[:, b] >= 0)
             rows.append(cv[ok, a])
             cols.append(cv[ok, b])
-            vals.append(ec[ok] * K[a, b])
+            if tensor:
+                vals.append(sum(ec[ok, i] * K[i][a, b] for i in range(d)))
+            else:
+                vals.append(ec[ok] * K[a, b])
     A = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
                       shape=(lv.n_slots, lv.n_slots))
     return A.tocsr()

@@ -77,6 +77,20 @@ def jump_eps(level: int, dim: int, low: float = 1.0, high: float = 0.1) -> np.nd
     return np.broadcast_to(col.reshape(shape), (n,) * dim).astype(np.float64).copy()
 
 
+def axis_checkerboard_eps(level: int, dim: int, low: float = 1.0, high: float = 0.1) -> np.ndarray:
+    """The paper's `checkerboard` coefficient, a diagonal tensor per cell: eps_i = `low`
+    where the cell centre has x_i < 0.5, else `high`.  Shape (3^level,)*dim + (dim,)."""
+    n = 3**level
+    xc = (np.arange(n) + 0.5) / n
+    col = np.where(xc < 0.5, low, high)
+    out = np.empty((n,) * dim + (dim,))
+    for i in range(dim):
+        shape = [1] * dim
+        shape[i] = n
+        out[..., i] = np.broadcast_to(col.reshape(shape), (n,) * dim)
+    return out
+
+
 def unit_load(level: int, dim: int) -> np.ndarray:
     """Lumped load b_v = h^d f with f = 1 (the paper's `jump` and `checkerboard` right-hand side)."""
     n = 3**level + 1
