@@ -205,6 +205,64 @@ class Hierarchy:
                 u[lv - 1] = self.inject(lv, u[lv])
                 bb[lv - 1] = np.where(self.ops[lv - 1].dof, self.restrict(lv, rh), 0.0)
 
+    def c_points(self, lv: int) -> np.ndarray:
+        """Slots of level lv that coincide with a level lv-1 vertex (every coordinate a
+        multiple of 3): the c-points of Sect. 4.2 / Alg. 3."""
+        c = self.tree.levels[lv].coords
+        return (c[:, 0] >= 0) & np.all(c % 3 == 0, axis=1)
+
+    def bpx_traversal(self, u: dict, d: dict, i: dict, b: np.ndarray) -> None:
+        """One grid traversal of the BPX variant of Alg. 3, in place on u[l], d[l] and the
+        injected skipped updates i[l].
+
+        Reading of the paper: as Alg. 2, except that (a) on every level above the
+        coarsest the c-points skip their own Jacobi update (u_l += d_l off the c-points
+        only); their corrections are injected to the coarser level, i_{l-1} = I d_l, and
+        then zeroed (d_l = 0 at c-points); (b) the descent applies P d_{l-1} at c-points
+        and P d_{l-1} - P i_{l-1} elsewhere, to d_l and u_l; (c) the coarse iterates are
+        not overwritten by injection (the printed surplus line lacks its u, read as
+        uh_l = u_l - P u_{l-1}).  The coarsest level has no c-points."""
+        L, c = self.L, self.coarsest
+        uh, bb = {}, {}
+        for lv in range(c, L + 1):
+            dof = self.ops[lv].dof
+            if lv > c:
+                cp = self.c_points(lv)
+                corr = (np.where(dof, self.prolong(lv, d[lv - 1]), 0.0)
+                        - np.where(dof & ~cp, self.prolong(lv, i[lv - 1]), 0.0))
+                d[lv] = d[lv] + corr
+                u[lv] = u[lv] + corr
+                uh[lv] = u[lv] - np.where(dof, self.prolong(lv, u[lv - 1]), 0.0)
+            else:
+                uh[lv] = u[lv].copy()
+            bb[lv] = b if lv == L else np.zeros_like(u[lv])
+        for lv in range(L, c - 1, -1):
+            o = self.ops[lv]
+            r = self.residual(lv, u[lv], bb[lv])
+            rh = self.residual(lv, uh[lv], bb[lv])
+            d[lv] = np.where(o.dof, self.omega * r / o.diag, 0.0)
+            cp = self.c_points(lv) if lv > c else np.zeros_like(o.dof)
+            u[lv] = u[lv] + np.where(cp, 0.0, d[lv])
+            if lv > c:
+                bb[lv - 1] = np.where(self.ops[lv - 1].dof, self.restrict(lv, rh), 0.0)
+                i[lv - 1] = self.inject(lv, d[lv])
+                d[lv] = np.where(cp, 0.0, d[lv])
+
+    def bpx_solve(self, b: np.ndarray, rel_tol: float = 1e-10, max_cycles: int = 100):
+        """BPX traversals from u = 0 until ||b - A u_L||_2 / ||b||_2 <= rel_tol."""
+        L = self.L
+        u = {lv: np.zeros(self.ops[lv].dof.size) for lv in range(self.coarsest, L + 1)}
+        d = {lv: np.zeros_like(u[lv]) for lv in u}
+        i = {lv: np.zeros_like(u[lv]) for lv in u}
+        r0 = np.linalg.norm(self.residual(L, u[L], b))
+        hist = [r0]
+        for _ in range(max_cycles):
+            if hist[-1] <= rel_tol * r0:
+                break
+            self.bpx_traversal(u, d, i, b)
+            hist.append(np.linalg.norm(self.residual(L, u[L], b)))
+        return u[L], np.array(hist)
+
     def additive_solve(self, b: np.ndarray, rel_tol: float = 1e-10, max_cycles: int = 100):
         """Additive traversals from u = 0 until ||b - A u_L||_2 / ||b||_2 <= rel_tol;
         returns (u_L, history of relative residuals)."""
