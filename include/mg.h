@@ -209,8 +209,10 @@ mg_status mg_setup(mg_hier* h, const double* eps, void* stream);
 
 /* ---------------------------------------------------------------- A3-A7 steps (FP64) */
 
-/* nu damped Jacobi sweeps u <- u + omega diag(A)^-1 (b - A u) on level (Alg. 1),
- * in place on u (device, n_slots); b device, n_slots. */
+/* nu smoothing steps of the hierarchy's smoother on level, in place on u (device,
+ * n_slots); b device, n_slots.  MG_SMOOTH_JACOBI: damped Jacobi sweeps
+ * u <- u + omega diag(A)^-1 (b - A u) (Alg. 1); MG_SMOOTH_BLOCK: block Jacobi steps
+ * (Sect. 4.2, see mg_smoother). */
 mg_status mg_smooth(mg_hier* h, int level, double* u, const double* b, int nu, void* stream);
 
 /* r = b - A u on level (device vectors).  norm2_host (nullable): receives
@@ -279,7 +281,10 @@ mg_status mg_autotune(mg_hier* h, int32_t* chosen, void* stream);
  * unrefined level-t DoFs; b is read there only.  On return the level-L hanging
  * entries hold the interpolant of level t and the refined level-t entries the
  * injected level-L value (Sect. 3, rules 1 and 2); on entry the hanging entries
- * are recomputed and every other non-unknown entry must be zero. */
+ * are recomputed and every other non-unknown entry must be zero.
+ * Additive hierarchy (MG_CYCLE_ADDITIVE): one traversal of Alg. 2 instead, on the
+ * coarse iterates and corrections the hierarchy keeps between calls (zeroed by
+ * mg_setup and at the start of mg_solve). */
 mg_status mg_vcycle(mg_hier* h, double* u, const double* b, void* stream);
 
 typedef struct mg_solve_stats {
