@@ -299,9 +299,12 @@ typedef struct mg_solve_stats {
 } mg_solve_stats;
 
 /* Solve A u = b from u = 0 on the finest level until ||r||/||r0|| <= rel_tol
- * (Euclidean over DoFs) or max_cycles.  FP64: V-cycles.  Mixed: FP64 residual and
- * update (iterative refinement) around inner_cycles FP32 V-cycles that read the
- * BF16/FP16 deltas.  u, b device; stats host, nullable.  Synchronises stream.
+ * (Euclidean over DoFs) or max_cycles.  FP64: V-cycles (additive hierarchies:
+ * traversals of Alg. 2, counted as cycles).  Mixed: FP64 residual and update
+ * (iterative refinement) around inner_cycles FP32 V-cycles that read the
+ * BF16/FP16 codes or the bpa streams of the deltas.  The block smoother, where
+ * chosen, replaces the Jacobi sweeps of every cycle.  u, b device; stats host,
+ * nullable.  Synchronises stream.
  * Returns MG_ERR_NOT_CONVERGED / MG_ERR_DIVERGED / MG_ERR_NONFINITE with u holding
  * the last iterate.  Adaptive hierarchy: composite cycles on level-concatenated u
  * and b (layout as in mg_vcycle); the residual is the composite one (level-L DoFs
