@@ -700,7 +700,7 @@ def run_sweeps(args):
 
 
 def run_batched(args, n_problems=512, seed=3):
-    """Task config 4: n independent 2D problems, edge 3^m cells with m ~ U{3,4,5,6},
+    """Batched workload: n independent 2D problems, edge 3^m cells with m ~ U{3,4,5,6},
     log-normal eps (sigma 2, correlation length 0.1, seed 1000+i), f ~ U[-1,1]
     (seed 2000+i), solved to 1e-10 together (mg_batch_solve): mixed vs FP64."""
     import torch
@@ -763,7 +763,7 @@ def run_batched(args, n_problems=512, seed=3):
 
 
 def run_serve(args, seed=4):
-    """Task config 5: Poisson arrivals (mean 200 req/s) of 3D solves with edges
+    """Served workload: Poisson arrivals (mean 200 req/s) of 3D solves with edges
     {27, 81, 243} cells (weights 6:3:1), log-normal eps (sigma 1.5, correlation length
     0.1), f ~ U[-1,1], tolerance 1e-8 each, mixed precision, served by mg_server with
     an HBM budget; reports solves/s and p50 / p99 latency from submission."""
@@ -916,8 +916,8 @@ def main():
                     help="multigrid cycle of the timed FP64 solve (additive: Alg. 2; FP64 only)")
     ap.add_argument("--codecs", action="store_true",
                     help="mixed solves with BF16 deltas against the bpa codec at eps_mf 1e-2 / 1e-4 / 1e-8")
-    ap.add_argument("--batched", action="store_true", help="task config 4: batched mixed vs FP64 solves")
-    ap.add_argument("--serve", action="store_true", help="task config 5: served 3D requests, p50 / p99 latency")
+    ap.add_argument("--batched", action="store_true", help="512 uneven 2D problems solved as one batch: mixed vs FP64")
+    ap.add_argument("--serve", action="store_true", help="a Poisson stream of 3D solve requests through mg_server: p50 / p99 latency")
     ap.add_argument("--serve-requests", type=int, default=300)
     ap.add_argument("--serve-budget-gb", type=float, default=64.0)
     ap.add_argument("--batch-size", type=int, default=0)
