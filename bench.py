@@ -68,17 +68,21 @@ ADAPTIVE = {
                              "BF16 deltas + FP32 cycles + FP64 refinement to 1e-10"),
 }
 
-FP64_PEAK_TFLOPS = 1.25  # nominal dense FP64 of a GB300 (2 FMA / clock / SM at ~2.07 GHz)
-# FP64 flops per DoF of the finest 2D in-situ Jacobi sweep: 4 pair sums of cell
-# coefficients, 2 x (1 mul + 3 fma) for the edge and corner neighbour sums, 1 mul +
-# 1 fma for the off-diagonal part, b - off, (1 - omega) u and the final fma (an fma
-# counts 2 flops): 4 + 14 + 3 + 1 + 1 + 2
-FLOPS_PER_DOF_SWEEP_2D = 25
-BYTES_PER_DOF_SWEEP_FP64 = 40  # u, b, eps, omega/diag read + u' written, 8 B each
-# DRAM bytes per DoF of that sweep from ncu (dram__bytes_read.sum + dram__bytes_write.sum)
-# on the 2D level-7 case (python bench.py --sweep-level 7 --sweep-dim 2 --sweep-prec fp64),
-# whose vectors exceed L2; the level-6 launch is scaled by its DoFs
-TRAFFIC_PER_DOF_SWEEP_FP64_2D = 38.2
+# FP64 flops per DoF of the finest 2D in-situ Jacobi sweep (k_sweep2f): two pair sums of
+# cell coefficients (the other two are shared with the neighbouring column and the row
+# below), the corner products (1 mul + 3 fma), their doubling, the edge products
+# (4 fma), b - off (1 fma), (1 - omega) u and the update (1 mul + 1 fma); an fma counts
+# 2 flops.  14 FP64 instructions issue these 23 flops.
+FLOPS_PER_DOF_SWEEP_2D = 23
+FP64_INSTR_PER_DOF_SWEEP_2D = 14
+# algorithmic bytes of a finest Jacobi sweep: u, b, eps read and u' written, 8 B each
+# (the stored omega / diag(A) adds 8 B read per DoF in this implementation)
+BYTES_PER_DOF_SWEEP_FP64 = 32
+BYTES_PER_DOF_SWEEP_FP64_IMPL = 40
+# DRAM bytes per DoF of k_sweep2f from ncu (dram__bytes_read.sum + dram__bytes_write.sum)
+# on the 2D level-7 case (python bench.py --sweep-level 7 --sweep-dim 2 --sweep-prec
+# fp64), whose vectors exceed L2
+TRAFFIC_PER_DOF_SWEEP_FP64_2D = 38.40
 BYTES_PER_DOF_SWEEP_FP32 = 16
 
 
@@ -106,6 +110,27 @@ def peaks():
             j = json.load(f)
         return float(j.get("hbm_gbs", 6800.0)), "measured"
     return 6800.0, "fallback"
+
+
+def fp64_peak_tflops(mg, torch, reps=5):
+    """FP64 fma rate of this GPU, measured: mg_probe_fp64_fma (8 independent fma chains
+    per thread, 16 resident CTAs of 256 threads per SM, four waves) timed with CUDA
+    events on the current stream; the best of `reps` launches after two warm-ups."""
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    n_ctas = sms * 8 * 4
+    sink = torch.zeros(n_ctas, dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        mg.probe_fp64_fma(n_ctas, 2048, sink)
+    best = None
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fl = mg.probe_fp64_fma(n_ctas, 2048, sink)
+        e1.record()
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1e3
+        best = t if best is None or t < best else best
+    return fl / best / 1e12
 
 
 class Clocks:
@@ -507,23 +532,34 @@ def run_ours(args):
     sweep_s = e0.elapsed_time(e1) / 1e3 / (2 * reps)
     Hmx.setup(eps_dev)
     hbm_peak, peak_src = peaks()
+    with Clocks(torch.cuda.current_device()) as clk_peak:
+        fp64_peak = fp64_peak_tflops(mg, torch)
     flops = FLOPS_PER_DOF_SWEEP_2D * n_dofs
-    roofline = {"bound": "alu", "kernel": "k_sweep<2,double,0,Jacobi> (finest FP64 Jacobi sweep)",
-                "achieved": flops / sweep_s / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": flops / sweep_s / 1e12 / FP64_PEAK_TFLOPS,
-                "peak_source": "nominal FP64 of the recipe (no measured FP64 peak)",
-                "flops_per_dof": FLOPS_PER_DOF_SWEEP_2D, "launch_us": sweep_s * 1e6,
+    achieved = flops / sweep_s / 1e12
+    # the binding roofline of the sweep, in DoF/s: min(HBM at the algorithmic bytes,
+    # FP64 units at the kernel's flops); the FP64 one binds on GB300
+    dofs_hbm = hbm_peak * 1e9 / BYTES_PER_DOF_SWEEP_FP64
+    dofs_fp64 = fp64_peak * 1e12 / FLOPS_PER_DOF_SWEEP_2D
+    traffic = TRAFFIC_PER_DOF_SWEEP_FP64_2D * n_dofs if TRAFFIC_PER_DOF_SWEEP_FP64_2D else None
+    roofline = {"bound": "alu", "kernel": "k_sweep2f<0,Jacobi> (finest FP64 Jacobi sweep, 2D column kernel)",
+                "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved / fp64_peak,
+                "peak_source": "measured: FP64 fma-chain probe (mg_probe_fp64_fma), CUDA events, this run",
+                "peak_clocks": clk_peak.summary(),
+                "flops_per_dof": FLOPS_PER_DOF_SWEEP_2D, "fp64_instr_per_dof": FP64_INSTR_PER_DOF_SWEEP_2D,
+                "fp64_issue_frac": FP64_INSTR_PER_DOF_SWEEP_2D * n_dofs / sweep_s / (fp64_peak * 1e12 / 2),
+                "dofs_per_launch": n_dofs, "launch_us": sweep_s * 1e6,
+                "l2": "the level-6 vectors (~21 MB) are L2-resident; the kernel is bound by the FP64 units",
+                "binding_roofline": {"hbm_dofs_per_s": dofs_hbm, "fp64_dofs_per_s": dofs_fp64,
+                                     "bytes_per_dof": BYTES_PER_DOF_SWEEP_FP64,
+                                     "achieved_dofs_per_s": n_dofs / sweep_s,
+                                     "frac": n_dofs / sweep_s / min(dofs_hbm, dofs_fp64)},
                 "hbm_equivalent": {"achieved": BYTES_PER_DOF_SWEEP_FP64 * n_dofs / sweep_s / 1e9,
                                    "peak": hbm_peak, "unit": "GB/s",
                                    "frac": BYTES_PER_DOF_SWEEP_FP64 * n_dofs / sweep_s / 1e9 / hbm_peak,
                                    "peak_source": peak_src},
-                # the kernel changed after its DRAM counters were taken (dependent-launch entry,
-                # the block-smoother flag), so no current traffic figure exists; the last
-                # capture is kept beside it for reference
-                "traffic": None,
-                "traffic_last_capture": TRAFFIC_PER_DOF_SWEEP_FP64_2D * n_dofs,
-                "traffic_note": "null: kernel edited since the ncu capture; last capture = DRAM bytes/DoF "
-                                "of the level-7 case x DoFs"}
+                "traffic": traffic,
+                "traffic_note": "ncu DRAM bytes per DoF of the level-7 case (vectors beyond L2) x DoFs"
+                if traffic else "null: no ncu capture of the current kernel yet"}
 
     # end to end through the public API with host buffers
     eps_h = torch.from_numpy(eps_cat).pin_memory()
@@ -696,6 +732,12 @@ def run_sweeps(args):
         t = e0.elapsed_time(e1) / 1e3 / (2 * reps)
         out[name] = {"launch_us": t * 1e6, "GB/s": bpd * n_dofs / t / 1e9, "hbm_frac": bpd * n_dofs / t / 1e9 / hbm,
                      "peak_source": src, "Gdof/s": n_dofs / t / 1e9}
+        if name == "fp64" and d == 2:
+            out[name]["TFLOP/s"] = FLOPS_PER_DOF_SWEEP_2D * n_dofs / t / 1e12
+    if args.sweep_prec != "fp32":
+        out["fp64_peak_tflops"] = fp64_peak_tflops(mg, torch)
+        if "TFLOP/s" in out.get("fp64", {}):
+            out["fp64"]["fp64_frac"] = out["fp64"]["TFLOP/s"] / out["fp64_peak_tflops"]
     print(json.dumps(out))
 
 

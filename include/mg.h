@@ -148,12 +148,17 @@ typedef enum mg_smoother {
 
 typedef enum mg_cycle {
   MG_CYCLE_V = 0,        /* multiplicative V(nu1, nu2) cycles (Alg. 1) */
-  MG_CYCLE_ADDITIVE = 1  /* additive multigrid (Alg. 2): per traversal, the coarse corrections of the
+  MG_CYCLE_ADDITIVE = 1, /* additive multigrid (Alg. 2): per traversal, the coarse corrections of the
                             previous traversal prolongated down (d_l += P d_{l-1}, u_l += P d_{l-1},
                             surplus uh_l = u_l - P u_{l-1}), then fine to coarse r_l = b_l - A_l u_l,
                             rh_l = b_l - A_l uh_l, d_l = omega D_l^-1 r_l, u_l += d_l, u_{l-1} = I u_l,
                             b_{l-1} = R rh_l; every level smoothed, none solved.  FP64 uniform
                             hierarchies, single problems only; mg_solve stops on ||b - A u||_2 */
+  MG_CYCLE_BPX = 2       /* BPX (Alg. 3): the additive traversal, except that above the coarsest level
+                            the c-points (every coordinate a multiple of 3) skip their own update, which
+                            is injected to the coarser level (i_{l-1} = I d_l) and zeroed; the descent
+                            applies P d_{l-1} at c-points and P d_{l-1} - P i_{l-1} elsewhere; the coarse
+                            iterates are not overwritten by injection.  Same restrictions as additive */
 } mg_cycle;
 
 typedef struct mg_options {
@@ -390,15 +395,34 @@ mg_status mg_get_stencils(mg_hier* h, int level, double* st, void* stream);
  * offsets in [-2,2]^d lexicographic). */
 mg_status mg_get_deltas(mg_hier* h, int level, double* a_hat, double* p_hat, void* stream);
 
-/* Mixed-path codes and scales of a coarse level (device, nullable, offset-major). */
+/* Mixed-path codes and scales of a coarse level (device, nullable, offset-major).
+ * a_scale carries the promotion flag of A_hat as its sign bit (see mg_encode_deltas_promote). */
 mg_status mg_get_codes(mg_hier* h, int level, uint16_t* a_codes, float* a_scale, uint16_t* p_codes,
                        float* p_scale, void* stream);
+
+/* Low halves of the A_hat codes of a coarse level of a BF16/FP16 hierarchy (device,
+ * n_slots*3^d, offset-major): non-zero only on promoted vertices, whose FP32 codes are
+ * (a_codes << 16 | a_lo).  MG_ERR_INVALID_ARG on FP64 / bpa hierarchies and the finest level. */
+mg_status mg_get_code_lo(mg_hier* h, int level, uint16_t* a_lo, void* stream);
 
 /* Standalone delta encoder (A10): for n rows of k FP64 entries (device, row-major
  * delta[i*k + j]) write scale[i] = fl32(max_j |delta|) and codes = RNE to
  * fmt (1 = BF16, 2 = FP16) of delta / scale formed in FP64 (device outputs). */
 mg_status mg_encode_deltas(int64_t n, int k, const double* delta, int fmt, uint16_t* codes, float* scale,
                            void* stream);
+
+/* The same encoder with per-row promotion (A10; the dtype counterpart of the paper's
+ * per-vertex storage choice against eps_mf, Sect. 5): reconstructing A = A_redisc + A_hat
+ * cancels where the delta is as large as the operator, so a row whose worst 16-bit
+ * rounding, h s (h = 2^-9 for BF16, 2^-12 for FP16, s = fl32(max_j |delta|)), exceeds
+ * 2^-8 |diag[i]| (diag: the row's reconstructed diagonal A_vv, device, n FP64) is stored
+ * as the FP32 bit pattern of fl32(delta / s) (RNE of the FP64 quotient): high half in
+ * codes, low half in lo, and scale[i] = -s (the sign bit is the flag).  Other rows:
+ * codes as mg_encode_deltas, lo = 0, scale[i] = +s.  Decoding: promoted rows
+ * fl32(float(codes << 16 | lo) * s), others fl32(value16(codes) * s).
+ * All buffers device, row-major n x k (scale, diag: n). */
+mg_status mg_encode_deltas_promote(int64_t n, int k, const double* delta, const double* diag, int fmt,
+                                   uint16_t* codes, uint16_t* lo, float* scale, void* stream);
 
 /* The bpa byte codec of Sect. 5 on caller buffers (NEXT row: the paper's delta storage).
  * Each of n rows of k FP64 entries (device, row-major x[i*k + j]) is one operator: it is
@@ -431,6 +455,17 @@ mg_status mg_get_bpa(mg_hier* h, int level, uint64_t* a_rec, uint8_t* a_stream, 
                      uint64_t* a_bytes, uint64_t* p_bytes, void* stream);
 
 void mg_destroy_hier(mg_hier* h);
+
+/* ---------------------------------------------------------------- measurement */
+
+/* FP64 fma-rate probe (the paper has no counterpart: it measures the denominator of
+ * the FP64 roofline that bounds the sweeps on this GPU).  Launches n_ctas CTAs of 256
+ * threads; every thread runs 8 independent chains of iters dependent FP64 fmas.  Time
+ * it with events on `stream`; *flops (host) receives the fma flops of the launch
+ * (2 per fma).  sink: device array of n_ctas doubles (never written for these inputs;
+ * it keeps the chains from being optimised away).  n_ctas in 1..2^24, iters >= 1,
+ * else MG_ERR_INVALID_ARG.  Enqueued only; no synchronisation. */
+mg_status mg_probe_fp64_fma(int64_t n_ctas, int32_t iters, double* sink, int64_t* flops, void* stream);
 
 const char* mg_last_error(void);
 const char* mg_version(void);

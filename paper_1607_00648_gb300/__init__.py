@@ -14,13 +14,13 @@ from . import _lib
 from ._lib import MgError, Options, SolveStats, check, load
 
 __all__ = ["Batch", "Server", "Grid", "Hierarchy", "MgError", "bpa_decode", "bpa_encode", "default_options",
-           "encode_deltas", "load"]
+           "encode_deltas", "encode_deltas_promote", "load", "probe_fp64_fma"]
 
 TRANSFER = {"dlinear": 0, "boxmg": 1}
 COARSE = {"redisc": 0, "galerkin": 1}
 PRECISION = {"fp64": 0, "mixed_bf16": 1, "mixed_fp16": 2, "mixed_bpa": 3}
 SMOOTHER = {"jacobi": 0, "block": 1}
-CYCLE = {"v": 0, "additive": 1}
+CYCLE = {"v": 0, "additive": 1, "bpx": 2}
 
 
 def _stream_ptr(stream) -> C.c_void_p:
@@ -241,6 +241,8 @@ class Hierarchy:
         check(load().mg_get_codes(self._h, level, f(a_codes), f(a_scale), f(p_codes), f(p_scale),
                                   _stream_ptr(stream)), "mg_get_codes")
 
+    def get_code_lo(self, level, a_lo, stream=None):
+        check(load().mg_get_code_lo(self._h, level, _dptr(a_lo), _stream_ptr(stream)), "mg_get_code_lo")
 
     def get_bpa(self, level, a_rec=None, a_stream=None, p_rec=None, p_stream=None, stream=None):
         """Copies of a bpa hierarchy's records / byte streams of a coarse level; returns the
@@ -327,6 +329,14 @@ class Server:
         return {"queued": q.value, "running": r.value, "bytes_in_use": b.value}
 
 
+def encode_deltas_promote(delta, diag, codes, lo, scale, fmt: int, stream=None):
+    """Rows of delta (n, k) FP64 with their reconstructed diagonals diag (n,) ->
+    codes, lo (n, k) int16 views of uint16, scale (n,) float32 (sign = promotion flag)."""
+    n, k = delta.shape
+    check(load().mg_encode_deltas_promote(n, k, _dptr(delta), _dptr(diag), fmt, _dptr(codes), _dptr(lo),
+                                          _dptr(scale), _stream_ptr(stream)), "mg_encode_deltas_promote")
+
+
 def encode_deltas(delta, codes, scale, fmt: int, stream=None):
     n, k = delta.shape
     check(load().mg_encode_deltas(n, k, _dptr(delta), fmt, _dptr(codes), _dptr(scale), _stream_ptr(stream)),
@@ -348,3 +358,11 @@ def bpa_decode(rec, stream_bytes, out, stream=None):
     fp32 = 1 if out.element_size() == 4 else 0
     check(load().mg_bpa_decode(n, k, _dptr(rec), _dptr(stream_bytes), fp32, _dptr(out), _stream_ptr(stream)),
           "mg_bpa_decode")
+
+
+def probe_fp64_fma(n_ctas: int, iters: int, sink, stream=None) -> int:
+    """Enqueue the FP64 fma-rate probe (mg_probe_fp64_fma); returns the launch's flops."""
+    fl = C.c_int64()
+    check(load().mg_probe_fp64_fma(int(n_ctas), int(iters), _dptr(sink), C.byref(fl), _stream_ptr(stream)),
+          "mg_probe_fp64_fma")
+    return int(fl.value)

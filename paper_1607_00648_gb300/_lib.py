@@ -83,6 +83,8 @@ _SIGS = {
     "mg_get_deltas": (C.c_int, [_P, C.c_int, _P, _P, _P]),
     "mg_get_codes": (C.c_int, [_P, C.c_int, _P, _P, _P, _P, _P]),
     "mg_encode_deltas": (C.c_int, [C.c_int64, C.c_int, _P, C.c_int, _P, _P, _P]),
+    "mg_encode_deltas_promote": (C.c_int, [C.c_int64, C.c_int, _P, _P, C.c_int, _P, _P, _P, _P]),
+    "mg_get_code_lo": (C.c_int, [_P, C.c_int, _P, _P]),
     "mg_bpa_encode": (C.c_int, [C.c_int64, C.c_int32, _P, C.c_double, _P, _P, _P, _P, _P]),
     "mg_bpa_decode": (C.c_int, [C.c_int64, C.c_int32, _P, _P, C.c_int32, _P, _P]),
     "mg_get_bpa": (C.c_int, [_P, C.c_int, _P, _P, _P, _P, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64), _P]),
@@ -96,6 +98,7 @@ _SIGS = {
     "mg_server_info": (C.c_int, [_P, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_size_t)]),
     "mg_server_destroy": (None, [_P]),
     "mg_destroy_hier": (None, [_P]),
+    "mg_probe_fp64_fma": (C.c_int, [C.c_int64, C.c_int32, _P, C.POINTER(C.c_int64), _P]),
     "mg_last_error": (C.c_char_p, []),
     "mg_version": (C.c_char_p, []),
 }

@@ -14,7 +14,7 @@ BUILD = os.path.join(HERE, "_build")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-lineinfo"]
-SOURCES = ["grid.cpp", "solver.cu", "noalloc.cu", "k2d_f64.cu", "k2d_f32.cu", "k3d_f64.cu", "k3d_f32.cu", "persist_2d_f64.cu", "persist_2d_mixed.cu", "persist_3d_f64.cu", "persist_3d_mixed.cu",
+SOURCES = ["grid.cpp", "solver.cu", "noalloc.cu", "probe.cu", "k2d_f64.cu", "k2d_f32.cu", "k3d_f64.cu", "k3d_f32.cu", "persist_2d_f64.cu", "persist_2d_mixed.cu", "persist_3d_f64.cu", "persist_3d_mixed.cu",
            "batch.cu", "server.cu", "batch_2d_f64.cu", "batch_2d_f32.cu", "batch_3d_f64.cu", "batch_3d_f32.cu"]
 
 
@@ -25,8 +25,18 @@ def _nvcc() -> str:
     return cand
 
 
-def _compile(src: str, extra: list[str]) -> str:
+def _headers_mtime() -> float:
+    hdrs = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
+    inc = os.path.join(os.path.dirname(HERE), "include")
+    hdrs += [os.path.join(inc, f) for f in os.listdir(inc) if f.endswith(".h")]
+    return max(os.path.getmtime(h) for h in hdrs)
+
+
+def _compile(src: str, extra: list[str], incremental: bool = False) -> str:
     obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
+    if incremental and not extra and os.path.exists(obj):
+        if os.path.getmtime(obj) > max(os.path.getmtime(os.path.join(CSRC, src)), _headers_mtime()):
+            return obj
     cmd = [_nvcc(), *ARCH, *COMMON, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
     if src.endswith(".cu"):
         cmd[1:1] = ["--expt-relaxed-constexpr"]
@@ -36,12 +46,14 @@ def _compile(src: str, extra: list[str]) -> str:
     return obj
 
 
-def build(verbose: bool = False, ptxas_info: bool = False) -> str:
+def build(verbose: bool = False, ptxas_info: bool = False, incremental: bool = False) -> str:
+    """Compile every translation unit (incremental: only those older than their source or
+    any header) and link libmg.so."""
     os.makedirs(BUILD, exist_ok=True)
     srcs = [s for s in SOURCES if os.path.exists(os.path.join(CSRC, s))]
     extra = ["-Xptxas", "-v"] if ptxas_info else []
     with cf.ThreadPoolExecutor(max_workers=len(srcs)) as ex:
-        objs = list(ex.map(lambda s: _compile(s, extra), srcs))
+        objs = list(ex.map(lambda s: _compile(s, extra, incremental), srcs))
     tmp = OUT + ".tmp"
     cmd = [_nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
     res = subprocess.run(cmd, capture_output=True, text=True)
@@ -54,4 +66,4 @@ def build(verbose: bool = False, ptxas_info: bool = False) -> str:
 
 
 if __name__ == "__main__":
-    build(verbose=True, ptxas_info="-v" in sys.argv)
+    build(verbose=True, ptxas_info="-v" in sys.argv, incremental="-i" in sys.argv)

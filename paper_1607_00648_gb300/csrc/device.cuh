@@ -168,22 +168,32 @@ __device__ __forceinline__ bool delta_row_live(uint64_t key) {
 // delta entry k of the vertex in slot `slot`; idx = its position in the 16-bit or FP64
 // planes.  aux: per-vertex FP32 scales (DMODE 2, 3); DMODE 4 decodes from the stream p
 // with the vertex's record `key` (delta_row).
+// lo_off (DMODE 2, 3; 0 = no promotion): distance from the code planes to the planes of
+// the low halves.  A promoted vertex (the sign bit of its scale set: its 16-bit codes
+// could not reconstruct its diagonal, Sect. 5 cancellation) stores the FP32 bit pattern
+// of delta / s as (code << 16 | low half); the value is then that FP32 number times |s|.
 template <int DMODE, typename T>
 __device__ __forceinline__ T load_delta(const void* p, const void* aux, int64_t idx, int64_t slot, int k = 0,
-                                        uint64_t key = 0) {
+                                        uint64_t key = 0, int64_t lo_off = 0) {
   if constexpr (DMODE == 1) {
     return static_cast<T>(static_cast<const double*>(p)[idx]);
-  } else if constexpr (DMODE == 2) {
-    return static_cast<T>(bf16_bits_to_float(static_cast<const uint16_t*>(p)[idx]) *
-                          static_cast<const float*>(aux)[slot]);
-  } else if constexpr (DMODE == 3) {
-    return static_cast<T>(fp16_bits_to_float(static_cast<const uint16_t*>(p)[idx]) *
-                          static_cast<const float*>(aux)[slot]);
+  } else if constexpr (DMODE == 2 || DMODE == 3) {
+    const float s = static_cast<const float*>(aux)[slot];
+    const uint16_t* q = static_cast<const uint16_t*>(p);
+    if (lo_off != 0 && s < 0.0f)
+      return static_cast<T>(__uint_as_float((static_cast<uint32_t>(q[idx]) << 16) | q[idx + lo_off]) * -s);
+    return static_cast<T>((DMODE == 2 ? bf16_bits_to_float(q[idx]) : fp16_bits_to_float(q[idx])) * s);
   } else if constexpr (DMODE == 4) {
     return bpa_decode<T>(static_cast<const uint8_t*>(p), key, k);
   } else {
     return T(0);
   }
+}
+
+// distance to the low-half planes of A_hat codes on level L (16-bit modes; 0 otherwise)
+template <int DMODE>
+__device__ __forceinline__ int64_t a_lo_off(const LevelDesc& L, int K) {
+  return (DMODE == 2 || DMODE == 3) ? L.n_slots * K : 0;
 }
 
 // P(V, o) = P_dlin(o) + P_hat_V(o) in FP64 (PMODE 0: d-linear only, 1: FP64 delta planes)

@@ -37,6 +37,7 @@ struct DevLevel {
   float *u32 = nullptr, *b32 = nullptr, *r32 = nullptr, *t32 = nullptr;
   double* dinv = nullptr;  // FP64 hierarchies: omega / diag(A) for the Jacobi sweeps
   double *ad = nullptr, *ar = nullptr;  // additive cycle: correction d_l, surplus residual rh_l
+  double* ai = nullptr;                 // BPX: injected skipped c-point updates i_l
   int32_t* child = nullptr;             // additive cycle: level-(l+1) slot at position 3x (injection)
   int R64 = 0, R32 = 0;    // slab depths picked by mg_autotune (0: the default rule)
   double* partial = nullptr;

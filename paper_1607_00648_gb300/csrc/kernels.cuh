@@ -304,7 +304,8 @@ __device__ __forceinline__ double sweep_item(const SweepArgs<T>& a, int64_t bric
             kk /= 3;
             m *= Bu;
           }
-          const T d = load_delta<AMODE, T>(a.ahat, a.ascale, (brick * N3 + k) * L.S + s, slot, k, akey);
+          const T d = load_delta<AMODE, T>(a.ahat, a.ascale, (brick * N3 + k) * L.S + s, slot, k, akey,
+                                           a_lo_off<AMODE>(L, N3));
           if (k == N3 / 2)
             D += d;
           else
@@ -445,7 +446,9 @@ __global__ void __launch_bounds__(DIM == 2 ? 256 : 64) k_patch_gs(SweepArgs<T> a
           if (ok) es += el[cl];
         }
         T st = static_cast<T>(elem_k(DIM, ham)) * es * scale;
-        if constexpr (AMODE != 0) st += load_delta<AMODE, T>(a.ahat, a.ascale, plane_index(L, vs[j], k, N3), vs[j], k, key);
+        if constexpr (AMODE != 0)
+          st += load_delta<AMODE, T>(a.ahat, a.ascale, plane_index(L, vs[j], k, N3), vs[j], k, key,
+                                     a_lo_off<AMODE>(L, N3));
         if (k == N3 / 2) diag = st;
         au = fma(st, ul[un], au);
       }

@@ -19,10 +19,16 @@ static void sweep_b(SweepArgs<T> a, int op, int amode, cudaStream_t s) {
     // as a template parameter so every plane's loads are issued together
     const dim3 grid(static_cast<unsigned>(sweep_ctas_x(DIM, B, T(0), a.L.n_bricks)), static_cast<unsigned>(B / R));
     const size_t sm = DIM == 2 ? 0 : sweep_tile_bytes<DIM, T>(B, R, true);
+    // 2D: 16-byte staging needs u and eps 16-byte aligned (user vectors may be offset views)
+    const bool v16 = ((reinterpret_cast<uintptr_t>(a.u) | reinterpret_cast<uintptr_t>(a.eps)) & 15) == 0;
 #define MG_SWR(AM, OP, RR)                                                                \
   do {                                                                                    \
-    if constexpr (DIM == 2) launch_pdl(k_sweep2c<T, AM, OP, RR>, grid, 128, 0, s, a);        \
-    else launch_pdl(k_sweep3c<T, AM, OP, (RR > 9 ? 9 : RR)>, grid, 128, sm, s, a);           \
+    if constexpr (DIM == 2) {                                                             \
+      if (v16) launch_pdl(k_sweep2v<AM, OP, RR>, grid, RR >= 3 ? 96 : 32, 0, s, a);        \
+      else launch_pdl(k_sweep2c<T, AM, OP, RR>, grid, 128, 0, s, a);                      \
+    } else {                                                                              \
+      launch_pdl(k_sweep3c<T, AM, OP, (RR > 9 ? 9 : RR)>, grid, 128, sm, s, a);           \
+    }                                                                                     \
   } while (0)
 #define MG_SW(AM, OP)                                                    \
   do {                                                                   \
@@ -40,6 +46,34 @@ static void sweep_b(SweepArgs<T> a, int op, int amode, cudaStream_t s) {
     }
 #undef MG_SW
 #undef MG_SWR
+  } else if (std::is_same<T, double>::value && ((DIM == 2 && B == 27) || (DIM == 3 && B == 9)) &&
+             (op == kResidual || a.dinv != nullptr)) {
+    // FP64 (FP64-unit bound): column-marching kernels that issue the fewest FP64
+    // instructions per vertex; Jacobi takes omega / diag(A) from the setup
+    if constexpr (std::is_same<T, double>::value && ((DIM == 2 && B == 27) || (DIM == 3 && B == 9))) {
+      const dim3 grid(static_cast<unsigned>(a.L.n_bricks), static_cast<unsigned>(B / R));
+#define MG_SWR(AM, OP, RR)                                                                                  \
+  do {                                                                                                      \
+    if constexpr (DIM == 2)                                                                                 \
+      launch_pdl(k_sweep2f<AM, OP, RR>, grid, RR >= 3 ? 96 : 32, 0, s, a);                                  \
+    else                                                                                                    \
+      launch_pdl(k_sweep3c<T, AM, OP, (RR > 9 ? 9 : RR)>, grid, 128, sweep_tile_bytes<DIM, T>(B, RR > 9 ? 9 : RR, true), s, a); \
+  } while (0)
+#define MG_SW(AM, OP)                                                    \
+  do {                                                                   \
+    if (R == 1) MG_SWR(AM, OP, 1);                                       \
+    else if (R == 3) MG_SWR(AM, OP, 3);                                  \
+    else if (R == 9) MG_SWR(AM, OP, 9);                                  \
+    else MG_SWR(AM, OP, 27);                                             \
+  } while (0)
+      if (op == kJacobi) {
+        if (amode == 1) MG_SW(1, kJacobi); else MG_SW(0, kJacobi);
+      } else {
+        if (amode == 1) MG_SW(1, kResidual); else MG_SW(0, kResidual);
+      }
+#undef MG_SW
+#undef MG_SWR
+    }
   } else {
     const dim3 grid(static_cast<unsigned>(a.L.n_bricks), static_cast<unsigned>(B / R));
     int threads = ((R * PLANE + 31) / 32) * 32;

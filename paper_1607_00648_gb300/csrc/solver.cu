@@ -91,6 +91,35 @@ __global__ void k_add_correct(LevelDesc L, const double* dinv, const double* r, 
   d[s] = c;
   u[s] += c;
 }
+// BPX (Alg. 3) ascent on a level above the coarsest: d = omega D^-1 r on DoFs; the
+// c-points (every coordinate a multiple of 3) skip their own update, keep d = 0 and
+// leave the skipped update in r for the injection i_{l-1} = I d_l
+template <int DIM>
+__global__ void k_bpx_correct(LevelDesc L, const double* dinv, double* r, double* d, double* u) {
+  const int64_t s = blockIdx.x * static_cast<int64_t>(kBlock) + threadIdx.x;
+  if (s >= L.n_slots) return;
+  const double c = is_dof(L.vflags[s]) ? dinv[s] * r[s] : 0.0;
+  int x[DIM];
+  bool cp = coords_of<DIM>(L, s, x);
+#pragma unroll
+  for (int i = 0; i < DIM; ++i) cp = cp && x[i] % 3 == 0;
+  r[s] = c;
+  d[s] = cp ? 0.0 : c;
+  if (!cp) u[s] += c;
+}
+// BPX descent at the c-points: x_f += i_c at the fine slot coinciding with each coarse
+// DoF (the prolongation of x = d - i left P i out there, and P is the injection at
+// c-points), for the correction d and the iterate u
+__global__ void k_bpx_cpoints(LevelDesc Lc, const int32_t* child, const double* ic, double* df, double* uf) {
+  const int64_t s = blockIdx.x * static_cast<int64_t>(kBlock) + threadIdx.x;
+  if (s >= Lc.n_slots || !is_dof(Lc.vflags[s]) || child[s] < 0) return;
+  df[child[s]] += ic[s];
+  uf[child[s]] += ic[s];
+}
+__global__ void k_sub(int64_t n, const double* x, const double* y, double* z) {
+  const int64_t s = blockIdx.x * static_cast<int64_t>(kBlock) + threadIdx.x;
+  if (s < n) z[s] = x[s] - y[s];
+}
 __global__ void k_negate(int64_t n, const double* x, double* y) {
   const int64_t s = blockIdx.x * static_cast<int64_t>(kBlock) + threadIdx.x;
   if (s < n) y[s] = -x[s];
@@ -182,19 +211,71 @@ __global__ void k_encode_rows(int64_t n, int K, const double* delta, uint16_t* c
   for (int k = 0; k < K; ++k) codes[i * K + k] = sd > 0.0 ? round_to_16<FMT>(delta[i * K + k] / sd) : 0;
 }
 
-// same on brick-major planes of a level
+// Promotion rule of a row (Sect. 5 cancellation, the dtype counterpart of the paper's
+// per-vertex choice against eps_mf): half a unit of the 16-bit format relative to the
+// scale, h s (h = 2^-9 for BF16, 2^-12 for FP16), exceeds 2^-8 of the reconstructed
+// diagonal |A_vv|.  Products by powers of two: the comparison is exact.
 template <int FMT>
-__global__ void k_encode_planes(LevelDesc L, int K, const double* delta, uint16_t* codes, float* scale) {
+__device__ __forceinline__ bool promote_row(float sc, double diag) {
+  constexpr double h = FMT == 1 ? 0x1p-9 : 0x1p-12;
+  return static_cast<double>(sc) * h > 0x1p-8 * fabs(diag);
+}
+
+// codes of one row: plain 16-bit codes, or (promoted) the FP32 bit pattern of
+// fl32(delta / s) split into the code (high half) and lo (low half)
+template <int FMT>
+__device__ __forceinline__ void put_codes(double d, double sd, bool prom, uint16_t* code, uint16_t* lo) {
+  if (prom) {
+    const uint32_t bits = __float_as_uint(__double2float_rn(d / sd));
+    *code = static_cast<uint16_t>(bits >> 16);
+    *lo = static_cast<uint16_t>(bits & 0xffffu);
+  } else {
+    *code = sd > 0.0 ? round_to_16<FMT>(d / sd) : 0;
+    if (lo) *lo = 0;
+  }
+}
+
+// per row with promotion against diag[i]: the flag is the sign of scale[i]
+template <int FMT>
+__global__ void k_encode_rows_promote(int64_t n, int K, const double* delta, const double* diag, uint16_t* codes,
+                                      uint16_t* lo, float* scale) {
+  const int64_t i = blockIdx.x * static_cast<int64_t>(kBlock) + threadIdx.x;
+  if (i >= n) return;
+  double m = 0.0;
+  for (int k = 0; k < K; ++k) m = fmax(m, fabs(delta[i * K + k]));
+  const float s = __double2float_rn(m);
+  const bool prom = s > 0.0f && promote_row<FMT>(s, diag[i]);
+  scale[i] = prom ? -s : s;
+  const double sd = static_cast<double>(s);
+  for (int k = 0; k < K; ++k) put_codes<FMT>(delta[i * K + k], sd, prom, codes + i * K + k, lo + i * K + k);
+}
+
+// same on brick-major planes of a level.  promote (A_hat only): the row's reconstructed
+// diagonal A_redisc + A_hat is formed from the level's coefficients (full_stencil) and
+// promoted rows write their low halves n_slots * K entries after the code planes
+template <int DIM, int FMT>
+__global__ void k_encode_planes(LevelDesc L, int K, const double* delta, uint16_t* codes, float* scale,
+                                const double* eps, int promote) {
   const int64_t s = blockIdx.x * static_cast<int64_t>(kBlock) + threadIdx.x;
   if (s >= L.n_slots) return;
   double m = 0.0;
   for (int k = 0; k < K; ++k) m = fmax(m, fabs(delta[plane_index(L, s, k, K)]));
   const float sc = __double2float_rn(m);
-  scale[s] = sc;
+  bool prom = false;
+  if (promote && sc > 0.0f) {
+    int x[DIM];
+    if (coords_of<DIM>(L, s, x)) {
+      double st[cpow(3, DIM)];
+      full_stencil<DIM>(L, eps, delta, x, s, st);
+      prom = promote_row<FMT>(sc, st[cpow(3, DIM) / 2]);
+    }
+  }
+  scale[s] = prom ? -sc : sc;
   const double sd = static_cast<double>(sc);
+  uint16_t* lo = promote ? codes + L.n_slots * K : nullptr;
   for (int k = 0; k < K; ++k) {
     const int64_t idx = plane_index(L, s, k, K);
-    codes[idx] = sd > 0.0 ? round_to_16<FMT>(delta[idx] / sd) : 0;
+    put_codes<FMT>(delta[idx], sd, prom, codes + idx, lo ? lo + idx : nullptr);
   }
 }
 
@@ -497,9 +578,10 @@ static mg_status create(const Grid* g, const mg_options& o, Hier** out, int prio
     if ((st = dalloc(*H, &D.eps, ns)) != MG_OK) return fail(st);
     if ((st = dalloc(*H, &D.r, ns)) != MG_OK) return fail(st);
     if ((st = dalloc(*H, &D.t, ns)) != MG_OK) return fail(st);
-    if (o.cycle == MG_CYCLE_ADDITIVE) {
+    if (o.cycle != MG_CYCLE_V) {
       if ((st = dalloc(*H, &D.ad, ns)) != MG_OK) return fail(st);
       if ((st = dalloc(*H, &D.ar, ns)) != MG_OK) return fail(st);
+      if (o.cycle == MG_CYCLE_BPX && l < H->L && (st = dalloc(*H, &D.ai, ns)) != MG_OK) return fail(st);
       if (l < H->L) {  // injection map: the level-(l+1) slot at position 3x
         const HostLevel& hf = g->levels[l + 1];
         std::vector<int32_t> child(hl.n_slots, -1);
@@ -541,7 +623,8 @@ static mg_status create(const Grid* g, const mg_options& o, Hier** out, int prio
         }
       } else if (l < H->top) {
         if (H->galerkin) {
-          if ((st = dalloc(*H, &D.a16, ns * n3)) != MG_OK) return fail(st);
+          // code planes followed by the low-half planes of promoted vertices
+          if ((st = dalloc(*H, &D.a16, 2 * ns * n3)) != MG_OK) return fail(st);
           if ((st = dalloc(*H, &D.ascale, ns)) != MG_OK) return fail(st);
         }
         if (H->boxmg) {
@@ -640,8 +723,8 @@ mg_status hier_create(const Grid* g, const mg_options& o, int priority, Hier** o
   *out = nullptr;
   if (o.coarsest_level < 1 || o.coarsest_level >= g->L || o.nu1 < 0 || o.nu2 < 0 || !(o.omega > 0.0) ||
       o.transfer < 0 || o.transfer > 1 || o.coarse < 0 || o.coarse > 1 || o.precision < 0 || o.precision > 3 || o.smoother < 0 || o.smoother > 1 ||
-      (o.smoother == MG_SMOOTH_BLOCK && (o.gs_sweeps < 1 || o.gs_sweeps > 64)) || o.cycle < 0 || o.cycle > 1 ||
-      (o.cycle == MG_CYCLE_ADDITIVE && (o.precision != MG_PREC_FP64 || o.smoother != MG_SMOOTH_JACOBI)) ||
+      (o.smoother == MG_SMOOTH_BLOCK && (o.gs_sweeps < 1 || o.gs_sweeps > 64)) || o.cycle < 0 || o.cycle > 2 ||
+      (o.cycle != MG_CYCLE_V && (o.precision != MG_PREC_FP64 || o.smoother != MG_SMOOTH_JACOBI)) ||
       (o.precision == MG_PREC_MIXED_BPA && !(o.eps_mf >= 0.0 && o.eps_mf < 1e300))) {
     set_error("mg_hier_create: invalid options");
     return MG_ERR_INVALID_ARG;
@@ -686,12 +769,14 @@ size_t hier_footprint(const Grid& g, const mg_options& o) {
     bytes += nb * n3 * 4 + nb * d * 4 + hl.brick_rank.size() * 4 + 2 * ns + (hl.n_hanging > 0 ? ns * full * 12 : 0);
     bytes += 3 * ns * 8 + nb * hl.B * 8 + 4 + (mixed ? 0 : ns * 8);
     if (l < g.L) bytes += 2 * ns * 8;
-    if (o.cycle == MG_CYCLE_ADDITIVE) bytes += 2 * ns * 8 + (l < g.L ? ns * 4 : 0);
+    if (o.cycle != MG_CYCLE_V) bytes += 2 * ns * 8 + (l < g.L ? ns * 4 : 0);
+    if (o.cycle == MG_CYCLE_BPX && l < g.L) bytes += ns * 8;
     if (l < top) bytes += (galerkin ? ns * n3 * 8 : 0) + (boxmg ? ns * n5 * 8 : 0);
     if (mixed) {
       bytes += 5 * ns * 4;
       const size_t per = o.precision == MG_PREC_MIXED_BPA ? 8 : 2, sc = o.precision == MG_PREC_MIXED_BPA ? 8 : 4;
-      if (l < top) bytes += (galerkin ? ns * n3 * per + ns * sc : 0) + (boxmg ? ns * n5 * per + ns * sc : 0);
+      const size_t per_a = o.precision == MG_PREC_MIXED_BPA ? 8 : 4;  // 16-bit codes + low halves
+      if (l < top) bytes += (galerkin ? ns * n3 * per_a + ns * sc : 0) + (boxmg ? ns * n5 * per + ns * sc : 0);
     }
     if (l == top && top < g.L) bytes += ns * 4 + (mixed ? 2 * ns * 4 : 0);  // injection map, FP32 composite vectors
   }
@@ -953,23 +1038,23 @@ static mg_status run_setup(Hier& H, const double* eps_in, cudaStream_t s, bool c
           bpa_encode_enqueue(BpaSrc{D.phat, n5, true, D.d}, ns, H.opt.eps_mf, D.pbpa_rec, D.pbpa,
                              H.bpa_used + 2 * l + 1, H.d_status, 4, 5, s);
       } else if (l < H.top) {
-        if (H.galerkin) {
-          if (H.fmt == 1)
-            k_encode_planes<1><<<nblk(D.d.n_slots), kBlock, 0, s>>>(D.d, n3, D.ahat, D.a16, D.ascale);
-          else
-            k_encode_planes<2><<<nblk(D.d.n_slots), kBlock, 0, s>>>(D.d, n3, D.ahat, D.a16, D.ascale);
+        const unsigned g = nblk(D.d.n_slots);
+#define MG_ENC(DIM, FMT)                                                                          \
+  do {                                                                                            \
+    if (H.galerkin) k_encode_planes<DIM, FMT><<<g, kBlock, 0, s>>>(D.d, n3, D.ahat, D.a16, D.ascale, D.eps, 1); \
+    if (H.boxmg) k_encode_planes<DIM, FMT><<<g, kBlock, 0, s>>>(D.d, n5, D.phat, D.p16, D.pscale, D.eps, 0);    \
+  } while (0)
+        if (d == 2) {
+          if (H.fmt == 1) MG_ENC(2, 1); else MG_ENC(2, 2);
+        } else {
+          if (H.fmt == 1) MG_ENC(3, 1); else MG_ENC(3, 2);
         }
-        if (H.boxmg) {
-          if (H.fmt == 1)
-            k_encode_planes<1><<<nblk(D.d.n_slots), kBlock, 0, s>>>(D.d, n5, D.phat, D.p16, D.pscale);
-          else
-            k_encode_planes<2><<<nblk(D.d.n_slots), kBlock, 0, s>>>(D.d, n5, D.phat, D.p16, D.pscale);
-        }
+#undef MG_ENC
       }
     }
     MG_CHECK(last_launch("setup: encode"));
   }
-  if (H.opt.cycle == MG_CYCLE_ADDITIVE) MG_CHECK(additive_reset(H, nullptr, s));
+  if (H.opt.cycle != MG_CYCLE_V) MG_CHECK(additive_reset(H, nullptr, s));
   if (!check_now) {  // the caller reads d_status after one synchronisation for many hierarchies
     H.ready = true;
     return MG_OK;
@@ -1135,16 +1220,30 @@ static mg_status solve_fp64(Hier& H, double* u, const double* b, double tol, int
 // P d_{l-1}, u_l += P d_{l-1}, uh_l = u_l - P u_{l-1}; ascent: r_l = b_l - A_l u_l (D.r),
 // rh_l = b_l - A_l uh_l (D.ar), d_l = omega D^-1 r_l, u_l += d_l, u_{l-1} = I u_l,
 // b_{l-1} = R rh_l.  The coarse b_l are rebuilt by the restriction every traversal.
+//
+// BPX (Alg. 3), in the same pass: above the coarsest level the c-points skip their own
+// update, which is injected to the coarser level (i_{l-1} = I d_l, D.ai of level l-1)
+// and zeroed; the descent applies P d_{l-1} at c-points and P (d_{l-1} - i_{l-1})
+// elsewhere (P is the injection at c-points, so P (d - i) + i there); the coarse
+// iterates are not overwritten by injection.
 static void additive_traversal(Hier& H, double* u, const double* b, cudaStream_t s) {
   auto U = [&](int l) { return l == H.L ? u : H.lv[l].u; };
   auto Bv = [&](int l) { return l == H.L ? b : static_cast<const double*>(H.lv[l].b); };
+  const bool bpx = H.opt.cycle == MG_CYCLE_BPX;
   for (int l = H.c; l <= H.L; ++l) {
     DevLevel& D = H.lv[l];
     const size_t bytes = static_cast<size_t>(D.d.n_slots) * sizeof(double);
     if (l > H.c) {
       DevLevel& C = H.lv[l - 1];
-      transfer<double>(H, l, false, C.ad, D.ad, s);
-      transfer<double>(H, l, false, C.ad, U(l), s);
+      if (bpx) {
+        k_sub<<<nblk(C.d.n_slots), kBlock, 0, s>>>(C.d.n_slots, C.ad, C.ai, C.ar);  // x = d - i
+        transfer<double>(H, l, false, C.ar, D.ad, s);
+        transfer<double>(H, l, false, C.ar, U(l), s);
+        k_bpx_cpoints<<<nblk(C.d.n_slots), kBlock, 0, s>>>(C.d, C.child, C.ai, D.ad, U(l));
+      } else {
+        transfer<double>(H, l, false, C.ad, D.ad, s);
+        transfer<double>(H, l, false, C.ad, U(l), s);
+      }
       cudaMemcpyAsync(D.t, U(l), bytes, cudaMemcpyDeviceToDevice, s);
       k_negate<<<nblk(C.d.n_slots), kBlock, 0, s>>>(C.d.n_slots, C.u, C.ar);  // rh_{l-1} is formed later
       transfer<double>(H, l, false, C.ar, D.t, s);
@@ -1156,6 +1255,16 @@ static void additive_traversal(Hier& H, double* u, const double* b, cudaStream_t
     DevLevel& D = H.lv[l];
     sweep<double>(H, l, kResidual, U(l), Bv(l), D.r, nullptr, s);
     sweep<double>(H, l, kResidual, D.t, Bv(l), D.ar, nullptr, s);
+    if (bpx && l > H.c) {
+      DevLevel& C = H.lv[l - 1];
+      if (H.dim == 2)
+        k_bpx_correct<2><<<nblk(D.d.n_slots), kBlock, 0, s>>>(D.d, D.dinv, D.r, D.ad, U(l));
+      else
+        k_bpx_correct<3><<<nblk(D.d.n_slots), kBlock, 0, s>>>(D.d, D.dinv, D.r, D.ad, U(l));
+      k_inject_level<<<nblk(C.d.n_slots), kBlock, 0, s>>>(C.d, C.child, D.r, C.ai);
+      transfer<double>(H, l, true, D.ar, C.b, s);
+      continue;
+    }
     k_add_correct<<<nblk(D.d.n_slots), kBlock, 0, s>>>(D.d, D.dinv, D.r, D.ad, U(l));
     if (l > H.c) {
       DevLevel& C = H.lv[l - 1];
@@ -1171,6 +1280,7 @@ static mg_status additive_reset(Hier& H, double* u, cudaStream_t s) {
     DevLevel& D = H.lv[l];
     const size_t bytes = static_cast<size_t>(D.d.n_slots) * sizeof(double);
     MG_TRY_CUDA(cudaMemsetAsync(D.ad, 0, bytes, s));
+    if (D.ai) MG_TRY_CUDA(cudaMemsetAsync(D.ai, 0, bytes, s));
     if (l < H.L) MG_TRY_CUDA(cudaMemsetAsync(D.u, 0, bytes, s));
   }
   if (u) MG_TRY_CUDA(cudaMemsetAsync(u, 0, H.lv[H.L].d.n_slots * sizeof(double), s));
@@ -1918,7 +2028,7 @@ mg_status mg_vcycle(mg_hier* h, double* u, const double* b, void* stream) {
     fill_hanging<double>(*H, v.ut, v.uL, s);
     composite_cycle<double>(*H, v.uL, v.bL, v.ut, v.bt, s);
     inject<double>(*H, v.uL, v.ut, s);
-  } else if (H->opt.cycle == MG_CYCLE_ADDITIVE) {
+  } else if (H->opt.cycle != MG_CYCLE_V) {
     additive_traversal(*H, u, b, s);  // on the stored coarse iterates and corrections
   } else {
     vcycle<double>(*H, H->L, u, b, s);
@@ -1941,7 +2051,7 @@ mg_status mg_solve(mg_hier* h, double* u, const double* b, double rel_tol, int m
                           H->n_c <= 64 && H->L < kMaxLevels;
   const mg_status st = H->adaptive ? (H->mixed ? solve_comp_mixed(*H, u, b, rel_tol, max_cycles, stats, s)
                                                  : solve_comp_fp64(*H, u, b, rel_tol, max_cycles, stats, s))
-                       : H->opt.cycle == MG_CYCLE_ADDITIVE ? solve_additive(*H, u, b, rel_tol, max_cycles, stats, s)
+                       : H->opt.cycle != MG_CYCLE_V ? solve_additive(*H, u, b, rel_tol, max_cycles, stats, s)
                        : persistent ? solve_persistent(*H, u, b, rel_tol, max_cycles, stats, s)
                        : H->mixed   ? solve_mixed(*H, u, b, rel_tol, max_cycles, stats, s)
                                     : solve_fp64(*H, u, b, rel_tol, max_cycles, stats, s);
@@ -2023,6 +2133,35 @@ mg_status mg_get_codes(mg_hier* h, int level, uint16_t* a_codes, float* a_scale,
     k_planes16_to_offset_major<<<nblk(D.d.n_slots), kBlock, 0, s>>>(D.d, ipow(5, H->dim), D.p16, p_codes);
   if (p_scale && D.pscale) MG_TRY_CUDA(cudaMemcpyAsync(p_scale, D.pscale, ns * sizeof(float), cudaMemcpyDeviceToDevice, s));
   return last_launch("mg_get_codes");
+}
+
+mg_status mg_get_code_lo(mg_hier* h, int level, uint16_t* a_lo, void* stream) {
+  Hier* H = H_(h);
+  MG_CHECK(check_level(H, level, true));
+  if (!H->mixed || level >= H->top || !H->lv[level].a16 || !a_lo) {
+    set_error("mg_get_code_lo: no A_hat codes (FP64 or bpa hierarchy, finest level, or no Galerkin operator)");
+    return MG_ERR_INVALID_ARG;
+  }
+  DevLevel& D = H->lv[level];
+  cudaStream_t s = pick(*H, stream);
+  k_planes16_to_offset_major<<<nblk(D.d.n_slots), kBlock, 0, s>>>(D.d, ipow(3, H->dim),
+                                                                    D.a16 + D.d.n_slots * ipow(3, H->dim), a_lo);
+  return last_launch("mg_get_code_lo");
+}
+
+mg_status mg_encode_deltas_promote(int64_t n, int k, const double* delta, const double* diag, int fmt,
+                                   uint16_t* codes, uint16_t* lo, float* scale, void* stream) {
+  if (n < 0 || k <= 0 || (n > 0 && (!delta || !diag || !codes || !lo || !scale)) || (fmt != 1 && fmt != 2)) {
+    set_error("mg_encode_deltas_promote: invalid argument");
+    return MG_ERR_INVALID_ARG;
+  }
+  if (n == 0) return MG_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (fmt == 1)
+    k_encode_rows_promote<1><<<nblk(n), kBlock, 0, s>>>(n, k, delta, diag, codes, lo, scale);
+  else
+    k_encode_rows_promote<2><<<nblk(n), kBlock, 0, s>>>(n, k, delta, diag, codes, lo, scale);
+  return last_launch("mg_encode_deltas_promote");
 }
 
 mg_status mg_encode_deltas(int64_t n, int k, const double* delta, int fmt, uint16_t* codes, float* scale,

@@ -9,6 +9,48 @@ from oracle import multigrid
 from oracle import spacetree as stt
 import synthetic as syn
 
+# Unit roundoff of FP64.
+U64 = 2.0 ** -53
+
+# Parity bound of multi-step FP64 outputs (V-cycles, block steps, traversals, solves)
+# against the oracle, as an infinity-norm relative difference:
+#     |gpu - oracle|_inf / |oracle|_inf  <=  U64 * (C1 + C2 * F),
+# F the cancellation factor of the hierarchy (Case.amplification: the largest
+# sum|terms| / |sum| over the coarse Galerkin diagonals; 1 without Galerkin operators).
+# Two correct FP64 evaluations of a Galerkin entry differ by up to a small multiple of
+# U64 * sum|terms| (Higham's bound for a sum), i.e. U64 * F relative to the diagonal,
+# and a cycle's coarse corrections inherit that perturbation (the C2 F term); the
+# smoothing and transfer arithmetic itself adds a few hundred roundings (the C1 term).
+# Measured on the GPU (err / U64 of every check is recorded and printed at the end of
+# the session): without cancellation at most 322 (solves) and 57 (cycles); with it at
+# most 0.05 F (solves, the full-size checkerboard) and 0.03 F (cycles).  The constants
+# keep a margin of at least 6x over every measured error.  On the composite grid the
+# two-level FAS cycle amplifies rounding beyond F (measured 10,700 u per cycle and
+# 42,700 u per solve at F = 118), so it has its own C1.
+BOUNDS = {
+    "cycle": (2.0 ** 12, 0.25),
+    "solve": (2.0 ** 13, 0.5),
+    "composite_cycle": (2.0 ** 17, 0.0),
+    "composite_solve": (2.0 ** 19, 0.0),
+}
+# residual histories (relative residuals, down to 1e-10) of two correct solves
+HIST_RTOL, HIST_ATOL = 4e-9, 1e-13
+
+# (check, err / U64, F, bound / U64) of every comparison of the session
+OBSERVED: list = []
+
+
+def parity_bound(amp: float, kind: str) -> float:
+    c1, c2 = BOUNDS[kind]
+    return U64 * (c1 + c2 * max(float(amp), 1.0))
+
+
+def parity_check(name: str, err: float, amp: float, kind: str) -> None:
+    """Record err / U64 and assert err <= U64 (C1 + C2 F) for the kind of output."""
+    bound = parity_bound(amp, kind)
+    OBSERVED.append((name, float(err) / U64, float(amp), bound / U64))
+    assert err <= bound, f"{name}: err {err:.3e} = {err / U64:.1f} u > bound {bound / U64:.1f} u (F = {amp:.3e})"
+
 
 def lib():
     import paper_1607_00648_gb300 as mg

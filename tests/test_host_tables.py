@@ -131,14 +131,17 @@ def test_option_validation_needs_no_gpu(mg):
 def test_footprints_of_the_storage_modes(mg):
     # device bytes planned per mode: the bpa streams are held at their worst case (8 bytes
     # per entry plus an 8-byte record per slot and operator, against 2 bytes + a 4-byte
-    # scale for BF16); the additive cycle adds two vectors per level and injection maps
+    # scale for BF16, and for A_hat 2 more bytes per entry: the low halves of promoted
+    # vertices); the additive cycle adds two vectors per level and injection maps, BPX
+    # one more vector per coarse level
     g = mg.Grid(2, 5)
     base = mg.hier_footprint(g)
     bf16 = mg.hier_footprint(g, precision="mixed_bf16")
     bpa = mg.hier_footprint(g, precision="mixed_bpa")
     coarse = sum(g.info(lv).n_slots for lv in range(1, 5))
-    assert bpa - bf16 == coarse * ((9 + 25) * 6 + 2 * 4)
+    assert bpa - bf16 == coarse * (9 * 4 + 25 * 6 + 2 * 4)
     add = mg.hier_footprint(g, cycle="additive")
     allv = sum(g.info(lv).n_slots for lv in range(1, 6))
     assert add - base == allv * 16 + coarse * 4
+    assert mg.hier_footprint(g, cycle="bpx") - add == coarse * 8
     assert mg.hier_footprint(g, smoother="block") == base
