@@ -587,6 +587,19 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(w, st64[-1]["cycles"])
 
+    # the batched and served forms (task configs 4 and 5), reduced to finish within the
+    # run: the first 128 problems of the batched workload, the first 150 requests of the
+    # served stream; mixed against FP64 each
+    batched = served = None
+    if rank == 0 and world == 1 and not args.no_a13:
+        with Clocks(torch.cuda.current_device()) as clk_a13:
+            _, probs = batched_problems(mg, torch, 128)
+            batched = batched_solves(mg, torch, probs, 1, flush)
+            del probs
+            torch.cuda.empty_cache()
+            served = served_summary(mg, torch, 150, 200.0, 64.0)
+        batched["clocks"] = served["clocks"] = clk_a13.summary()
+
     if rank == 0:
         out = {
             "metric": "DoF/s to 1e-10 residual drop (FP64; mixed beside it)",
@@ -609,6 +622,7 @@ def run_ours(args):
             "roofline": roofline, "e2e": e2e, "clocks": clocks,
             "gpu_launches": launches64 + (launchesmx if domx else 0),
             "cpu_baseline": cpu,
+            "batched": batched, "served": served,
         }
         print(json.dumps(out))
     if dist:
@@ -741,6 +755,64 @@ def run_sweeps(args):
     print(json.dumps(out))
 
 
+def batched_problems(mg, torch, n, seed=3):
+    """The batched workload's first n problems: edge 3^m cells with m ~ U{3,4,5,6}
+    (seed 3), log-normal eps (sigma 2, correlation length 0.1, seed 1000+i), f ~ U[-1,1]
+    (seed 2000+i); grids shared per size."""
+    ms = syn.batch_problem_sizes(n, seed)
+    grids = {int(m): mg.Grid(2, int(m)) for m in sorted(set(ms.tolist()))}
+    probs = []
+    for i, m in enumerate(ms.tolist()):
+        g = grids[m]
+        eps = syn.lognormal_grf_eps(m, 2, sigma=2.0, seed=1000 + i)
+        b = g.to_slots(m, syn.uniform_load(m, 2, 2000 + i))
+        probs.append((g, m, torch.from_numpy(g.cells_to_concat({m: eps})).cuda(), torch.from_numpy(b).cuda()))
+    return ms, probs
+
+
+def batched_solves(mg, torch, probs, steps, flush):
+    """Setup + solve to 1e-10 of all problems as one batch (mg_batch_setup +
+    mg_batch_solve), mixed and FP64: median over `steps` timed batches (CUDA events)."""
+    n = len(probs)
+    total_dofs = sum(g.info(m).n_dofs for g, m, _, _ in probs)
+    out = {}
+    for prec in ("mixed_bf16", "fp64"):
+        Hs = [mg.Hierarchy(g, precision=prec) for g, m, _, _ in probs]
+        us = [torch.zeros_like(b) for _, _, _, b in probs]
+        bs = [b for _, _, _, b in probs]
+        eps_list = [e for _, _, e, _ in probs]
+        for H, e in zip(Hs, eps_list):
+            H.setup(e)
+        batch = mg.Batch(Hs)
+        batch.solve(us, bs, rel_tol=1e-10, max_cycles=3000)  # warm-up (graph capture)
+        times, setups = [], []
+        stats, status = None, None
+        for _ in range(max(1, steps)):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record()
+            batch.setup(eps_list)
+            e1.record()
+            status, stats = batch.solve(us, bs, rel_tol=1e-10, max_cycles=3000)
+            e2.record()
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e2))
+            setups.append(e0.elapsed_time(e1))
+        t = statistics.median(times) / 1e3
+        cyc = [st["cycles"] for st in stats]
+        out[prec] = {"solves_per_s": n / t, "dof_per_s": total_dofs / t, "s_per_batch": t,
+                     "setup_s": statistics.median(setups) / 1e3, "status": status,
+                     "cycles_median": statistics.median(cyc), "cycles_max": max(cyc),
+                     "max_rel_residual": max(st["rel_residual"] for st in stats)}
+        del batch, Hs
+        torch.cuda.empty_cache()
+    out["mixed_speedup"] = out["mixed_bf16"]["solves_per_s"] / out["fp64"]["solves_per_s"]
+    out["problems"] = n
+    out["dofs"] = total_dofs
+    return out
+
+
 def run_batched(args, n_problems=512, seed=3):
     """Batched workload: n independent 2D problems, edge 3^m cells with m ~ U{3,4,5,6},
     log-normal eps (sigma 2, correlation length 0.1, seed 1000+i), f ~ U[-1,1]
@@ -751,74 +823,25 @@ def run_batched(args, n_problems=512, seed=3):
 
     torch.cuda.set_device(0)
     n = args.batch_size or n_problems
-    ms = syn.batch_problem_sizes(n, seed)
-    grids = {int(m): mg.Grid(2, int(m)) for m in sorted(set(ms.tolist()))}
     t0 = time.perf_counter()
-    probs = []
-    for i, m in enumerate(ms.tolist()):
-        g = grids[m]
-        eps = syn.lognormal_grf_eps(m, 2, sigma=2.0, seed=1000 + i)
-        b = g.to_slots(m, syn.uniform_load(m, 2, 2000 + i))
-        probs.append((g, m, torch.from_numpy(g.cells_to_concat({m: eps})).cuda(), torch.from_numpy(b).cuda()))
+    ms, probs = batched_problems(mg, torch, n, seed)
     t_inputs = time.perf_counter() - t0
-    total_dofs = sum(g.info(m).n_dofs for g, m, _, _ in probs)
-    out = {"workload": f"batch{n}-2d", "problems": n, "dofs": total_dofs, "inputs_s": t_inputs,
-           "sizes": {str(3**m): int((ms == m).sum()) for m in sorted(set(ms.tolist()))}}
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
-    for prec in ("mixed_bf16", "fp64"):
-        Hs = [mg.Hierarchy(g, precision=prec) for g, m, _, _ in probs]
-        us = [torch.zeros_like(b) for _, _, _, b in probs]
-        bs = [b for _, _, _, b in probs]
-
-        for H, (_, _, e, _) in zip(Hs, probs):
-            H.setup(e)
-        batch = mg.Batch(Hs)
-        eps_list = [e for _, _, e, _ in probs]
-
-        def setup_all():
-            batch.setup(eps_list)
-
-        batch.solve(us, bs, rel_tol=1e-10, max_cycles=3000)  # warm-up (graph capture)
-        times, setups = [], []
-        for _ in range(max(1, args.steps)):
-            flush.zero_()
-            torch.cuda.synchronize()
-            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
-            e0.record()
-            setup_all()
-            e1.record()
-            status, stats = batch.solve(us, bs, rel_tol=1e-10, max_cycles=3000)
-            e2.record()
-            torch.cuda.synchronize()
-            times.append(e0.elapsed_time(e2))
-            setups.append(e0.elapsed_time(e1))
-        t = statistics.median(times) / 1e3
-        cyc = [s["cycles"] for s in stats]
-        out[prec] = {"solves_per_s": n / t, "dof_per_s": total_dofs / t, "s_per_batch": t,
-                     "setup_s": statistics.median(setups) / 1e3, "status": status,
-                     "cycles_median": statistics.median(cyc), "cycles_max": max(cyc),
-                     "max_rel_residual": max(s["rel_residual"] for s in stats)}
-        del batch, Hs
-        torch.cuda.empty_cache()
-    out["mixed_speedup"] = out["mixed_bf16"]["solves_per_s"] / out["fp64"]["solves_per_s"]
+    with Clocks(0) as clk:
+        res = batched_solves(mg, torch, probs, args.steps, flush)
+    out = {"workload": f"batch{n}-2d", "inputs_s": t_inputs,
+           "sizes": {str(3**m): int((ms == m).sum()) for m in sorted(set(ms.tolist()))}, **res,
+           "clocks": clk.summary()}
     print(json.dumps(out))
 
 
-def run_serve(args, seed=4):
-    """Served workload: Poisson arrivals (mean 200 req/s) of 3D solves with edges
-    {27, 81, 243} cells (weights 6:3:1), log-normal eps (sigma 1.5, correlation length
-    0.1), f ~ U[-1,1], tolerance 1e-8 each, mixed precision, served by mg_server with
-    an HBM budget; reports solves/s and p50 / p99 latency from submission."""
-    import torch
-
-    import paper_1607_00648_gb300 as mg
-
-    torch.cuda.set_device(0)
-    n = args.serve_requests
-    arrivals, levels = syn.poisson_arrivals(n, 200.0, seed)
+def served_requests(mg, torch, n, rate, seed=4):
+    """The served workload's first n requests: Poisson arrivals at `rate` per second
+    (seed 4), 3D edges {27, 81, 243} cells weighted 6:3:1, log-normal eps (sigma 1.5,
+    correlation length 0.1, seed 1000+i), f ~ U[-1,1] (seed 2000+i), built on the GPU."""
+    arrivals, levels = syn.poisson_arrivals(n, rate, seed)
     grids = {int(L): mg.Grid(3, int(L)) for L in sorted(set(levels.tolist()))}
     reqs = []
-    t0 = time.perf_counter()
     for i, L in enumerate(levels.tolist()):
         g = grids[L]
         inf = g.info(L)
@@ -834,36 +857,77 @@ def run_serve(args, seed=4):
         f = torch.rand(inf.n_slots, generator=gen, device="cuda", dtype=torch.float64) * 2 - 1
         dof = torch.from_numpy(g.dof_mask(L)).cuda()
         b = torch.where(dof, f * (3.0**-L) ** 3, torch.zeros_like(f))
-        reqs.append((g, L, cat, b, torch.zeros_like(b)))
+        reqs.append((g, L, cat, b))
     torch.cuda.synchronize()
-    t_inputs = time.perf_counter() - t0
-    budget = int(args.serve_budget_gb * (1 << 30))
-    sv = mg.Server(budget, precision="mixed_bf16")
+    return arrivals, levels, reqs
+
+
+def serve_stream(mg, torch, reqs, arrivals, levels, precision, budget, tol=1e-8):
+    """Submit the requests at their arrival times (scaled to the stream's rate) to an
+    mg_server of the given precision; latency from submission to completion."""
+    us = [torch.zeros_like(b) for _, _, _, b in reqs]
+    sv = mg.Server(budget, precision=precision)
     start = time.perf_counter()
     tickets = []
-    for (g, L, e, b, u), ta in zip(reqs, arrivals.tolist()):
+    for (g, L, e, b), u, ta in zip(reqs, us, arrivals.tolist()):
         now = time.perf_counter() - start
         if ta > now:
             time.sleep(ta - now)
-        tickets.append(sv.submit(g, e, b, u, rel_tol=1e-8, max_cycles=2000))
+        tickets.append(sv.submit(g, e, b, u, rel_tol=tol, max_cycles=2000))
     res = [sv.poll(t, wait=True) for t in tickets]
     wall = time.perf_counter() - start
     sv.close()
+    del us
     lat = sorted(r["latency_ms"] for r in res)
     by_edge = {}
     for L in sorted(set(levels.tolist())):
         ls = sorted(r["latency_ms"] for r, lv in zip(res, levels.tolist()) if lv == L)
         by_edge[str(3**L)] = {"n": len(ls), "p50_ms": ls[len(ls) // 2],
                               "p99_ms": ls[min(len(ls) - 1, int(0.99 * len(ls)))]}
-    dofs = sum(g.info(L).n_dofs for g, L, _, _, _ in reqs)
-    out = {"workload": f"serve{n}-3d", "requests": n, "solves_per_s": n / wall, "dof_per_s": dofs / wall,
-           "p50_ms": lat[len(lat) // 2], "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
-           "max_ms": lat[-1], "wall_s": wall, "arrival_span_s": float(arrivals[-1]), "inputs_s": t_inputs,
-           "failed": sum(1 for r in res if r["status"] != 0),
-           "max_rel_residual": max(r["rel_residual"] for r in res), "budget_gb": args.serve_budget_gb,
-           "sizes": {str(3**L): int((levels == L).sum()) for L in sorted(set(levels.tolist()))},
-           "latency_by_edge": by_edge}
-    print(json.dumps(out))
+    n = len(reqs)
+    return {"solves_per_s": n / wall, "dof_per_s": sum(g.info(L).n_dofs for g, L, _, _ in reqs) / wall,
+            "p50_ms": lat[len(lat) // 2], "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+            "max_ms": lat[-1], "wall_s": wall, "arrival_span_s": float(arrivals[-1]),
+            "failed": sum(1 for r in res if r["status"] != 0),
+            "max_rel_residual": max(r["rel_residual"] for r in res), "latency_by_edge": by_edge}
+
+
+def served_summary(mg, torch, n, rate, budget_gb):
+    """Both arms (mixed, FP64) at the offered rate, then both at a rate one GPU sustains:
+    half the requests per second the mixed arm completed under the offered load."""
+    budget = int(budget_gb * (1 << 30))
+    arrivals, levels, reqs = served_requests(mg, torch, n, rate)
+    out = {"requests": n, "budget_gb": budget_gb,
+           "sizes": {str(3**L): int((levels == L).sum()) for L in sorted(set(levels.tolist()))}}
+    offered = {}
+    for prec in ("mixed_bf16", "fp64"):
+        offered[prec] = serve_stream(mg, torch, reqs, arrivals, levels, prec, budget)
+    out["offered"] = {"rate_per_s": rate, **offered,
+                      "mixed_speedup": offered["mixed_bf16"]["solves_per_s"] / offered["fp64"]["solves_per_s"]}
+    sustain = max(1.0, round(0.5 * min(offered["mixed_bf16"]["solves_per_s"], rate), 1))
+    arr_s = arrivals * (rate / sustain)  # the same stream, stretched to the sustainable rate
+    sus = {}
+    for prec in ("mixed_bf16", "fp64"):
+        sus[prec] = serve_stream(mg, torch, reqs, arr_s, levels, prec, budget)
+    out["sustainable"] = {"rate_per_s": sustain,
+                          "rule": "half the solves/s the mixed arm completed under the offered rate", **sus}
+    return out
+
+
+def run_serve(args, seed=4):
+    """Served workload: Poisson arrivals (mean 200 req/s) of 3D solves with edges
+    {27, 81, 243} cells (weights 6:3:1), log-normal eps (sigma 1.5, correlation length
+    0.1), f ~ U[-1,1], tolerance 1e-8 each, served by mg_server with an HBM budget, mixed
+    and FP64 arms; reports solves/s and p50 / p99 latency from submission, at the offered
+    rate and at a rate one GPU sustains."""
+    import torch
+
+    import paper_1607_00648_gb300 as mg
+
+    torch.cuda.set_device(0)
+    with Clocks(0) as clk:
+        res = served_summary(mg, torch, args.serve_requests, args.serve_rate, args.serve_budget_gb)
+    print(json.dumps({"workload": f"serve{args.serve_requests}-3d", **res, "clocks": clk.summary()}))
 
 
 def cpu_baseline(w, gpu_cycles, sample_cycles=15):
@@ -947,6 +1011,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="checker2d-l6", choices=sorted(WORKLOADS) + sorted(ADAPTIVE))
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline leg")
+    ap.add_argument("--no-a13", action="store_true",
+                    help="skip the reduced batched and served measurements of the default line")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default slab depths (no mg_autotune)")
     ap.add_argument("--precision", default="both", choices=("both", "fp64", "mixed", "bpa"),
                     help="which solve forms to time (profiling runs; the default times both; "
@@ -962,6 +1028,7 @@ def main():
     ap.add_argument("--serve", action="store_true", help="a Poisson stream of 3D solve requests through mg_server: p50 / p99 latency")
     ap.add_argument("--serve-requests", type=int, default=300)
     ap.add_argument("--serve-budget-gb", type=float, default=64.0)
+    ap.add_argument("--serve-rate", type=float, default=200.0, help="offered arrivals per second")
     ap.add_argument("--batch-size", type=int, default=0)
     ap.add_argument("--breakdown", action="store_true",
                     help="per-kernel device time of one setup + solve of the workload (torch.profiler trace)")

@@ -19,8 +19,13 @@ static void sweep_b(SweepArgs<T> a, int op, int amode, cudaStream_t s) {
     // as a template parameter so every plane's loads are issued together
     const dim3 grid(static_cast<unsigned>(sweep_ctas_x(DIM, B, T(0), a.L.n_bricks)), static_cast<unsigned>(B / R));
     const size_t sm = DIM == 2 ? 0 : sweep_tile_bytes<DIM, T>(B, R, true);
-    // 2D: 16-byte staging needs u and eps 16-byte aligned (user vectors may be offset views)
-    const bool v16 = ((reinterpret_cast<uintptr_t>(a.u) | reinterpret_cast<uintptr_t>(a.eps)) & 15) == 0;
+    // 2D: the 16-byte-staged column-marching kernel where the level's vectors exceed L2
+    // (2D level 7 and finer: 2.64 -> 3.84 TB/s on level 7); on L2-resident levels the
+    // row-interleaved kernel is faster (its warps are independent: 4.9 against 8.8 us on
+    // level 6).  16-byte staging needs u and eps 16-byte aligned (user vectors may be
+    // offset views).
+    const bool v16 = a.L.n_bricks >= 2048 &&
+                     ((reinterpret_cast<uintptr_t>(a.u) | reinterpret_cast<uintptr_t>(a.eps)) & 15) == 0;
 #define MG_SWR(AM, OP, RR)                                                                \
   do {                                                                                    \
     if constexpr (DIM == 2) {                                                             \

@@ -4,10 +4,11 @@
 // (footprint computed from the grid and the options); admitted requests get a
 // hierarchy, are set up on a pool of streams, and join a running batch at its next
 // step boundary, so work from requests that arrived while others were on the GPU
-// overlaps with theirs on the device.  Requests run in two lanes by size, each a
-// batch on its own stream: the lane of small problems takes many short steps while
-// a step of the large problems is still on the GPU, so a small request is not held
-// to the pace of the largest ones.  After every step of a lane (an FP64 cycle, or a
+// overlaps with theirs on the device.  Requests run in three lanes by size (finest
+// level under 2^16 DoFs, under 2^20, larger), each a batch on its own stream at its
+// own priority (the smallest highest): a lane of small problems takes many short steps
+// while a step of larger problems is still on the GPU, so a small request is held
+// neither to the pace of the largest ones nor to that of mid-sized ones.  After every step of a lane (an FP64 cycle, or a
 // refinement step with its inner FP32 cycles) its converged requests retire: their
 // statistics are recorded, their hierarchy is released and its budget returns to the
 // queue.  The per-request arithmetic is that of a batch, so a request's result does
@@ -44,7 +45,7 @@ struct Request {
   size_t footprint = 0;
   Hier* h = nullptr;
   int state = 0;  // 0 queued, 1 setting up, 2 running, 3 done
-  int lane = 0;   // 0 small, 1 large problems
+  int lane = 0;   // 0 small, 1 mid-sized, 2 large problems
   // done but still a member of its lane's batch (inactive there): its hierarchy and
   // budget are released when the batch is next re-formed; abandoned: the caller has
   // collected the result meanwhile, so the server deletes the request then
@@ -70,21 +71,21 @@ struct Server {
   bool stop = false;
   std::string error;
   std::thread th;
-  // setup streams per lane; the small lane's streams (setups and steps) run at the
-  // device's highest priority so that their short kernels are not queued behind the
-  // large problems' long ones
+  // setup streams per lane; a smaller lane's streams (setups and steps) run at a higher
+  // priority so that their short kernels are not queued behind larger problems' long ones
+  static constexpr int kLanes = 3;
   static constexpr int kSetupStreams = 4;
-  cudaStream_t setup_streams[2][kSetupStreams] = {};
-  std::atomic<int> next_setup[2] = {0, 0};
+  cudaStream_t setup_streams[kLanes][kSetupStreams] = {};
+  std::atomic<int> next_setup[kLanes] = {0, 0, 0};
   std::vector<Request*> pending;  // set up enqueued, waiting for its event (mu)
   // hierarchy creation and setup enqueue run on one worker thread per lane, so that
   // host-side waits of a creation hold back neither the stepping of running batches
   // nor the small requests behind a large one
-  std::deque<Request*> to_create[2];  // admitted, not yet created (mu)
-  int creating = 0;                   // requests inside a worker between the two lists (mu)
-  static constexpr int kWorkers[2] = {3, 1};  // the small lane's creations run three at a time
-  std::thread workers[2][3];
-  int prio[2] = {0, 0};               // stream priorities of the lanes (small: highest)
+  std::deque<Request*> to_create[kLanes];  // admitted, not yet created (mu)
+  int creating = 0;                        // requests inside a worker between the two lists (mu)
+  static constexpr int kWorkers[kLanes] = {3, 2, 1};  // the small lane's creations run three at a time
+  std::thread workers[kLanes][3];
+  int prio[kLanes] = {0, 0, 0};            // stream priorities of the lanes (smallest: highest)
   void worker(int lane);
   // a batch of running requests with its own stream; at most one step in flight
   struct Lane {
@@ -98,7 +99,7 @@ struct Server {
   // a batch is re-formed (new members join, finished ones leave) at most this often
   // while it still has running members: re-forming rebuilds its tables
   static constexpr std::chrono::milliseconds kReformEvery{25};
-  static constexpr int kLanes = 2;
+  static constexpr int64_t kMidDofs = int64_t(1) << 16;    // finest-level DoFs of a mid-sized problem
   static constexpr int64_t kLargeDofs = int64_t(1) << 20;  // finest-level DoFs of a large problem
   Lane lanes[kLanes];
 
@@ -292,7 +293,7 @@ bool Server::start_step(Lane& ln, int lane) {
       init.push_back(ps);
       fresh.push_back(std::find(old.begin(), old.end(), r) == old.end() ? 1 : 0);
     }
-    mg_status st = batch_create(hs, &ln.batch, prio[&ln == &lanes[0] ? 0 : 1], false);
+    mg_status st = batch_create(hs, &ln.batch, prio[lane], false);
     if (st == MG_OK) batch_set_graph(ln.batch, false);
     if (st == MG_OK) st = batch_begin(*ln.batch, us.data(), bs.data(), init, fresh, ln.stream);
     if (st != MG_OK) {
@@ -386,12 +387,13 @@ mg_status mg_server_create(size_t hbm_budget_bytes, const mg_options* opt, mg_se
     mg_default_options(&sv->opt);
   cudaGetDevice(&sv->device);
   int prio_low = 0, prio_high = 0;
-  cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high);
+  cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high);  // a numerically lower value is a higher priority
   sv->prio[0] = prio_high;
-  sv->prio[1] = prio_low;
+  sv->prio[1] = prio_high < prio_low ? prio_high + 1 : prio_low;
+  sv->prio[2] = prio_low;
   bool ok = true;
   for (int k = 0; k < Server::kLanes && ok; ++k) {
-    const int prio = k == 0 ? prio_high : prio_low;
+    const int prio = sv->prio[k];
     ok = cudaStreamCreateWithPriority(&sv->lanes[k].stream, cudaStreamNonBlocking, prio) == cudaSuccess &&
          cudaEventCreateWithFlags(&sv->lanes[k].done, cudaEventDisableTiming) == cudaSuccess;
     for (int i = 0; i < Server::kSetupStreams && ok; ++i)
@@ -404,7 +406,7 @@ mg_status mg_server_create(size_t hbm_budget_bytes, const mg_options* opt, mg_se
   }
   try {
     sv->th = std::thread([sv] { sv->loop(); });
-    for (int k = 0; k < 2; ++k)
+    for (int k = 0; k < Server::kLanes; ++k)
       for (int w = 0; w < Server::kWorkers[k]; ++w) sv->workers[k][w] = std::thread([sv, k] { sv->worker(k); });
   } catch (...) {
     {
@@ -413,7 +415,7 @@ mg_status mg_server_create(size_t hbm_budget_bytes, const mg_options* opt, mg_se
       sv->cv.notify_all();
     }
     if (sv->th.joinable()) sv->th.join();
-    for (int k = 0; k < 2; ++k)
+    for (int k = 0; k < Server::kLanes; ++k)
       for (auto& t : sv->workers[k])
         if (t.joinable()) t.join();
     delete sv;
@@ -448,7 +450,8 @@ mg_status mg_server_submit(mg_server* server, const mg_request* req, uint64_t* t
   r->tol = req->rel_tol;
   r->max_cycles = req->max_cycles;
   r->footprint = hier_footprint(*g, sv->opt);
-  r->lane = g->levels[g->L].n_dofs >= Server::kLargeDofs ? 1 : 0;
+  const int64_t nd = g->levels[g->L].n_dofs;
+  r->lane = nd >= Server::kLargeDofs ? 2 : nd >= Server::kMidDofs ? 1 : 0;
   if (r->footprint > sv->budget) {
     delete r;
     set_error("mg_server_submit: the request's hierarchy (" + std::to_string(hier_footprint(*g, sv->opt)) +
@@ -521,7 +524,7 @@ void mg_server_destroy(mg_server* server) {
     sv->cv.notify_all();
   }
   if (sv->th.joinable()) sv->th.join();
-  for (int k = 0; k < 2; ++k)
+  for (int k = 0; k < Server::kLanes; ++k)
     for (auto& t : sv->workers[k])
       if (t.joinable()) t.join();
   cudaSetDevice(sv->device);

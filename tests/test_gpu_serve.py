@@ -20,21 +20,28 @@ from tests.gpu_common import lib, rel_inf
 pytestmark = pytest.mark.gpu
 
 
-def _req(mg, torch, L, seed):
-    eps = syn.lognormal_grf_eps(L, 2, sigma=1.5, seed=1000 + seed)
-    g = mg.Grid(2, L)
-    b = g.to_slots(L, syn.uniform_load(L, 2, 2000 + seed))
-    return dict(L=L, g=g, eps=eps, eps_dev=torch.from_numpy(g.cells_to_concat({L: eps})).cuda(), b=b,
+def _req(mg, torch, L, seed, dim=2):
+    eps = syn.lognormal_grf_eps(L, dim, sigma=1.5, seed=1000 + seed)
+    g = mg.Grid(dim, L)
+    b = g.to_slots(L, syn.uniform_load(L, dim, 2000 + seed))
+    return dict(L=L, dim=dim, g=g, eps=eps, eps_dev=torch.from_numpy(g.cells_to_concat({L: eps})).cuda(), b=b,
                 b_dev=torch.from_numpy(b).cuda())
 
 
+# 2D: levels 3..5 (676 .. 58,564 DoFs); 3D: the served workload's shape at sizes the
+# oracle checks quickly, levels 2..4 (512, 17,576 and 512,000 DoFs: two of the server's
+# size lanes, the largest in the lane of mid-sized problems)
+SHAPES = {2: [4, 3, 5, 3, 4, 5, 3], 3: [3, 2, 4, 3, 2, 3, 3]}
+
+
+@pytest.mark.parametrize("dim", [2, 3])
 @pytest.mark.parametrize("precision", ["fp64", "mixed_bf16"])
-def test_served_results_equal_solo_results(precision):
+def test_served_results_equal_solo_results(precision, dim):
     mg = lib()
     import torch
 
-    levels = [4, 3, 5, 3, 4, 5, 3]
-    reqs = [_req(mg, torch, L, i) for i, L in enumerate(levels)]
+    levels = SHAPES[dim]
+    reqs = [_req(mg, torch, L, i, dim) for i, L in enumerate(levels)]
     # budget for about two of the largest requests at a time: the rest must queue
     budget = int(2.5 * mg.hier_footprint(reqs[2]["g"], precision=precision))
     sv = mg.Server(budget, precision=precision)
@@ -58,8 +65,12 @@ def test_served_results_equal_solo_results(precision):
         else:
             mg.Batch([H]).solve([u1], [r["b_dev"]], rel_tol=1e-10, max_cycles=2000)
         assert rel_inf(u.cpu().numpy(), u1.cpu().numpy()) < 1e-12
-        O = multigrid.Hierarchy(stt.Spacetree(2, r["L"]), {r["L"]: r["eps"]})
-        assert rel_inf(u.cpu().numpy(), O.direct(r["b"])) < 1e-8
+        O = multigrid.Hierarchy(stt.Spacetree(dim, r["L"]), {r["L"]: r["eps"]})
+        ug = u.cpu().numpy()
+        if dim == 2 or r["L"] <= 3:
+            assert rel_inf(ug, O.direct(r["b"])) < 1e-8
+        else:  # 512,000 unknowns: the oracle's FP64 residual of the served result instead
+            assert np.linalg.norm(O.residual(r["L"], ug, r["b"])) <= 1.0001e-10 * np.linalg.norm(r["b"])
 
 
 def test_server_rejects_requests_beyond_its_budget():
