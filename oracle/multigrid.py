@@ -38,12 +38,49 @@ class LevelOps:
     extra: dict = field(default_factory=dict)
 
 
+# Dynamic coarsest level (Sect. 4.3): the paper starts from the coarsest level 1 and
+# raises it (a) at once when a Galerkin computation gives a coarse stencil that is not
+# diagonally dominant or has a non-positive diagonal, (b) between two cycles when the
+# residual stagnates or grows.  Readings: dominance is checked on the operator over the
+# unknowns (entries towards Dirichlet vertices multiply 0), with a relative rounding
+# allowance; (a) makes the coarsest level the one above the finest failing level; (b)
+# raises it by one level after a cycle whose residual contraction exceeds STALL.
+AUDIT_REL = 1e-12
+STALL = 0.95
+
+
+def audit_rows(A: sp.csr_matrix, dof: np.ndarray) -> np.ndarray:
+    """Per slot: True where a DoF row of A (over DoF columns) has a non-positive
+    diagonal or sum |off-diagonal| > (1 + AUDIT_REL) |diagonal| (not diagonally dominant)."""
+    A = A.tocsr()
+    diag = np.asarray(A.diagonal())
+    absum = np.asarray(abs(A).sum(axis=1)).ravel()
+    off = absum - np.abs(diag)
+    fail = (diag <= 0.0) | (off > (1.0 + AUDIT_REL) * np.abs(diag))
+    return fail & dof
+
+
+def raised_coarsest(failing_levels, coarsest: int) -> int:
+    """Rule (a): one level above the finest level whose audit failed (or unchanged)."""
+    return max([coarsest] + [lv + 1 for lv in failing_levels])
+
+
+def stalled(hist) -> bool:
+    """Rule (b): the last cycle contracted the residual by less than a factor 1/STALL."""
+    return len(hist) >= 2 and hist[-2] > 0 and hist[-1] > STALL * hist[-2]
+
+
 class Hierarchy:
-    """Operators of a uniform spacetree hierarchy (levels ``coarsest`` .. max_level)."""
+    """Operators of a uniform spacetree hierarchy (levels ``coarsest`` .. max_level).
+
+    dynamic_coarsest: apply the Sect. 4.3 rules above, with the coarsest level kept at
+    most max_coarse_dofs unknowns (it is solved directly); a raise beyond that, or to the
+    finest level, raises ValueError (no admissible coarsest level)."""
 
     def __init__(self, tree: Spacetree, leaf_eps: dict[int, np.ndarray], transfer: str = "boxmg",
                  coarse: str = "galerkin", omega: float = 0.6, nu1: int = 2, nu2: int = 2,
-                 coarsest: int = 1, smoother: str = "jacobi", gs_sweeps: int = 1):
+                 coarsest: int = 1, smoother: str = "jacobi", gs_sweeps: int = 1,
+                 dynamic_coarsest: bool = False, max_coarse_dofs: int = 1024):
         self.tree, self.omega, self.nu1, self.nu2, self.coarsest = tree, omega, nu1, nu2, coarsest
         self.smoother, self.gs_sweeps = smoother, gs_sweeps
         self.transfer, self.coarse = transfer, coarse
@@ -71,10 +108,23 @@ class Hierarchy:
             if lv > coarsest:
                 ops.P = boxmg.prolongation(tree, lv, st, kind=transfer)
                 ops.p_hat = galerkin.p_delta(tree, lv, ops.P)
-        c = self.ops[coarsest]
-        idx = np.nonzero(c.dof)[0]
+        self.dynamic, self.max_coarse_dofs = dynamic_coarsest, max_coarse_dofs
+        if dynamic_coarsest:
+            failing = [lv for lv in range(coarsest, L) if audit_rows(self.ops[lv].A, self.ops[lv].dof).any()]
+            self.failing_levels = failing
+            self.set_coarsest(raised_coarsest(failing, coarsest))
+        else:
+            self.set_coarsest(coarsest)
+
+    def set_coarsest(self, c: int) -> None:
+        """Solve level c directly from now on (levels below it are left out)."""
+        if c >= self.L or int(self.ops[c].dof.sum()) > self.max_coarse_dofs and self.dynamic:
+            raise ValueError(f"no admissible coarsest level: level {c} of {self.L}")
+        self.coarsest = c
+        o = self.ops[c]
+        idx = np.nonzero(o.dof)[0]
         self._coarse_idx = idx
-        self._coarse_dense = c.A[idx][:, idx].toarray()
+        self._coarse_dense = o.A[idx][:, idx].toarray()
 
     # --- single steps -----------------------------------------------------
     def smooth(self, lv: int, u: np.ndarray, b: np.ndarray, nu: int) -> np.ndarray:
@@ -162,6 +212,9 @@ class Hierarchy:
                 break
             u = self.vcycle(u, b)
             hist.append(np.linalg.norm(self.residual(self.L, u, b)))
+            if self.dynamic and stalled(hist) and self.coarsest + 1 < self.L and \
+                    int(self.ops[self.coarsest + 1].dof.sum()) <= self.max_coarse_dofs:
+                self.set_coarsest(self.coarsest + 1)  # rule (b), before the next cycle
         return u, np.array(hist)
 
     # --- additive multigrid (Alg. 2) --------------------------------------
