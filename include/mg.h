@@ -178,6 +178,21 @@ typedef struct mg_options {
   int32_t smoother;       /* mg_smoother (default MG_SMOOTH_JACOBI); nu1, nu2 count its steps */
   int32_t gs_sweeps;      /* MG_SMOOTH_BLOCK: Gauss-Seidel sweeps per patch and step, 1..64 (default 1) */
   int32_t cycle;          /* mg_cycle (default MG_CYCLE_V); mg_vcycle runs one traversal of it */
+  int32_t dynamic_coarsest; /* 1: the dynamic coarsest level of Sect. 4.3 (uniform grids, single
+                             hierarchies; default 0).  mg_setup audits every coarse level: a level
+                             with a DoF row whose diagonal is not positive or whose off-diagonal
+                             magnitudes over the unknowns exceed the diagonal (beyond a relative
+                             1e-12) makes the level above it the coarsest one; mg_solve (FP64)
+                             raises the coarsest level by one after a cycle that reduces the
+                             residual by less than a factor 1/0.95.  The coarsest level stays at
+                             most 1024 unknowns (it is solved directly): a raise beyond that, or to
+                             the finest level, makes mg_setup return MG_ERR_INDEFINITE_COARSE.
+                             mg_get_coarsest reports the level in use */
+  int32_t tensor_coefficients; /* 1: the hierarchy takes diagonal-tensor coefficients eps = diag(eps_i)
+                             through mg_setup_tensor (the paper's `checkerboard` benchmark, Sect. 7;
+                             default 0).  Uniform grids, Galerkin coarse operators, Jacobi smoother,
+                             single hierarchies (not batches, the server, the persistent solve or
+                             the bpa codec) */
 } mg_options;
 
 void mg_default_options(mg_options* opt); /* BoxMG, Galerkin, FP64, V(2,2), omega 0.6, coarsest 1, eps_mf 1e-4,
@@ -211,6 +226,20 @@ mg_status mg_hier_footprint(const mg_grid* grid, const mg_options* opt, size_t* 
  * diagonal or the coarsest Cholesky fails (Sect. 4.3 definiteness check);
  * MG_ERR_NONFINITE if a delta cannot be stored in the bpa codec. */
 mg_status mg_setup(mg_hier* h, const double* eps, void* stream);
+
+/* Setup for a diagonal-tensor coefficient eps = diag(eps_1, .., eps_d) per leaf cell
+ * (eq. "pde" with a diagonal diffusion tensor; the paper's `checkerboard` benchmark,
+ * Sect. 7, Table "parameters"), for hierarchies created with tensor_coefficients = 1.
+ * eps_axes: device, d level-concatenated cell arrays one after the other (axis i at
+ * eps_axes + i * n, n = sum of n_slots over levels 0..L, layout as mg_setup's eps).
+ * The finest level's stencils are rebuilt in situ from the per-cell mean of eps_i plus
+ * the anisotropic part (per pair of corners, 2D: -d_x/2 for corners differing in x only,
+ * +d_x/2 for those differing in y only; 3D, times h: -d_i/6 along axis i, +d_k/12 for
+ * corners differing in the two axes other than k; d_i = eps_i - mean), applied by a
+ * correction pass after every finest-level sweep; coarse levels carry the anisotropy in
+ * their Galerkin operators (A_hat).  mg_setup on such a hierarchy sets eps_i = eps for
+ * all i.  Errors as mg_setup. */
+mg_status mg_setup_tensor(mg_hier* h, const double* eps_axes, void* stream);
 
 /* ---------------------------------------------------------------- A3-A7 steps (FP64) */
 
@@ -251,14 +280,18 @@ mg_status mg_vcycle_f32(mg_hier* h, float* u, const float* b, void* stream); /* 
  * must not call cudaMalloc: code running under a fixed device-memory budget handed
  * out by a host framework, or latency-critical loops where an allocation call could
  * block on work already queued on the GPU.  The hierarchy h is created beforehand.
- * The reduction's per-brick partial sums live in a file-scope device array of 4096
+ * The reduction's per-CTA partial sums live in a file-scope device array of 4096
  * doubles (32 KiB, held by every GPU that loads the library until the process
- * exits); levels with more than 4096 bricks are rejected with MG_ERR_INVALID_ARG
- * (2D up to level 6 and 3D up to level 4 fit).  The first call on a device looks
+ * exits); a level whose sweep needs more than 4096 per-CTA partial sums (bricks x
+ * slabs) is rejected with MG_ERR_INVALID_ARG (2D up to level 6 and 3D up to level 4
+ * fit).  The first call on a device looks
  * up that array's device address (cudaGetSymbolAddress) with the device current;
  * make that first call before any stream capture.  Every call on a device shares
  * the one array, so calls whose kernels overlap on the GPU (concurrent streams)
- * race; serialise them.  u, b, r: device vectors of n_slots; norm2: device. */
+ * race; serialise them.  *norm2 agrees with mg_residual's norm to about 1e-15
+ * relative (the partial sums are added with another stride), not bit for bit.  The
+ * finest level of a tensor-coefficient hierarchy is rejected (MG_ERR_UNSUPPORTED).
+ * u, b, r: device vectors of n_slots; norm2: device. */
 mg_status mg_residual_norm_noalloc(mg_hier* h, int level, const double* u, const double* b, double* r,
                                    double* norm2, void* stream);
 
@@ -453,6 +486,10 @@ mg_status mg_bpa_decode(int64_t n, int32_t k, const uint64_t* rec, const uint8_t
  * Buffers hold n_slots records and n_slots * 3^d * 8 (5^d * 8) bytes.  Synchronises. */
 mg_status mg_get_bpa(mg_hier* h, int level, uint64_t* a_rec, uint8_t* a_stream, uint64_t* p_rec, uint8_t* p_stream,
                      uint64_t* a_bytes, uint64_t* p_bytes, void* stream);
+
+/* The level a hierarchy currently solves directly (host *level): the coarsest_level of
+ * its options, or the level the dynamic rule (mg_options.dynamic_coarsest) chose. */
+mg_status mg_get_coarsest(mg_hier* h, int32_t* level);
 
 void mg_destroy_hier(mg_hier* h);
 

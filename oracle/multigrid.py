@@ -113,6 +113,7 @@ class Hierarchy:
             failing = [lv for lv in range(coarsest, L) if audit_rows(self.ops[lv].A, self.ops[lv].dof).any()]
             self.failing_levels = failing
             self.set_coarsest(raised_coarsest(failing, coarsest))
+            self.setup_coarsest = self.coarsest
         else:
             self.set_coarsest(coarsest)
 
@@ -203,7 +204,10 @@ class Hierarchy:
         return self.smooth(lv, u, b, self.nu2)
 
     def solve(self, b: np.ndarray, rel_tol: float = 1e-10, max_cycles: int = 100):
-        """V-cycles from u = 0 until ||r||_2 / ||r_0||_2 <= rel_tol; returns (u, history)."""
+        """V-cycles from u = 0 until ||r||_2 / ||r_0||_2 <= rel_tol; returns (u, history).
+        With the dynamic coarsest level every solve starts from the level of rule (a)."""
+        if self.dynamic and self.coarsest != self.setup_coarsest:
+            self.set_coarsest(self.setup_coarsest)
         u = np.zeros_like(b)
         r0 = np.linalg.norm(self.residual(self.L, u, b))
         hist = [r0]

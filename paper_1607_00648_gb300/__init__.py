@@ -171,6 +171,10 @@ class Hierarchy:
     def setup(self, eps, stream=None):
         check(load().mg_setup(self._h, _dptr(eps), _stream_ptr(stream)), "mg_setup")
 
+    def setup_tensor(self, eps_axes, stream=None):
+        """mg_setup_tensor: eps_axes (d * n,) device FP64, one level-concatenated array per axis."""
+        check(load().mg_setup_tensor(self._h, _dptr(eps_axes), _stream_ptr(stream)), "mg_setup_tensor")
+
     def smooth(self, level, u, b, nu, stream=None):
         check(load().mg_smooth(self._h, level, _dptr(u), _dptr(b), nu, _stream_ptr(stream)), "mg_smooth")
 
@@ -240,6 +244,12 @@ class Hierarchy:
         f = lambda t: _dptr(t) if t is not None else None
         check(load().mg_get_codes(self._h, level, f(a_codes), f(a_scale), f(p_codes), f(p_scale),
                                   _stream_ptr(stream)), "mg_get_codes")
+
+    def coarsest(self) -> int:
+        """The level this hierarchy solves directly (after the dynamic rule, if enabled)."""
+        c = C.c_int32()
+        check(load().mg_get_coarsest(self._h, C.byref(c)), "mg_get_coarsest")
+        return int(c.value)
 
     def get_code_lo(self, level, a_lo, stream=None):
         check(load().mg_get_code_lo(self._h, level, _dptr(a_lo), _stream_ptr(stream)), "mg_get_code_lo")

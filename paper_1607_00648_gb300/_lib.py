@@ -38,7 +38,8 @@ class Options(C.Structure):
                 ("nu1", C.c_int32), ("nu2", C.c_int32), ("omega", C.c_double),
                 ("coarsest_level", C.c_int32), ("inner_cycles", C.c_int32), ("use_graphs", C.c_int32),
                 ("persistent", C.c_int32), ("eps_mf", C.c_double), ("smoother", C.c_int32),
-                ("gs_sweeps", C.c_int32), ("cycle", C.c_int32)]
+                ("gs_sweeps", C.c_int32), ("cycle", C.c_int32), ("dynamic_coarsest", C.c_int32),
+                ("tensor_coefficients", C.c_int32)]
 
 
 class SolveStats(C.Structure):
@@ -67,6 +68,7 @@ _SIGS = {
     "mg_hier_create": (C.c_int, [_P, C.POINTER(Options), C.POINTER(_P)]),
     "mg_hier_footprint": (C.c_int, [_P, C.POINTER(Options), C.POINTER(C.c_size_t)]),
     "mg_setup": (C.c_int, [_P, _P, _P]),
+    "mg_setup_tensor": (C.c_int, [_P, _P, _P]),
     "mg_smooth": (C.c_int, [_P, C.c_int, _P, _P, C.c_int, _P]),
     "mg_residual": (C.c_int, [_P, C.c_int, _P, _P, _P, _F64P, _P]),
     "mg_smooth_f32": (C.c_int, [_P, C.c_int, _P, _P, C.c_int, _P]),
@@ -97,6 +99,7 @@ _SIGS = {
     "mg_server_poll": (C.c_int, [_P, C.c_uint64, C.c_int, C.POINTER(C.c_int), C.POINTER(SolveStats)]),
     "mg_server_info": (C.c_int, [_P, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_size_t)]),
     "mg_server_destroy": (None, [_P]),
+    "mg_get_coarsest": (C.c_int, [_P, C.POINTER(C.c_int32)]),
     "mg_destroy_hier": (None, [_P]),
     "mg_probe_fp64_fma": (C.c_int, [C.c_int64, C.c_int32, _P, C.POINTER(C.c_int64), _P]),
     "mg_last_error": (C.c_char_p, []),

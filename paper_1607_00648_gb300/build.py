@@ -15,7 +15,7 @@ BUILD = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-lineinfo"]
 SOURCES = ["grid.cpp", "solver.cu", "noalloc.cu", "probe.cu", "k2d_f64.cu", "k2d_f32.cu", "k3d_f64.cu", "k3d_f32.cu", "persist_2d_f64.cu", "persist_2d_mixed.cu", "persist_3d_f64.cu", "persist_3d_mixed.cu",
-           "batch.cu", "server.cu", "batch_2d_f64.cu", "batch_2d_f32.cu", "batch_3d_f64.cu", "batch_3d_f32.cu"]
+           "batch.cu", "server.cu", "batch_persist_2d.cu", "batch_persist_3d.cu", "batch_2d_f64.cu", "batch_2d_f32.cu", "batch_3d_f64.cu", "batch_3d_f32.cu"]
 
 
 def _nvcc() -> str:

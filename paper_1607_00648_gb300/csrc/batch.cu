@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "batch_kernels.cuh"
+#include "batch_persist.cuh"
 #include "hier.h"
 
 namespace mg {
@@ -33,6 +34,10 @@ void blaunch_sweep<2, float>(const BatchArgs<float>&, const BatchGroup&, int, in
 template <>
 void blaunch_sweep<3, float>(const BatchArgs<float>&, const BatchGroup&, int, int, int, int, cudaStream_t);
 template <>
+cudaError_t bpersist_launch<2>(const QueueArgs&, int, int, int, int, cudaStream_t);
+template <>
+cudaError_t bpersist_launch<3>(const QueueArgs&, int, int, int, int, cudaStream_t);
+template <>
 void blaunch_transfer<2, double>(const BatchArgs<double>&, const BatchGroup&, bool, int, cudaStream_t);
 template <>
 void blaunch_transfer<3, double>(const BatchArgs<double>&, const BatchGroup&, bool, int, cudaStream_t);
@@ -43,50 +48,10 @@ void blaunch_transfer<3, float>(const BatchArgs<float>&, const BatchGroup&, bool
 
 namespace {
 
-struct BatchState {
-  int* active;
-  int* cycles;
-  int* status;  // 0 converged, 1 not converged, 2 non-finite, 3 diverged
-  double* r0;
-  double* rel;
-  double* sigma;
-  const double* invc;
-  int* n_active;
-  const int2* prange;
-  const double* partial;
-  const double* tol;     // per problem
-  const int* max_cycles; // per problem
-  int inc;
-  int n;
-};
-
 // per-problem convergence test from the partial sums of the norm phase
 __global__ void k_bcheck(BatchState s) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= s.n || !s.active[p]) return;
-  double n2 = 0.0;
-  for (int i = s.prange[p].x; i < s.prange[p].y; ++i) n2 += s.partial[i];
-  double rel;
-  if (s.r0[p] < 0.0) {
-    s.r0[p] = sqrt(n2);
-    rel = s.r0[p] > 0.0 ? 1.0 : 0.0;
-  } else {
-    rel = sqrt(n2) / s.r0[p];
-  }
-  s.rel[p] = rel;
-  int st = -1;
-  if (!(rel == rel) || isinf(rel)) st = 2;
-  else if (rel <= s.tol[p]) st = 0;
-  else if (rel > 1e6) st = 3;
-  else if (s.cycles[p] >= s.max_cycles[p]) st = 1;
-  if (st >= 0) {
-    s.status[p] = st;
-    s.active[p] = 0;
-    return;
-  }
-  s.cycles[p] += s.inc;
-  s.sigma[p] = sqrt(n2 * s.invc[p]);
-  atomicAdd(s.n_active, 1);
+  if (p < s.n) bcheck_one(s, p);
 }
 
 __global__ void k_breset(int* n_active) { *n_active = 0; }
@@ -139,22 +104,7 @@ __global__ void k_bcoarse(const PLevel<T>* lv, const int* cp, const int* active,
                           const int32_t* const* cslots, const int* nc, int n) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= n || !active[p]) return;
-  const PLevel<T>& P = lv[p * kMaxLevels + cp[p]];
-  const double* Lm = chol[p];
-  const int32_t* cs = cslots[p];
-  const int m = nc[p];
-  double y[64];
-  for (int i = 0; i < m; ++i) {
-    double v = static_cast<double>(P.b[cs[i]]);
-    for (int j = 0; j < i; ++j) v -= Lm[i * m + j] * y[j];
-    y[i] = v / Lm[i * m + i];
-  }
-  for (int i = m - 1; i >= 0; --i) {
-    double v = y[i];
-    for (int j = i + 1; j < m; ++j) v -= Lm[j * m + i] * y[j];
-    y[i] = v / Lm[i * m + i];
-  }
-  for (int i = 0; i < m; ++i) P.u[cs[i]] = static_cast<T>(y[i]);
+  bcoarse_one<T>(lv, cp, chol, cslots, nc, p);
 }
 
 }  // namespace
@@ -187,6 +137,15 @@ struct Batch {
   Graph graph;
   bool use_graph = true;  // the server re-forms batches often and launches steps directly
   BatchState state{};
+  // persistent steps (every hierarchy's options.persistent): the step's work queue, its
+  // ticket, the per-problem progress counters, the error word and the norm slots
+  bool persistent = false;
+  QItem* d_queue = nullptr;
+  int n_queue = 0;
+  unsigned* d_head = nullptr;
+  int* d_prog = nullptr;
+  int* d_err = nullptr;
+  int2* d_prange_q = nullptr;
   cudaStream_t own = nullptr;
   int priority = 0;
   bool blocking = true;
@@ -342,6 +301,136 @@ void emit_mixed_step(Batch& bt, const BatchState& st, cudaStream_t s) {
   cudaMemcpyAsync(bt.h_pin, bt.d_nactive, sizeof(int), cudaMemcpyDeviceToHost, s);
 }
 
+// The queue of one step: every problem's phases in the order of emit_fp64_step /
+// emit_mixed_step, merged phase-major (phase k of every problem before phase k + 1 of
+// any); an entry's `need` is the number of its problem's entries in earlier phases.
+struct QueueBuilder {
+  const Batch& bt;
+  std::vector<std::vector<std::vector<QItem>>> ph;  // [problem][phase] entries
+  std::vector<int2> prange;
+  int part = 0;
+  explicit QueueBuilder(const Batch& b) : bt(b), ph(b.n), prange(b.n, make_int2(0, 0)) {}
+  std::vector<QItem>& phase(int p) {
+    ph[p].emplace_back();
+    return ph[p].back();
+  }
+  static int code(int qop, bool f32, int sop = 0, int src = 0, int dst = 0) {
+    return qop | (f32 ? 16 : 0) | (sop << 8) | (src << 12) | (dst << 16);
+  }
+  void sweeps(int p, int l, bool f32, int sop, int src, int dst, bool norm) {
+    const LevelDesc& D = bt.H[p]->lv[l].d;
+    auto& v = phase(p);
+    if (norm) prange[p].x = part;
+    for (int64_t b = 0; b < D.n_bricks; ++b)
+      v.push_back(QItem{code(kQSweep, f32, sop, src, dst), p, l, static_cast<int>(b), 0, norm ? part++ : -1});
+    if (norm) prange[p].y = part;
+  }
+  void chunks(int p, int l, int qop, bool f32, int src = 0, int dst = 0) {
+    const LevelDesc& D = bt.H[p]->lv[l].d;
+    auto& v = phase(p);
+    for (int64_t c = 0; c < (D.n_slots + kBlock - 1) / kBlock; ++c)
+      v.push_back(QItem{code(qop, f32, 0, src, dst), p, l, static_cast<int>(c), 0, -1});
+  }
+  void single(int p, int qop, bool f32) { phase(p).push_back(QItem{code(qop, f32), p, 0, 0, 0, -1}); }
+  // one V-cycle of problem p (emit_cycle's schedule restricted to p)
+  void cycle(int p, bool f32, bool first_done) {
+    const Hier& h = *bt.H[p];
+    const int D = h.L - h.c;
+    for (int j = 0; j < D; ++j) {
+      const int l = h.L - j;
+      int cur = kSelU, oth = kSelT, k0 = 0;
+      if (j == 0 && first_done) {
+        cur = kSelT;
+        oth = kSelU;
+        k0 = 1;
+      }
+      for (int k = k0; k < bt.nu1; ++k) {
+        sweeps(p, l, f32, kJacobi, cur, oth, false);
+        std::swap(cur, oth);
+      }
+      if (cur != kSelU) chunks(p, l, kQCopy, f32, cur, kSelU);
+      sweeps(p, l, f32, kResidual, kSelU, kSelR, false);
+      chunks(p, l - 1, kQRestrict, f32);
+    }
+    single(p, kQCoarse, f32);
+    for (int j = D - 1; j >= 0; --j) {
+      const int l = h.L - j;
+      chunks(p, l, kQProlong, f32);
+      int cur = kSelU, oth = kSelT;
+      for (int k = 0; k < bt.nu2; ++k) {
+        sweeps(p, l, f32, kJacobi, cur, oth, false);
+        std::swap(cur, oth);
+      }
+      if (cur != kSelU) chunks(p, l, kQCopy, f32, cur, kSelU);
+    }
+  }
+  std::vector<QItem> build() {
+    for (int p = 0; p < bt.n; ++p) {
+      const int L = bt.H[p]->L;
+      if (bt.mixed) {
+        chunks(p, L, kQUpdate, false);
+        sweeps(p, L, false, kResidual, kSelU, kSelR, true);
+        single(p, kQCheck, false);
+        chunks(p, L, kQScale, false);
+        for (int k = 0; k < bt.inner; ++k) cycle(p, true, false);
+      } else {
+        sweeps(p, L, false, kJacobiNorm, kSelU, kSelT, true);
+        single(p, kQCheck, false);
+        cycle(p, false, true);
+      }
+    }
+    std::vector<QItem> out;
+    std::vector<int> done(bt.n, 0);
+    size_t maxph = 0;
+    for (auto& v : ph) maxph = std::max(maxph, v.size());
+    for (size_t k = 0; k < maxph; ++k)
+      for (int p = 0; p < bt.n; ++p) {
+        if (k >= ph[p].size()) continue;
+        for (QItem it : ph[p][k]) {
+          it.need = done[p];
+          out.push_back(it);
+        }
+        done[p] += static_cast<int>(ph[p][k].size());
+      }
+    return out;
+  }
+};
+
+// one persistent step: reset the ticket, the counters and the active count, run the
+// queue, bring back the active count and the error word
+mg_status persist_step(Batch& bt, cudaStream_t s) {
+  QueueArgs q{};
+  q.b64 = BatchArgs<double>{bt.d_lv64, bt.d_u64, bt.d_b64, bt.d_Lp, bt.d_active, bt.d_partial, bt.omega};
+  if (bt.mixed)
+    q.b32 = BatchArgs<float>{bt.d_lv32, bt.d_u32, bt.d_b32, bt.d_Lp, bt.d_active, nullptr,
+                             static_cast<float>(bt.omega)};
+  q.st = bt.state;
+  q.st.prange = bt.d_prange_q;
+  q.cp = bt.d_c;
+  q.chol = bt.d_chol;
+  q.cslots = bt.d_cslots;
+  q.nc = bt.d_nc;
+  q.items = bt.d_queue;
+  q.n_items = bt.n_queue;
+  q.head = bt.d_head;
+  q.prog = bt.d_prog;
+  q.err = bt.d_err;
+  if (cudaMemsetAsync(bt.d_head, 0, sizeof(unsigned), s) != cudaSuccess ||
+      cudaMemsetAsync(bt.d_prog, 0, static_cast<size_t>(bt.n) * sizeof(int), s) != cudaSuccess ||
+      cudaMemsetAsync(bt.d_nactive, 0, sizeof(int), s) != cudaSuccess) {
+    set_error("batch: persistent step reset failed");
+    return MG_ERR_CUDA;
+  }
+  const cudaError_t e = bt.dim == 2 ? bpersist_launch<2>(q, bt.amc64, bt.pm64, bt.amc32, bt.pm32, s)
+                                    : bpersist_launch<3>(q, bt.amc64, bt.pm64, bt.amc32, bt.pm32, s);
+  if (e != cudaSuccess || cudaMemcpyAsync(bt.h_pin, bt.d_nactive, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaMemcpyAsync(bt.h_pin + 1, bt.d_err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) {
+    set_error(std::string("batch: persistent step: ") + cudaGetErrorString(e != cudaSuccess ? e : cudaGetLastError()));
+    return MG_ERR_CUDA;
+  }
+  return MG_OK;
+}
+
 mg_status build_batch(Batch& bt) {
   if (cudaStreamCreateWithPriority(&bt.own, bt.blocking ? cudaStreamDefault : cudaStreamNonBlocking, bt.priority) !=
       cudaSuccess) {
@@ -366,8 +455,9 @@ mg_status build_batch(Batch& bt) {
       set_error("mg_batch_create: every hierarchy of a batch needs the same dimension and options");
       return MG_ERR_INVALID_ARG;
     }
-    if (h->opt.smoother != MG_SMOOTH_JACOBI || h->opt.cycle != MG_CYCLE_V) {
-      set_error("mg_batch_create: batches run V-cycles with the Jacobi smoother only");
+    if (h->opt.smoother != MG_SMOOTH_JACOBI || h->opt.cycle != MG_CYCLE_V || h->opt.dynamic_coarsest ||
+        h->tensor) {
+      set_error("mg_batch_create: batches run V-cycles with the Jacobi smoother and a fixed coarsest level only");
       return MG_ERR_UNSUPPORTED;
     }
     if (h->fmt == 4) {
@@ -476,6 +566,30 @@ mg_status build_batch(Batch& bt) {
   }
   if ((st = balloc(bt, &bt.d_partial, std::max(part, 1))) != MG_OK) return st;
   if ((st = bupload(bt, &bt.d_prange, prange)) != MG_OK) return st;
+  // persistent steps: every hierarchy asks for them and the batch's storage modes have
+  // an instantiated queue kernel (BoxMG + Galerkin with BF16 codes, or geometric)
+  bool want = true;
+  for (const Hier* h : bt.H) want = want && h->opt.persistent;
+  const bool modes = (bt.amc64 == 1 && bt.pm64 == 1 && bt.amc32 == 2 && bt.pm32 == 2) ||
+                     (bt.amc64 == 0 && bt.pm64 == 0 && bt.amc32 == 0 && bt.pm32 == 0);
+  if (want && modes) {
+    QueueBuilder qb(bt);
+    const std::vector<QItem> q = qb.build();
+    if ((st = bupload(bt, &bt.d_queue, q)) != MG_OK) return st;
+    if ((st = bupload(bt, &bt.d_prange_q, qb.prange)) != MG_OK) return st;
+    if ((st = balloc(bt, &bt.d_head, 1)) != MG_OK) return st;
+    if ((st = balloc(bt, &bt.d_prog, n)) != MG_OK) return st;
+    if ((st = balloc(bt, &bt.d_err, 1)) != MG_OK) return st;
+    if (qb.part > part) {  // the norm slots of the queue
+      if ((st = balloc(bt, &bt.d_partial, qb.part)) != MG_OK) return st;
+    }
+    if (cudaMemsetAsync(bt.d_err, 0, sizeof(int), bt.own) != cudaSuccess) {
+      set_error("mg_batch_create: upload failed");
+      return MG_ERR_CUDA;
+    }
+    bt.n_queue = static_cast<int>(q.size());
+    bt.persistent = true;
+  }
   bt.h_pin = static_cast<int*>(pinned_slot());
   if (!bt.h_pin) {
     set_error("mg_batch_create: pinned host memory unavailable");
@@ -573,7 +687,7 @@ mg_status batch_begin(Batch& bt, double* const* u, const double* const* b, const
   cudaFreeAsync(d_mask, s);
   bt.state = BatchState{bt.d_active, bt.d_cycles, bt.d_status, bt.d_r0, bt.d_rel, bt.d_sigma, bt.d_invc,
                         bt.d_nactive, bt.d_prange, bt.d_partial, bt.d_tol, bt.d_max, bt.mixed ? bt.inner : 1, n};
-  if (bt.use_graph && !bt.graph.exec) {
+  if (bt.use_graph && !bt.persistent && !bt.graph.exec) {
     const BatchState& st = bt.state;
     cudaGraph_t graph = nullptr;
     if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
@@ -602,6 +716,23 @@ mg_status batch_begin(Batch& bt, double* const* u, const double* const* b, const
 // cycles), stopping early once no problem is active.
 mg_status batch_run(Batch& bt, int max_steps, cudaStream_t s, int* n_active) {
   *n_active = bt.n;
+  if (bt.persistent) {
+    for (int it = 0; it < max_steps; ++it) {
+      const mg_status ps = persist_step(bt, s);
+      if (ps != MG_OK) return ps;
+      if (cudaStreamSynchronize(s) != cudaSuccess) {
+        set_error(std::string("batch: ") + cudaGetErrorString(cudaGetLastError()));
+        return MG_ERR_CUDA;
+      }
+      if (bt.h_pin[1] != 0) {
+        set_error("batch: a persistent step's wait for a problem's earlier phase timed out");
+        return MG_ERR_TIMEOUT;
+      }
+      *n_active = bt.h_pin[0];
+      if (*n_active == 0) break;
+    }
+    return MG_OK;
+  }
   for (int it = 0; it < max_steps; ++it) {
     if (!bt.use_graph) {
       if (bt.mixed) {
@@ -623,6 +754,7 @@ mg_status batch_run(Batch& bt, int max_steps, cudaStream_t s, int* n_active) {
 // Enqueues one step on s (direct launches) without waiting for it; batch_read after the
 // stream has reached it gives the problems' states.
 mg_status batch_step_enqueue(Batch& bt, cudaStream_t s) {
+  if (bt.persistent) return persist_step(bt, s);
   if (bt.mixed) {
     if (bt.dim == 2) emit_mixed_step<2>(bt, bt.state, s); else emit_mixed_step<3>(bt, bt.state, s);
   } else {

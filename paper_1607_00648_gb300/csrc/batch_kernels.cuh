@@ -23,6 +23,77 @@ struct BatchArgs {
   T omega;
 };
 
+// per-problem solve state of a batch (device arrays of n entries)
+struct BatchState {
+  int* active;
+  int* cycles;
+  int* status;  // 0 converged, 1 not converged, 2 non-finite, 3 diverged
+  double* r0;
+  double* rel;
+  double* sigma;
+  const double* invc;
+  int* n_active;
+  const int2* prange;
+  const double* partial;
+  const double* tol;     // per problem
+  const int* max_cycles; // per problem
+  int inc;
+  int n;
+};
+
+// convergence test of problem p from the partial sums of its norm sweep: first call
+// (r0 < 0) records r0; retires the problem on convergence, a non-finite or diverged
+// residual, or max_cycles; otherwise counts the cycles, stores sigma (mixed scaling)
+// and counts the problem active
+__device__ inline void bcheck_one(const BatchState& s, int p) {
+  if (!s.active[p]) return;
+  double n2 = 0.0;
+  for (int i = s.prange[p].x; i < s.prange[p].y; ++i) n2 += s.partial[i];
+  double rel;
+  if (s.r0[p] < 0.0) {
+    s.r0[p] = sqrt(n2);
+    rel = s.r0[p] > 0.0 ? 1.0 : 0.0;
+  } else {
+    rel = sqrt(n2) / s.r0[p];
+  }
+  s.rel[p] = rel;
+  int st = -1;
+  if (!(rel == rel) || isinf(rel)) st = 2;
+  else if (rel <= s.tol[p]) st = 0;
+  else if (rel > 1e6) st = 3;
+  else if (s.cycles[p] >= s.max_cycles[p]) st = 1;
+  if (st >= 0) {
+    s.status[p] = st;
+    s.active[p] = 0;
+    return;
+  }
+  s.cycles[p] += s.inc;
+  s.sigma[p] = sqrt(n2 * s.invc[p]);
+  atomicAdd(s.n_active, 1);
+}
+
+// coarsest level of problem p by its FP64 Cholesky factor (one thread)
+template <typename T>
+__device__ void bcoarse_one(const PLevel<T>* lv, const int* cp, const double* const* chol,
+                            const int32_t* const* cslots, const int* nc, int p) {
+  const PLevel<T>& P = lv[p * kMaxLevels + cp[p]];
+  const double* Lm = chol[p];
+  const int32_t* cs = cslots[p];
+  const int m = nc[p];
+  double y[64];
+  for (int i = 0; i < m; ++i) {
+    double v = static_cast<double>(P.b[cs[i]]);
+    for (int j = 0; j < i; ++j) v -= Lm[i * m + j] * y[j];
+    y[i] = v / Lm[i * m + i];
+  }
+  for (int i = m - 1; i >= 0; --i) {
+    double v = y[i];
+    for (int j = i + 1; j < m; ++j) v -= Lm[j * m + i] * y[j];
+    y[i] = v / Lm[i * m + i];
+  }
+  for (int i = 0; i < m; ++i) P.u[cs[i]] = static_cast<T>(y[i]);
+}
+
 // a launch group: items of one phase sharing the brick edge(s)
 struct BatchGroup {
   int B, BC, BF;   // sweep: B; transfer: coarse / fine brick edge

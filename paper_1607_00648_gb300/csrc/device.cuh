@@ -153,11 +153,13 @@ __device__ __forceinline__ T bpa_decode(const uint8_t* bytes, uint64_t rec, int 
   return ((word >> M) & 1u) ? -x : x;
 }
 
-// per-vertex key of a delta row: the bpa record (DMODE 4), else a non-zero constant;
-// a zero key marks a dropped operator whose entries all read as zero
+// per-vertex key of a delta row: the bpa record (DMODE 4; a zero bpa marks a dropped
+// operator whose entries all read as zero), the bit pattern of the FP32 scale (DMODE 2,
+// 3: its sign bit is the promotion flag), else a non-zero constant
 template <int DMODE>
 __device__ __forceinline__ uint64_t delta_row(const void* aux, int64_t slot) {
   if constexpr (DMODE == 4) return static_cast<const uint64_t*>(aux)[slot];
+  else if constexpr (DMODE == 2 || DMODE == 3) return __float_as_uint(static_cast<const float*>(aux)[slot]);
   else return 1;
 }
 template <int DMODE>
@@ -166,19 +168,19 @@ __device__ __forceinline__ bool delta_row_live(uint64_t key) {
 }
 
 // delta entry k of the vertex in slot `slot`; idx = its position in the 16-bit or FP64
-// planes.  aux: per-vertex FP32 scales (DMODE 2, 3); DMODE 4 decodes from the stream p
-// with the vertex's record `key` (delta_row).
+// planes; key = the vertex's delta_row.  DMODE 2, 3: the scale comes from the key.
 // lo_off (DMODE 2, 3; 0 = no promotion): distance from the code planes to the planes of
 // the low halves.  A promoted vertex (the sign bit of its scale set: its 16-bit codes
 // could not reconstruct its diagonal, Sect. 5 cancellation) stores the FP32 bit pattern
 // of delta / s as (code << 16 | low half); the value is then that FP32 number times |s|.
+// DMODE 4 decodes from the stream p with the vertex's record.
 template <int DMODE, typename T>
 __device__ __forceinline__ T load_delta(const void* p, const void* aux, int64_t idx, int64_t slot, int k = 0,
                                         uint64_t key = 0, int64_t lo_off = 0) {
   if constexpr (DMODE == 1) {
     return static_cast<T>(static_cast<const double*>(p)[idx]);
   } else if constexpr (DMODE == 2 || DMODE == 3) {
-    const float s = static_cast<const float*>(aux)[slot];
+    const float s = __uint_as_float(static_cast<uint32_t>(key));
     const uint16_t* q = static_cast<const uint16_t*>(p);
     if (lo_off != 0 && s < 0.0f)
       return static_cast<T>(__uint_as_float((static_cast<uint32_t>(q[idx]) << 16) | q[idx + lo_off]) * -s);
@@ -215,9 +217,37 @@ __device__ __forceinline__ double p_entry_d(const LevelDesc& Lc, const double* p
 // st[k], k over offsets {-1,0,1}^d lexicographic (x fastest): rediscretised from
 // the adjacent existing cells' eps (cell slot = lower-left vertex slot), plus the
 // stored FP64 delta when ahat != nullptr.
+// Anisotropy of a diagonal-tensor coefficient eps = diag(eps_i) (Sect. 7 `checkerboard`):
+// with the per-cell mean e = mean_i eps_i and d_i = eps_i - e, the d-linear element
+// matrix is e K + sum_i d_i K_i (K_i = int d_i phi_a d_i phi_b), and since sum_i d_i = 0
+// the second term is, per pair of corners, 2D: -d_x / 2 for corners differing in x only,
+// +d_x / 2 for those differing in y only, 0 otherwise; 3D (times h): -d_i / 6 for corners
+// differing in axis i only, +d_k / 12 for corners differing in the two axes other than
+// k, 0 otherwise (nothing on the diagonal).  Returned: the entry of one cell with per-axis
+// deviations dv for neighbour offset o (o in {-1, 0, 1}^d, o != 0, inside the cell).
+template <int DIM>
+__device__ __forceinline__ double aniso_entry(const double* dv, const int* o, double h) {
+  int nz = 0, k0 = -1, z = -1;
+#pragma unroll
+  for (int i = 0; i < DIM; ++i) {
+    if (o[i] != 0) {
+      ++nz;
+      k0 = i;
+    } else {
+      z = i;
+    }
+  }
+  if constexpr (DIM == 2) return nz == 1 ? (k0 == 0 ? -0.5 * dv[0] : 0.5 * dv[0]) : 0.0;
+  if (nz == 1) return -h * dv[k0] / 6.0;
+  if (nz == 2) return h * dv[z] / 12.0;
+  return 0.0;
+}
+
+// aniso (nullable): per-axis deviations d_i of a diagonal-tensor coefficient on this level,
+// axis-major (aniso[i * n_slots + cell slot]); eps then holds the per-cell mean.
 template <int DIM>
 __device__ void full_stencil(const LevelDesc& L, const double* eps, const double* ahat, const int* x,
-                             int64_t slot, double* st) {
+                             int64_t slot, double* st, const double* aniso = nullptr) {
   constexpr int N3 = cpow(3, DIM);
   double ec[1 << DIM];
 #pragma unroll
@@ -253,6 +283,26 @@ __device__ void full_stencil(const LevelDesc& L, const double* eps, const double
     }
     st[k] = elem_k(DIM, ham) * es * scale;
     if (ahat && slot >= 0) st[k] += ahat[plane_index(L, slot, k, N3)];
+    if (aniso && ham > 0) {
+#pragma unroll
+      for (int e = 0; e < (1 << DIM); ++e) {
+        bool ok = true;
+        int c[DIM];
+#pragma unroll
+        for (int i = 0; i < DIM; ++i) {
+          const int t = ((e >> i) & 1) + o[i];
+          ok = ok && t >= 0 && t <= 1;
+          c[i] = x[i] - ((e >> i) & 1);
+        }
+        if (!ok) continue;
+        const int64_t cs = slot_of<DIM>(L, c);
+        if (cs < 0) continue;
+        double dv[DIM];
+#pragma unroll
+        for (int i = 0; i < DIM; ++i) dv[i] = aniso[i * L.n_slots + cs];
+        st[k] += aniso_entry<DIM>(dv, o, L.h);
+      }
+    }
   }
 }
 

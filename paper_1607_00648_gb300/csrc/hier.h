@@ -35,6 +35,8 @@ struct DevLevel {
   uint8_t* pbpa = nullptr;
   double *u = nullptr, *b = nullptr, *r = nullptr, *t = nullptr;
   float *u32 = nullptr, *b32 = nullptr, *r32 = nullptr, *t32 = nullptr;
+  double* aniso = nullptr;   // finest level of a tensor hierarchy: per-axis coefficient deviations
+  float* aniso32 = nullptr;  // (axis-major, cell slots) and their FP32 copy
   double* dinv = nullptr;  // FP64 hierarchies: omega / diag(A) for the Jacobi sweeps
   double *ad = nullptr, *ar = nullptr;  // additive cycle: correction d_l, surplus residual rh_l
   double* ai = nullptr;                 // BPX: injected skipped c-point updates i_l
@@ -56,10 +58,19 @@ struct Graph {
   }
 };
 
+// the dynamic coarsest level (Sect. 4.3) keeps the directly solved level at most this
+// many unknowns
+constexpr int kMaxDynCoarse = 1024;
+
 struct Hier {
   const Grid* g = nullptr;
   mg_options opt{};
   int L = 0, c = 1, dim = 2;
+  int c_user = 1, c_max = 1;  // the options' coarsest level; the finest the dynamic rule may take
+  int c_setup = 1;            // the coarsest level the last setup chose (dynamic rule (a))
+  std::vector<int32_t*> cs_lv, cm_lv;  // per candidate coarsest level: DoF slots, slot -> row map
+  std::vector<int> nc_lv;              // and its number of unknowns
+  int* d_audit = nullptr;              // dynamic rule: per level, 1 where the audit failed
   int top = 0;            // finest complete level (= L on uniform grids, L - 1 on adaptive ones)
   bool adaptive = false;  // level L only partly refined: composite solve
   int32_t* child_top = nullptr;  // level-top slot -> level-L slot at the same position
@@ -70,6 +81,7 @@ struct Hier {
   int32_t *ref_top = nullptr, *dof_L = nullptr, *hang_L = nullptr;
   int64_t n_ref_top = 0, n_dof_L = 0, n_hang_L = 0;
   bool galerkin = false, boxmg = false, mixed = false;
+  bool tensor = false;  // diagonal-tensor coefficients (mg_setup_tensor)
   int fmt = 1;  // 1 bf16, 2 fp16, 4 bpa codec
   uint64_t* bpa_used = nullptr;  // bpa codec: stream lengths per level, [2 l] A_hat, [2 l + 1] P_hat
   std::vector<DevLevel> lv;

@@ -143,8 +143,8 @@ __device__ __forceinline__ double sweep_item(const SweepArgs<T>& a, int64_t bric
     const int nvec = (nin + VEC - 1) / VEC;
 #pragma unroll 2
     for (int j = threadIdx.x; j < nvec; j += nt) {
-      const V uv = __ldg(up + j);
-      const V ev = __ldg(ep + j);
+      const V uv = up[j];  // plain loads: coherent with writes of earlier work in the same launch
+      const V ev = ep[j];
       const T* uu = reinterpret_cast<const T*>(&uv);
       const T* ee = reinterpret_cast<const T*>(&ev);
 #pragma unroll

@@ -79,6 +79,8 @@ int64_t launch_residual(const Hier& H, const DevLevel& D, bool coarse_delta, con
   a.eps = D.eps;
   a.ahat = coarse_delta ? D.ahat : nullptr;
   a.partial = partial;
+  // the default slab rule, not a depth chosen by mg_autotune: a tuned depth can need
+  // more partial sums than the fixed array holds
   a.R = pick_slab(D.d.B, D.d.n_bricks, kSweepTargetCtas);
   if (H.dim == 2)
     launch_sweep<2, double>(a, kResidual, coarse_delta ? 1 : 0, s);
@@ -102,6 +104,10 @@ extern "C" mg_status mg_residual_norm_noalloc(mg_hier* h, int level, const doubl
   if (level < H->c || level > H->L || !u || !b || !r || !norm2) {
     set_error("mg_residual_norm_noalloc: invalid level or NULL vector");
     return MG_ERR_INVALID_ARG;
+  }
+  if (H->tensor && level == H->L) {
+    set_error("mg_residual_norm_noalloc: the finest level of a tensor-coefficient hierarchy; use mg_residual");
+    return MG_ERR_UNSUPPORTED;
   }
   const DevLevel& D = H->lv[level];
   if (D.d.n_bricks > kMaxBricks) {

@@ -370,8 +370,10 @@ mg_status mg_server_create(size_t hbm_budget_bytes, const mg_options* opt, mg_se
     set_error("mg_server_create: invalid argument");
     return MG_ERR_INVALID_ARG;
   }
-  if (opt && (opt->precision == MG_PREC_MIXED_BPA || opt->smoother != MG_SMOOTH_JACOBI || opt->cycle != MG_CYCLE_V)) {
-    set_error("mg_server_create: the server runs batches: V-cycles, Jacobi smoothing, no bpa codec");
+  if (opt && (opt->precision == MG_PREC_MIXED_BPA || opt->smoother != MG_SMOOTH_JACOBI || opt->cycle != MG_CYCLE_V ||
+              opt->dynamic_coarsest || opt->tensor_coefficients)) {
+    set_error("mg_server_create: the server runs batches: V-cycles, Jacobi smoothing, no bpa codec, a fixed "
+              "coarsest level");
     return MG_ERR_UNSUPPORTED;
   }
   *out = nullptr;

@@ -81,7 +81,8 @@ __device__ __forceinline__ bool small_solve(double (&M)[NMAX][NMAX], double (&rh
 // sigma_i = +1 on its zero axes.  Output: P_hat = P - P_dlin on 5^d planes.
 template <int DIM>
 __global__ void __launch_bounds__(64) k_boxmg(LevelDesc Lc, LevelDesc Lf, const double* eps_f,
-                                                const double* ahat_f, double* phat_c, int* status) {
+                                                const double* ahat_f, double* phat_c, int* status,
+                                                const double* aniso_f = nullptr) {
   constexpr int N3 = cpow(3, DIM), N5 = cpow(5, DIM);
   // one thread per (coarse slot, patch): the patches of a vertex write disjoint entries
   const int64_t tid = blockIdx.x * static_cast<int64_t>(64) + threadIdx.x;
@@ -129,7 +130,7 @@ __global__ void __launch_bounds__(64) k_boxmg(LevelDesc Lc, LevelDesc Lf, const 
           for (int i = 0; i < DIM; ++i) xf[i] = 3 * V[i] + sigma[i] * rpos[j][i];
           const int64_t fsl = slot_of<DIM>(Lf, xf);
           double st[N3];
-          full_stencil<DIM>(Lf, eps_f, ahat_f, xf, fsl, st);
+          full_stencil<DIM>(Lf, eps_f, ahat_f, xf, fsl, st, aniso_f);
           for (int k = 0; k < N3; ++k) {
             int o[DIM], kk = k;
 #pragma unroll
@@ -249,7 +250,8 @@ constexpr size_t rap_dyn_smem() {
 
 template <int DIM, int PMODE>
 __global__ void __launch_bounds__(128) k_rap(LevelDesc Lc, LevelDesc Lf, const double* eps_f, const double* ahat_f,
-                                               const double* eps_c, const double* phat_c, double* ahat_c) {
+                                               const double* eps_c, const double* phat_c, double* ahat_c,
+                                               const double* aniso_f = nullptr) {
   constexpr int N3 = cpow(3, DIM), N5 = cpow(5, DIM);
   constexpr int TPV = rap_tpv<DIM>(), VPB = 128 / TPV, WPV = TPV / 32;
   __shared__ int64_t pbase[VPB][N3];   // plane-0 index of P_hat(W) for W = V + o if W is a DoF, else -1
@@ -307,7 +309,7 @@ __global__ void __launch_bounds__(128) k_rap(LevelDesc Lc, LevelDesc Lf, const d
     const int64_t fs = (vdof && j < N5) ? slot_of<DIM>(Lf, f) : -1;
     if (fs >= 0 && is_dof(Lf.vflags[fs])) {
       const double pV = p_entry_d<DIM, PMODE>(Lc, phat_c, cs, d);
-      full_stencil<DIM>(Lf, eps_f, ahat_f, f, fs, st);
+      full_stencil<DIM>(Lf, eps_f, ahat_f, f, fs, st, aniso_f);
 #pragma unroll
       for (int e = 0; e < N3; ++e) {
         int g[DIM], ee = e;

@@ -281,7 +281,8 @@ __global__ void k_encode_planes(LevelDesc L, int K, const double* delta, uint16_
 
 // reconstructed stencils (offset-major export) and the diagonal audit (Sect. 4.3)
 template <int DIM>
-__global__ void k_export_stencils(LevelDesc L, const double* eps, const double* ahat, double* out, int* status) {
+__global__ void k_export_stencils(LevelDesc L, const double* eps, const double* ahat, double* out, int* status,
+                                  const double* aniso = nullptr) {
   constexpr int N3 = cpow(3, DIM);
   const int64_t s = blockIdx.x * static_cast<int64_t>(kBlock) + threadIdx.x;
   if (s >= L.n_slots) return;
@@ -292,10 +293,117 @@ __global__ void k_export_stencils(LevelDesc L, const double* eps, const double* 
       for (int k = 0; k < N3; ++k) out[k * L.n_slots + s] = 0.0;
     return;
   }
-  full_stencil<DIM>(L, eps, ahat, x, s, st);
+  full_stencil<DIM>(L, eps, ahat, x, s, st, aniso);
   if (out)
     for (int k = 0; k < N3; ++k) out[k * L.n_slots + s] = st[k];
   if (status && is_dof(L.vflags[s]) && !(st[N3 / 2] > 0.0)) atomicExch(status, 2);
+}
+
+// diagonal-tensor coefficients of the finest level (d level-concatenated arrays, one per
+// axis, stride n_total): the per-cell mean into eps, the deviations d_i = eps_i - mean
+// into aniso (axis-major)
+template <int DIM>
+__global__ void k_tensor_split(LevelDesc L, const double* axes, int64_t n_total, double* eps, double* aniso) {
+  const int64_t s = blockIdx.x * static_cast<int64_t>(kBlock) + threadIdx.x;
+  if (s >= L.n_slots) return;
+  double e[DIM], m = 0.0;
+#pragma unroll
+  for (int i = 0; i < DIM; ++i) {
+    e[i] = axes[i * n_total + s];
+    m += e[i];
+  }
+  m /= DIM;
+  eps[s] = m;
+#pragma unroll
+  for (int i = 0; i < DIM; ++i) aniso[i * L.n_slots + s] = e[i] - m;
+}
+
+// The anisotropic part B u of a diagonal-tensor operator on the finest level (the
+// sweeps apply the per-cell mean coefficient): after a Jacobi sweep out -= dinv B u
+// (FP64: omega / diag from the setup; FP32: omega / D with D from the mean coefficients;
+// B has no diagonal), after a residual sweep out -= B u with the squared norm of the
+// result (the sweep itself then runs without its norm).  u is the sweep's input.
+template <int DIM, typename T, int OP>
+__global__ void __launch_bounds__(kBlock) k_aniso_fix(LevelDesc L, const T* u, T* out, const T* aniso, const T* eps,
+                                                       const double* dinv, T omega, double* partial, unsigned* counter,
+                                                       double* norm2) {
+  const int64_t s = blockIdx.x * static_cast<int64_t>(kBlock) + threadIdx.x;
+  double part = 0.0;
+  int x[DIM];
+  if (s < L.n_slots && is_dof(L.vflags[s]) && coords_of<DIM>(L, s, x)) {
+    double Bu = 0.0, es = 0.0;
+#pragma unroll
+    for (int e = 0; e < (1 << DIM); ++e) {
+      int c[DIM];
+#pragma unroll
+      for (int i = 0; i < DIM; ++i) c[i] = x[i] - ((e >> i) & 1);
+      const int64_t cs = slot_of<DIM>(L, c);
+      if (cs < 0) continue;
+      double dv[DIM];
+#pragma unroll
+      for (int i = 0; i < DIM; ++i) dv[i] = static_cast<double>(aniso[i * L.n_slots + cs]);
+      es += static_cast<double>(eps[cs]);
+      // the cell's other corners: offsets o_i in {0, 1 - 2 e_i}
+#pragma unroll
+      for (int m = 1; m < (1 << DIM); ++m) {
+        int o[DIM], y[DIM];
+#pragma unroll
+        for (int i = 0; i < DIM; ++i) {
+          o[i] = ((m >> i) & 1) ? 1 - 2 * ((e >> i) & 1) : 0;
+          y[i] = x[i] + o[i];
+        }
+        const double w = aniso_entry<DIM>(dv, o, L.h);
+        if (w == 0.0) continue;
+        const int64_t ns = slot_of<DIM>(L, y);
+        if (ns >= 0) Bu += w * static_cast<double>(u[ns]);
+      }
+    }
+    if constexpr (OP == kJacobi) {
+      double f;
+      if (dinv) {
+        f = dinv[s];
+      } else {
+        const double D = DIM == 2 ? elem_k(2, 0) * es : elem_k(3, 0) * L.h * es;
+        f = static_cast<double>(omega) / D;
+      }
+      out[s] = static_cast<T>(static_cast<double>(out[s]) - f * Bu);
+    } else {
+      const T r = static_cast<T>(static_cast<double>(out[s]) - Bu);
+      out[s] = r;
+      part = static_cast<double>(r) * static_cast<double>(r);
+    }
+  }
+  if constexpr (OP == kResidual) {
+    if (partial) store_partial_and_finish(part, partial, counter, norm2);
+  }
+}
+
+// Sect. 4.3 audit of one level for the dynamic coarsest level: *fail = 1 if a DoF row
+// has a non-positive diagonal or is not diagonally dominant over the unknowns (sum of
+// |off-diagonal| over DoF neighbours > (1 + 1e-12) |diagonal|); entries towards
+// Dirichlet vertices multiply zero and are left out
+template <int DIM>
+__global__ void k_audit(LevelDesc L, const double* eps, const double* ahat, int* fail) {
+  constexpr int N3 = cpow(3, DIM);
+  const int64_t s = blockIdx.x * static_cast<int64_t>(kBlock) + threadIdx.x;
+  if (s >= L.n_slots || !is_dof(L.vflags[s])) return;
+  int x[DIM];
+  if (!coords_of<DIM>(L, s, x)) return;
+  double st[N3];
+  full_stencil<DIM>(L, eps, ahat, x, s, st);
+  double off = 0.0;
+  for (int k = 0; k < N3; ++k) {
+    if (k == N3 / 2) continue;
+    int y[DIM], kk = k;
+    for (int i = 0; i < DIM; ++i) {
+      y[i] = x[i] + kk % 3 - 1;
+      kk /= 3;
+    }
+    const int64_t ns = slot_of<DIM>(L, y);
+    if (ns >= 0 && is_dof(L.vflags[ns])) off += fabs(st[k]);
+  }
+  const double d = st[N3 / 2];
+  if (!(d > 0.0) || off > (1.0 + 1e-12) * fabs(d)) *fail = 1;
 }
 
 // dense coarsest operator over its DoFs
@@ -539,6 +647,7 @@ static mg_status create(const Grid* g, const mg_options& o, Hier** out, int prio
   H->top = H->adaptive ? g->L - 1 : g->L;
   H->dim = g->dim;
   H->galerkin = o.coarse == MG_COARSE_GALERKIN;
+  H->tensor = o.tensor_coefficients != 0;
   H->boxmg = o.transfer == MG_TRANSFER_BOXMG;
   H->mixed = o.precision != MG_PREC_FP64;
   H->fmt = o.precision == MG_PREC_MIXED_FP16 ? 2 : (o.precision == MG_PREC_MIXED_BPA ? 4 : 1);
@@ -594,6 +703,10 @@ static mg_status create(const Grid* g, const mg_options& o, Hier** out, int prio
         }
         if ((st = upload(*H, &D.child, child)) != MG_OK) return fail(st);
       }
+    }
+    if (o.tensor_coefficients && l == H->L) {  // per-axis deviations of a diagonal-tensor coefficient
+      if ((st = dalloc(*H, &D.aniso, ns * d)) != MG_OK) return fail(st);
+      if (H->mixed && (st = dalloc(*H, &D.aniso32, ns * d)) != MG_OK) return fail(st);
     }
     if ((st = dalloc(*H, &D.partial, static_cast<size_t>(hl.n_bricks) * hl.B)) != MG_OK) return fail(st);
     if (!H->mixed && (st = dalloc(*H, &D.dinv, ns)) != MG_OK) return fail(st);
@@ -673,24 +786,42 @@ static mg_status create(const Grid* g, const mg_options& o, Hier** out, int prio
       if ((st = dalloc(*H, &H->cb32, static_cast<size_t>(ht.n_slots))) != MG_OK) return fail(st);
     }
   }
-  // coarsest dense system
-  const HostLevel& hc = g->levels[H->c];
-  std::vector<int32_t> slots, map(hc.n_slots, -1);
-  for (int64_t s = 0; s < hc.n_slots; ++s) {
-    const uint8_t f = hc.vflags[s];
-    if ((f & MG_V_EXISTS) && !(f & (MG_V_BOUNDARY | MG_V_HANGING))) {
-      map[s] = static_cast<int32_t>(slots.size());
-      slots.push_back(static_cast<int32_t>(s));
+  // coarsest dense system; with the dynamic coarsest level, the slot lists of every level
+  // that may become the coarsest one (up to kMaxDynCoarse unknowns) and a matrix buffer
+  // for the largest of them, so that mg_setup and mg_solve allocate nothing
+  H->c_user = H->c_setup = H->c;
+  H->c_max = H->c;
+  if (o.dynamic_coarsest)
+    while (H->c_max + 1 < H->L && g->levels[H->c_max + 1].n_dofs <= kMaxDynCoarse) ++H->c_max;
+  H->cs_lv.assign(H->L + 1, nullptr);
+  H->cm_lv.assign(H->L + 1, nullptr);
+  H->nc_lv.assign(H->L + 1, 0);
+  int nc_big = 0;
+  for (int l = H->c; l <= H->c_max; ++l) {
+    const HostLevel& hc = g->levels[l];
+    std::vector<int32_t> slots, map(hc.n_slots, -1);
+    for (int64_t s = 0; s < hc.n_slots; ++s) {
+      const uint8_t f = hc.vflags[s];
+      if ((f & MG_V_EXISTS) && !(f & (MG_V_BOUNDARY | MG_V_HANGING))) {
+        map[s] = static_cast<int32_t>(slots.size());
+        slots.push_back(static_cast<int32_t>(s));
+      }
     }
+    const int n = static_cast<int>(slots.size());
+    if (n == 0 || n > 4096) {
+      set_error("mg_hier_create: coarsest level has " + std::to_string(n) + " DoFs (need 1..4096)");
+      return fail(MG_ERR_INVALID_ARG);
+    }
+    if ((st = upload(*H, &H->cs_lv[l], slots)) != MG_OK) return fail(st);
+    if ((st = upload(*H, &H->cm_lv[l], map)) != MG_OK) return fail(st);
+    H->nc_lv[l] = n;
+    nc_big = std::max(nc_big, n);
   }
-  H->n_c = static_cast<int>(slots.size());
-  if (H->n_c == 0 || H->n_c > 4096) {
-    set_error("mg_hier_create: coarsest level has " + std::to_string(H->n_c) + " DoFs (need 1..4096)");
-    return fail(MG_ERR_INVALID_ARG);
-  }
-  if ((st = upload(*H, &H->c_slots, slots)) != MG_OK) return fail(st);
-  if ((st = upload(*H, &H->c_map, map)) != MG_OK) return fail(st);
-  if ((st = dalloc(*H, &H->c_mat, static_cast<size_t>(H->n_c) * H->n_c)) != MG_OK) return fail(st);
+  H->n_c = H->nc_lv[H->c];
+  H->c_slots = H->cs_lv[H->c];
+  H->c_map = H->cm_lv[H->c];
+  if ((st = dalloc(*H, &H->c_mat, static_cast<size_t>(nc_big) * nc_big)) != MG_OK) return fail(st);
+  if (o.dynamic_coarsest && (st = dalloc(*H, &H->d_audit, H->L + 1)) != MG_OK) return fail(st);
   if ((st = dalloc(*H, &H->d_status, 1)) != MG_OK) return fail(st);
   if (H->fmt == 4 && (st = dalloc(*H, &H->bpa_used, 2 * (H->L + 1))) != MG_OK) return fail(st);
   if ((st = dalloc(*H, &H->d_scal, 16)) != MG_OK) return fail(st);
@@ -725,6 +856,10 @@ mg_status hier_create(const Grid* g, const mg_options& o, int priority, Hier** o
       o.transfer < 0 || o.transfer > 1 || o.coarse < 0 || o.coarse > 1 || o.precision < 0 || o.precision > 3 || o.smoother < 0 || o.smoother > 1 ||
       (o.smoother == MG_SMOOTH_BLOCK && (o.gs_sweeps < 1 || o.gs_sweeps > 64)) || o.cycle < 0 || o.cycle > 2 ||
       (o.cycle != MG_CYCLE_V && (o.precision != MG_PREC_FP64 || o.smoother != MG_SMOOTH_JACOBI)) ||
+      o.dynamic_coarsest < 0 || o.dynamic_coarsest > 1 || (o.dynamic_coarsest && o.cycle != MG_CYCLE_V) ||
+      o.tensor_coefficients < 0 || o.tensor_coefficients > 1 ||
+      (o.tensor_coefficients && (o.coarse != MG_COARSE_GALERKIN || o.smoother != MG_SMOOTH_JACOBI || o.persistent ||
+                                 o.precision == MG_PREC_MIXED_BPA)) ||
       (o.precision == MG_PREC_MIXED_BPA && !(o.eps_mf >= 0.0 && o.eps_mf < 1e300))) {
     set_error("mg_hier_create: invalid options");
     return MG_ERR_INVALID_ARG;
@@ -742,8 +877,9 @@ mg_status hier_create(const Grid* g, const mg_options& o, int priority, Hier** o
       set_error("mg_hier_create: the coarsest level must lie below the finest complete level");
       return MG_ERR_INVALID_ARG;
     }
-    if (o.cycle != MG_CYCLE_V) {
-      set_error("mg_hier_create: adaptive grids run the composite V-cycle");
+    if (o.cycle != MG_CYCLE_V || o.dynamic_coarsest || o.tensor_coefficients) {
+      set_error("mg_hier_create: adaptive grids run the composite V-cycle with a fixed coarsest level and "
+                "scalar coefficients");
       return MG_ERR_UNSUPPORTED;
     }
   }
@@ -771,6 +907,7 @@ size_t hier_footprint(const Grid& g, const mg_options& o) {
     if (l < g.L) bytes += 2 * ns * 8;
     if (o.cycle != MG_CYCLE_V) bytes += 2 * ns * 8 + (l < g.L ? ns * 4 : 0);
     if (o.cycle == MG_CYCLE_BPX && l < g.L) bytes += ns * 8;
+    if (o.tensor_coefficients && l == g.L) bytes += ns * d * (mixed ? 12 : 8);
     if (l < top) bytes += (galerkin ? ns * n3 * 8 : 0) + (boxmg ? ns * n5 * 8 : 0);
     if (mixed) {
       bytes += 5 * ns * 4;
@@ -835,12 +972,37 @@ template <typename T>
 static void sweep(const Hier& H, int l, int op, const T* u, const T* b, T* out, double* norm2, cudaStream_t s) {
   int amode = 0;
   SweepArgs<T> a = sweep_args<T>(H, l, u, b, out, &amode);
-  if (norm2) {
-    a.partial = H.lv[l].partial;
-    a.counter = H.lv[l].counter;
+  const DevLevel& D = H.lv[l];
+  const bool tensor = H.tensor && l == H.L;
+  if (norm2 && !tensor) {
+    a.partial = D.partial;
+    a.counter = D.counter;
     a.norm2 = norm2;
   }
   launch<T>(H, a, op, amode, s);
+  if (tensor) {  // the anisotropic part of a diagonal-tensor coefficient (finest level)
+    const T* an;
+    const T* ep;
+    if constexpr (std::is_same<T, double>::value) {
+      an = D.aniso;
+      ep = D.eps;
+    } else {
+      an = D.aniso32;
+      ep = D.eps32;
+    }
+    const double* dinv = std::is_same<T, double>::value ? D.dinv : nullptr;
+    const unsigned g = static_cast<unsigned>((D.d.n_slots + kBlock - 1) / kBlock);
+    const T om = static_cast<T>(H.opt.omega);
+    if (op == kJacobi) {
+      if (H.dim == 2) k_aniso_fix<2, T, kJacobi><<<g, kBlock, 0, s>>>(D.d, u, out, an, ep, dinv, om, nullptr, nullptr, nullptr);
+      else k_aniso_fix<3, T, kJacobi><<<g, kBlock, 0, s>>>(D.d, u, out, an, ep, dinv, om, nullptr, nullptr, nullptr);
+    } else {
+      double* pa = norm2 ? D.partial : nullptr;
+      unsigned* ct = norm2 ? D.counter : nullptr;
+      if (H.dim == 2) k_aniso_fix<2, T, kResidual><<<g, kBlock, 0, s>>>(D.d, u, out, an, ep, dinv, om, pa, ct, norm2);
+      else k_aniso_fix<3, T, kResidual><<<g, kBlock, 0, s>>>(D.d, u, out, an, ep, dinv, om, pa, ct, norm2);
+    }
+  }
 }
 
 template <typename T>
@@ -945,12 +1107,88 @@ static void residual_norm(Hier& H, const T* u, const T* b, T* r, int slot, cudaS
 
 static mg_status additive_reset(Hier& H, double* u, cudaStream_t s);
 
-static mg_status run_setup(Hier& H, const double* eps_in, cudaStream_t s, bool check_now = true) {
+// make level c the directly solved one (its slot lists were prepared at creation);
+// captured cycles of another coarsest level are dropped
+static void set_coarsest(Hier& H, int c) {
+  if (c == H.c && H.c_slots == H.cs_lv[c]) return;
+  H.c = c;
+  H.n_c = H.nc_lv[c];
+  H.c_slots = H.cs_lv[c];
+  H.c_map = H.cm_lv[c];
+  for (Graph* gr : {&H.g_cycle64, &H.g_outer, &H.g_inner, &H.g_comp64, &H.g_comp_outer, &H.g_comp_inner, &H.g_add})
+    gr->reset();
+}
+
+// dense FP64 operator of the coarsest level and its Cholesky factor (status 3 if the
+// operator is not positive definite)
+static void coarse_factor(Hier& H, cudaStream_t s) {
+  DevLevel& C = H.lv[H.c];
+  const double* ah = (H.c < H.top && H.galerkin) ? C.ahat : nullptr;
+  if (H.dim == 2)
+    k_coarse_assemble<2><<<nblk(H.n_c), kBlock, 0, s>>>(C.d, C.eps, ah, H.c_slots, H.c_map, H.n_c, H.c_mat);
+  else
+    k_coarse_assemble<3><<<nblk(H.n_c), kBlock, 0, s>>>(C.d, C.eps, ah, H.c_slots, H.c_map, H.n_c, H.c_mat);
+  k_cholesky<<<1, kBlock, 0, s>>>(H.c_mat, H.n_c, H.d_status);
+}
+
+// Sect. 4.3, dynamic coarsest level, rule (a): audit the coarse levels and make the level
+// above the finest failing one the coarsest
+static mg_status dynamic_coarsest_setup(Hier& H, cudaStream_t s) {
+  MG_TRY_CUDA(cudaMemsetAsync(H.d_audit, 0, static_cast<size_t>(H.L + 1) * sizeof(int), s));
+  for (int l = H.c_user; l < H.top; ++l) {
+    DevLevel& D = H.lv[l];
+    const double* ah = H.galerkin ? D.ahat : nullptr;
+    if (H.dim == 2)
+      k_audit<2><<<nblk(D.d.n_slots), kBlock, 0, s>>>(D.d, D.eps, ah, H.d_audit + l);
+    else
+      k_audit<3><<<nblk(D.d.n_slots), kBlock, 0, s>>>(D.d, D.eps, ah, H.d_audit + l);
+  }
+  MG_CHECK(last_launch("setup: coarse-level audit"));
+  std::vector<int> fail(H.L + 1, 0);
+  MG_TRY_CUDA(cudaMemcpyAsync(fail.data(), H.d_audit, fail.size() * sizeof(int), cudaMemcpyDeviceToHost, s));
+  MG_TRY_CUDA(cudaStreamSynchronize(s));
+  int cn = H.c_user;
+  for (int l = H.c_user; l < H.top; ++l)
+    if (fail[l]) cn = std::max(cn, l + 1);
+  if (cn > H.c_max) {
+    set_error("mg_setup: the dynamic coarsest level (Sect. 4.3) would be level " + std::to_string(cn) +
+              ": beyond the finest level or the " + std::to_string(kMaxDynCoarse) +
+              " unknowns of the direct coarse solve");
+    return MG_ERR_INDEFINITE_COARSE;
+  }
+  set_coarsest(H, cn);
+  H.c_setup = cn;
+  return MG_OK;
+}
+
+// eps_in: level-concatenated leaf coefficients; tensor_axes (instead, tensor hierarchies):
+// d such arrays, one per axis, of a diagonal-tensor coefficient on the finest level
+static mg_status run_setup(Hier& H, const double* eps_in, cudaStream_t s, bool check_now = true,
+                           const double* tensor_axes = nullptr) {
   const Grid& g = *H.g;
   const int d = H.dim;
-  for (int l = H.c; l <= H.L; ++l) {
-    DevLevel& D = H.lv[l];
-    k_leaf_eps<<<nblk(D.d.n_slots), kBlock, 0, s>>>(D.d, D.cflags, eps_in + g.levels[l].slot_offset, D.eps);
+  if (H.opt.dynamic_coarsest) {
+    if (!check_now) {
+      set_error("mg_setup: the dynamic coarsest level needs a synchronous setup (single hierarchies)");
+      return MG_ERR_UNSUPPORTED;
+    }
+    set_coarsest(H, H.c_user);  // every setup starts again from the requested level
+  }
+  if (tensor_axes) {  // uniform grid: the leaves are the finest level's cells
+    DevLevel& D = H.lv[H.L];
+    const int64_t nt = g.levels[H.L].slot_offset + g.levels[H.L].n_slots;
+    const double* ax = tensor_axes + g.levels[H.L].slot_offset;
+    if (d == 2)
+      k_tensor_split<2><<<nblk(D.d.n_slots), kBlock, 0, s>>>(D.d, ax, nt, D.eps, D.aniso);
+    else
+      k_tensor_split<3><<<nblk(D.d.n_slots), kBlock, 0, s>>>(D.d, ax, nt, D.eps, D.aniso);
+  } else {
+    for (int l = H.c; l <= H.L; ++l) {
+      DevLevel& D = H.lv[l];
+      k_leaf_eps<<<nblk(D.d.n_slots), kBlock, 0, s>>>(D.d, D.cflags, eps_in + g.levels[l].slot_offset, D.eps);
+    }
+    if (H.tensor)  // a scalar coefficient on a tensor hierarchy: no anisotropy
+      MG_TRY_CUDA(cudaMemsetAsync(H.lv[H.L].aniso, 0, sizeof(double) * d * H.lv[H.L].d.n_slots, s));
   }
   for (int l = H.L - 1; l >= H.c; --l) {
     DevLevel& C = H.lv[l];
@@ -969,9 +1207,9 @@ static mg_status run_setup(Hier& H, const double* eps_in, cudaStream_t s, bool c
     if (H.boxmg) {
       const unsigned gp = static_cast<unsigned>(((C.d.n_slots << d) + 63) / 64);
       if (d == 2)
-        k_boxmg<2><<<gp, 64, 0, s>>>(C.d, F.d, F.eps, ahat_f, C.phat, H.d_status);
+        k_boxmg<2><<<gp, 64, 0, s>>>(C.d, F.d, F.eps, ahat_f, C.phat, H.d_status, F.aniso);
       else
-        k_boxmg<3><<<gp, 64, 0, s>>>(C.d, F.d, F.eps, ahat_f, C.phat, H.d_status);
+        k_boxmg<3><<<gp, 64, 0, s>>>(C.d, F.d, F.eps, ahat_f, C.phat, H.d_status, F.aniso);
     }
     if (H.galerkin) {
       // 128-thread CTAs: 4 coarse vertices (2D) or 1 (3D) per CTA
@@ -985,28 +1223,29 @@ static mg_status run_setup(Hier& H, const double* eps_in, cudaStream_t s, bool c
       (void)smem_opt_in;
       if (d == 2) {
         if (H.boxmg)
-          k_rap<2, 1><<<gr, 128, rap_dyn_smem<2, 1>(), s>>>(C.d, F.d, F.eps, ahat_f, C.eps, C.phat, C.ahat);
+          k_rap<2, 1><<<gr, 128, rap_dyn_smem<2, 1>(), s>>>(C.d, F.d, F.eps, ahat_f, C.eps, C.phat, C.ahat, F.aniso);
         else
-          k_rap<2, 0><<<gr, 128, rap_dyn_smem<2, 0>(), s>>>(C.d, F.d, F.eps, ahat_f, C.eps, C.phat, C.ahat);
+          k_rap<2, 0><<<gr, 128, rap_dyn_smem<2, 0>(), s>>>(C.d, F.d, F.eps, ahat_f, C.eps, C.phat, C.ahat, F.aniso);
       } else {
         const unsigned g3 = static_cast<unsigned>(C.d.n_slots);
         if (H.boxmg)
-          k_rap<3, 1><<<g3, 128, rap_dyn_smem<3, 1>(), s>>>(C.d, F.d, F.eps, ahat_f, C.eps, C.phat, C.ahat);
+          k_rap<3, 1><<<g3, 128, rap_dyn_smem<3, 1>(), s>>>(C.d, F.d, F.eps, ahat_f, C.eps, C.phat, C.ahat, F.aniso);
         else
-          k_rap<3, 0><<<g3, 128, rap_dyn_smem<3, 0>(), s>>>(C.d, F.d, F.eps, ahat_f, C.eps, C.phat, C.ahat);
+          k_rap<3, 0><<<g3, 128, rap_dyn_smem<3, 0>(), s>>>(C.d, F.d, F.eps, ahat_f, C.eps, C.phat, C.ahat, F.aniso);
       }
     }
     MG_CHECK(last_launch("setup: BoxMG / Galerkin"));
   }
+  if (H.opt.dynamic_coarsest) MG_CHECK(dynamic_coarsest_setup(H, s));
   // diagonal audit of every level (Sect. 4.3 definiteness check), Jacobi factors,
   // coarsest factor
   for (int l = H.c; l <= H.L; ++l) {
     DevLevel& D = H.lv[l];
     const double* ah = (l < H.top && H.galerkin) ? D.ahat : nullptr;
     if (d == 2)
-      k_export_stencils<2><<<nblk(D.d.n_slots), kBlock, 0, s>>>(D.d, D.eps, ah, nullptr, H.d_status);
+      k_export_stencils<2><<<nblk(D.d.n_slots), kBlock, 0, s>>>(D.d, D.eps, ah, nullptr, H.d_status, D.aniso);
     else
-      k_export_stencils<3><<<nblk(D.d.n_slots), kBlock, 0, s>>>(D.d, D.eps, ah, nullptr, H.d_status);
+      k_export_stencils<3><<<nblk(D.d.n_slots), kBlock, 0, s>>>(D.d, D.eps, ah, nullptr, H.d_status, D.aniso);
     if (D.dinv) {
       if (d == 2)
         k_jacobi_dinv<2><<<nblk(D.d.n_slots), kBlock, 0, s>>>(D.d, D.eps, ah, H.opt.omega, D.dinv);
@@ -1014,18 +1253,14 @@ static mg_status run_setup(Hier& H, const double* eps_in, cudaStream_t s, bool c
         k_jacobi_dinv<3><<<nblk(D.d.n_slots), kBlock, 0, s>>>(D.d, D.eps, ah, H.opt.omega, D.dinv);
     }
   }
-  {
-    DevLevel& C = H.lv[H.c];
-    const double* ah = (H.c < H.top && H.galerkin) ? C.ahat : nullptr;
-    if (d == 2)
-      k_coarse_assemble<2><<<nblk(H.n_c), kBlock, 0, s>>>(C.d, C.eps, ah, H.c_slots, H.c_map, H.n_c, H.c_mat);
-    else
-      k_coarse_assemble<3><<<nblk(H.n_c), kBlock, 0, s>>>(C.d, C.eps, ah, H.c_slots, H.c_map, H.n_c, H.c_mat);
-    k_cholesky<<<1, kBlock, 0, s>>>(H.c_mat, H.n_c, H.d_status);
-  }
+  coarse_factor(H, s);
   MG_CHECK(last_launch("setup: coarse factor"));
   if (H.mixed) {
     const int n3 = ipow(3, d), n5 = ipow(5, d);
+    if (H.tensor) {
+      DevLevel& F = H.lv[H.L];
+      k_to_f32<<<nblk(d * F.d.n_slots), kBlock, 0, s>>>(d * F.d.n_slots, F.aniso, F.aniso32);
+    }
     for (int l = H.c; l <= H.L; ++l) {
       DevLevel& D = H.lv[l];
       k_to_f32<<<nblk(D.d.n_slots), kBlock, 0, s>>>(D.d.n_slots, D.eps, D.eps32);
@@ -1182,6 +1417,12 @@ static mg_status solve_fp64(Hier& H, double* u, const double* b, double tol, int
   }
   double rel = r0 > 0 ? 1.0 : 0.0;
   int cycles = 0;
+  if (H.opt.dynamic_coarsest && H.c != H.c_setup) {
+    // rule (b) raised the coarsest level in an earlier solve: every solve starts from
+    // the level the setup chose (rule (a))
+    set_coarsest(H, H.c_setup);
+    coarse_factor(H, s);
+  }
   while (rel > tol && cycles < max_cycles) {
     MG_CHECK(graph_launch(H, H.g_cycle64, u, b, s, [&](cudaStream_t ss) {
       vcycle<double>(H, H.L, u, b, ss);
@@ -1190,7 +1431,21 @@ static mg_status solve_fp64(Hier& H, double* u, const double* b, double tol, int
     }));
     MG_TRY_CUDA(cudaStreamSynchronize(s));
     ++cycles;
+    const double prev = rel;
     rel = std::sqrt(H.h_pin[0]) / r0;
+    if (H.opt.dynamic_coarsest && rel > tol && rel > 0.95 * prev && H.c < H.c_max) {
+      // Sect. 4.3, rule (b): the residual stagnated or grew, raise the coarsest level
+      set_coarsest(H, H.c + 1);
+      MG_TRY_CUDA(cudaMemsetAsync(H.d_status, 0, sizeof(int), s));
+      coarse_factor(H, s);
+      int status = 0;
+      MG_TRY_CUDA(cudaMemcpyAsync(&status, H.d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+      MG_TRY_CUDA(cudaStreamSynchronize(s));
+      if (status != 0) {
+        set_error("mg_solve: the raised coarsest level is not positive definite");
+        return MG_ERR_INDEFINITE_COARSE;
+      }
+    }
     if (st && st->history && st->history_len < st->history_capacity) st->history[st->history_len++] = rel;
     if (!std::isfinite(rel)) {
       set_error("mg_solve: non-finite residual");
@@ -1864,6 +2119,21 @@ mg_status mg_setup(mg_hier* h, const double* eps, void* stream) {
   return run_setup(*H, eps, pick(*H, stream));
 }
 
+mg_status mg_setup_tensor(mg_hier* h, const double* eps_axes, void* stream) {
+  Hier* H = H_(h);
+  if (!H || !eps_axes) {
+    set_error("mg_setup_tensor: NULL argument");
+    return MG_ERR_INVALID_ARG;
+  }
+  if (!H->tensor) {
+    set_error("mg_setup_tensor: the hierarchy was created without tensor_coefficients");
+    return MG_ERR_INVALID_ARG;
+  }
+  H->ready = false;
+  cudaStream_t s = pick(*H, stream);
+  return run_setup(*H, nullptr, s, true, eps_axes);
+}
+
 mg_status mg_smooth(mg_hier* h, int level, double* u, const double* b, int nu, void* stream) {
   Hier* H = H_(h);
   MG_CHECK(check_level(H, level, true));
@@ -2071,9 +2341,9 @@ mg_status mg_get_stencils(mg_hier* h, int level, double* st, void* stream) {
   const double* ah = (level < H->top && H->galerkin) ? D.ahat : nullptr;
   cudaStream_t s = pick(*H, stream);
   if (H->dim == 2)
-    k_export_stencils<2><<<nblk(D.d.n_slots), kBlock, 0, s>>>(D.d, D.eps, ah, st, nullptr);
+    k_export_stencils<2><<<nblk(D.d.n_slots), kBlock, 0, s>>>(D.d, D.eps, ah, st, nullptr, D.aniso);
   else
-    k_export_stencils<3><<<nblk(D.d.n_slots), kBlock, 0, s>>>(D.d, D.eps, ah, st, nullptr);
+    k_export_stencils<3><<<nblk(D.d.n_slots), kBlock, 0, s>>>(D.d, D.eps, ah, st, nullptr, D.aniso);
   return last_launch("mg_get_stencils");
 }
 
@@ -2229,6 +2499,16 @@ mg_status mg_get_bpa(mg_hier* h, int level, uint64_t* a_rec, uint8_t* a_stream, 
   if (a_bytes) *a_bytes = D.abpa ? used[0] : 0;
   if (p_bytes) *p_bytes = D.pbpa ? used[1] : 0;
   return last_launch("mg_get_bpa");
+}
+
+mg_status mg_get_coarsest(mg_hier* h, int32_t* level) {
+  Hier* H = H_(h);
+  if (!H || !level) {
+    set_error("mg_get_coarsest: NULL argument");
+    return MG_ERR_INVALID_ARG;
+  }
+  *level = H->c;
+  return MG_OK;
 }
 
 void mg_destroy_hier(mg_hier* h) { free_hier(H_(h), true); }

@@ -90,3 +90,44 @@ def test_batch_retires_converged_and_reports_unconverged():
     assert status == 4  # MG_ERR_NOT_CONVERGED for the problems that needed more cycles
     assert stats[1]["cycles"] == 0 and float(us[1].abs().max()) == 0.0
     assert stats[0]["cycles"] == 3 and stats[2]["cycles"] == 3
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed_bf16"])
+@pytest.mark.parametrize("dim,levels", [(2, SIZES_2D), (3, [2, 3, 2, 3])])
+def test_persistent_batch_steps_equal_lockstep_steps(dim, levels, precision):
+    # options.persistent: every step of the batch in one persistent launch over a work
+    # queue with per-problem progress counters.  The entries run the lockstep schedule's
+    # per-vertex arithmetic, so each problem takes the same cycles and reaches the same
+    # iterate; only the norm's partial sums are added in another grouping (FP64: within
+    # 1e-12; mixed: the scaling sigma moves the FP32 iterates within their own rounding)
+    mg = lib()
+    import torch
+
+    res, us = {}, {}
+    for persistent in (0, 1):
+        probs = []
+        for i, L in enumerate(levels):
+            eps = syn.lognormal_grf_eps(L, dim, sigma=2.0, seed=1000 + i)
+            g = mg.Grid(dim, L)
+            H = mg.Hierarchy(g, precision=precision, persistent=persistent)
+            e = torch.from_numpy(g.cells_to_concat({L: eps})).cuda()
+            H.setup(e)
+            b = torch.from_numpy(g.to_slots(L, syn.uniform_load(L, dim, 2000 + i))).cuda()
+            probs.append((H, b, eps, g, L, i))
+        batch = mg.Batch([p[0] for p in probs])
+        u = [torch.zeros_like(p[1]) for p in probs]
+        status, stats = batch.solve(u, [p[1] for p in probs], rel_tol=1e-10, max_cycles=2000)
+        assert status == 0
+        res[persistent], us[persistent] = stats, [x.cpu().numpy() for x in u]
+        if persistent and precision == "fp64":
+            for (H, b, eps, g, L, i), x in zip(probs, us[1]):
+                O = multigrid.Hierarchy(stt.Spacetree(dim, L), {L: eps})
+                assert rel_inf(x, O.direct(g.to_slots(L, syn.uniform_load(L, dim, 2000 + i)))) < 1e-8
+    for a, b_, sa, sb in zip(us[0], us[1], res[0], res[1]):
+        assert sb["rel_residual"] <= 1e-10
+        if precision == "fp64":
+            assert sa["cycles"] == sb["cycles"]
+            assert rel_inf(b_, a) < 1e-12
+        else:
+            assert abs(sa["cycles"] - sb["cycles"]) <= 8  # one refinement step
+            assert rel_inf(b_, a) < 1e-8
