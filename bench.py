@@ -483,7 +483,7 @@ def run_ours(args):
             total_ms += e0.elapsed_time(e1)
             stats.append(res)
             o = H.options
-            if o.cycle == 1:  # setup and r0 as for V-cycles; per traversal and level: 3 prolongations,
+            if o.cycle in (1, 2):  # setup and r0 as for V-cycles; per traversal and level: 3 prolongations,
                 # negate, 2 residuals, correction, inject, restrict; the finest residual norm
                 lv = L - o.coarsest_level
                 launches += kernel_count(L, o.coarsest_level, o.nu1, o.nu2, w["transfer"], w["coarse"], prec,
@@ -613,7 +613,7 @@ def run_ours(args):
                        "tiles": tiles or "default rule",
                        "smoother": "damped Jacobi" if not smo else f"block Jacobi, {args.gs_sweeps} Gauss-Seidel "
                                                                      f"sweep(s) per patch (Sect. 4.2)",
-                       "cycle": "V(2,2)" if not cyc else "additive (Alg. 2)"},
+                       "cycle": "V(2,2)" if not cyc else {"additive": "additive (Alg. 2)", "bpx": "BPX (Alg. 3)"}[args.cycle]},
             "mixed": None if not (domx and do64) else {
                 "value": value_mx, "unit": "DoF/s", "dtype": "f32 cycles + f64 refinement, bf16 deltas",
                 "ms_per_step": tmx / args.steps, "inner_cycles": stmx[-1]["cycles"],
@@ -729,6 +729,17 @@ def run_sweeps(args):
     u32 = torch.zeros_like(b32)
     hbm, src = peaks()
     out = {"workload": f"sweep{d}d-l{L}", "dofs": n_dofs}
+    if H64 is not None:  # the FP64 setup of this grid (BoxMG, Galerkin R A P, deltas, coarse factor)
+        ts = []
+        for _ in range(3):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            H64.setup(eps_dev)
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        out["setup_fp64_ms"] = min(ts)
     for name, bpd in (("fp64", BYTES_PER_DOF_SWEEP_FP64), ("fp32", BYTES_PER_DOF_SWEEP_FP32)):
         if args.sweep_prec not in ("both", name):
             continue
@@ -1027,8 +1038,8 @@ def main():
     ap.add_argument("--smoother", default="jacobi", choices=("jacobi", "block"),
                     help="smoother of the timed solves (the workloads are defined with damped Jacobi)")
     ap.add_argument("--gs-sweeps", type=int, default=1, help="block smoother: Gauss-Seidel sweeps per patch")
-    ap.add_argument("--cycle", default="v", choices=("v", "additive"),
-                    help="multigrid cycle of the timed FP64 solve (additive: Alg. 2; FP64 only)")
+    ap.add_argument("--cycle", default="v", choices=("v", "additive", "bpx"),
+                    help="multigrid cycle of the timed FP64 solve (additive: Alg. 2, bpx: Alg. 3; FP64 only)")
     ap.add_argument("--codecs", action="store_true",
                     help="mixed solves with BF16 deltas against the bpa codec at eps_mf 1e-2 / 1e-4 / 1e-8")
     ap.add_argument("--batched", action="store_true", help="512 uneven 2D problems solved as one batch: mixed vs FP64")

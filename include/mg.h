@@ -170,9 +170,11 @@ typedef struct mg_options {
   int32_t coarsest_level; /* level solved directly (FP64 Cholesky), 1 <= c < max_level */
   int32_t inner_cycles;   /* mixed: FP32 V-cycles per refinement step */
   int32_t use_graphs;     /* host-stepped solve: capture cycles in CUDA graphs */
-  int32_t persistent;     /* 1: whole solve in one cooperative persistent launch;
-                             0: host-stepped, CUDA-graph-captured cycles (default: on GB300 a
-                             dependent graph kernel costs ~0.6 us, a grid-wide barrier ~1.2 us) */
+  int32_t persistent;     /* 1: whole solve in one cooperative persistent launch (batches: every
+                             step in one persistent launch over a work queue, see
+                             mg_batch_create); 0: host-stepped, CUDA-graph-captured cycles
+                             (default: on GB300 a dependent graph kernel costs ~0.6 us, a
+                             grid-wide barrier ~1.2 us) */
   double eps_mf;          /* MG_PREC_MIXED_BPA: absolute bound on |f_bpa(x) - x| per delta entry
                              (Sect. 5 uses 1e-2, 1e-4, 1e-8); default 1e-4 */
   int32_t smoother;       /* mg_smoother (default MG_SMOOTH_JACOBI); nu1, nu2 count its steps */
@@ -358,7 +360,12 @@ typedef struct mg_batch mg_batch;
 /* Group n set-up hierarchies (same dimension and options, any sizes) into one batch.
  * The problems of a batch advance through their V-cycles in lockstep, aligned by
  * depth below their own finest level; every phase of a cycle is one launch per brick
- * edge over the work items of all problems.  hiers: host array of n handles that must
+ * edge over the work items of all problems.  With options.persistent = 1 on every
+ * hierarchy (BoxMG + Galerkin with BF16 codes, or geometric hierarchies), every step
+ * (an FP64 cycle, or a mixed refinement step with its inner cycles) is instead one
+ * persistent launch over a device work queue of the problems' items in phase order,
+ * each problem advancing by its own progress counter; a wait that runs out makes
+ * mg_batch_solve return MG_ERR_TIMEOUT.  hiers: host array of n handles that must
  * outlive the batch (the batch reads their operators; re-running mg_setup on them
  * keeps the batch valid).  Errors: MG_ERR_INVALID_ARG on mismatched options or
  * hierarchies not set up (or with more than 64 coarsest DoFs). */
@@ -394,12 +401,15 @@ typedef struct mg_request {
   int32_t reserved;
 } mg_request;
 
-/* Start a server on the current device: a thread that admits queued requests whose
- * hierarchies fit the rest of hbm_budget_bytes (scanning in arrival order; a request
- * that does not fit yet does not hold back later ones that do), sets them up, and runs
- * all admitted requests as one continuously re-formed batch (requests join at the next
- * step boundary and retire, releasing their memory, as soon as they converge).  opt:
- * options of every request (NULL = defaults). */
+/* Start a server on the current device: it admits queued requests whose hierarchies
+ * fit the rest of hbm_budget_bytes (scanning in arrival order; a request that does not
+ * fit yet does not hold back later ones that do), sets them up, and runs the admitted
+ * requests in three lanes by finest-level size (under 2^16 DoFs, under 2^20, larger),
+ * each a continuously re-formed batch on its own stream and thread, the smaller lanes at
+ * higher stream priority (requests join at their lane's next step boundary and retire,
+ * releasing their memory, as soon as they converge).  opt: options of every request
+ * (NULL = defaults; options.persistent = 1 runs the lanes' steps as persistent
+ * launches). */
 mg_status mg_server_create(size_t hbm_budget_bytes, const mg_options* opt, mg_server** out);
 
 /* Queue a request; *ticket identifies it.  The request's buffers must stay valid until

@@ -104,7 +104,7 @@ __device__ void q_sweep(const BatchArgs<T>& ba, const QItem& it, unsigned char* 
   } while (0)
   if (finest || AMC == 0) MG_QS(0); else MG_QS(AMC);
 #undef MG_QS
-  if (op != kJacobi && ba.partial) {
+  if (op != kJacobi && ba.partial && it.aux >= 0) {  // norm sweeps only: cycle residuals carry no slot
     const double s = block_sum(part);
     if (threadIdx.x == 0) ba.partial[it.aux] = s;
   }
@@ -184,7 +184,7 @@ __device__ inline void q_update_scale(const QueueArgs& q, const QItem& it, bool 
 }
 
 template <int DIM, int AMC64, int PM64, int AMC32, int PM32>
-__global__ void __launch_bounds__(128) k_bpersist(QueueArgs q) {
+__global__ void __launch_bounds__(128, 6) k_bpersist(QueueArgs q) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_t, s_ok;
   for (;;) {
@@ -202,12 +202,12 @@ __global__ void __launch_bounds__(128) k_bpersist(QueueArgs q) {
           ok = 0;
           break;
         }
-        if (++spins > (1u << 22)) {  // about a second of waiting: give up
+        if (++spins > (1u << 24)) {  // about a second of waiting: give up
           atomicExch(q.err, 2);
           ok = 0;
           break;
         }
-        __nanosleep(256);
+        __nanosleep(64);
       }
       __threadfence();
       s_ok = ok && !*static_cast<volatile int*>(q.err);

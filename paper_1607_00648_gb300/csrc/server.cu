@@ -6,9 +6,10 @@
 // step boundary, so work from requests that arrived while others were on the GPU
 // overlaps with theirs on the device.  Requests run in three lanes by size (finest
 // level under 2^16 DoFs, under 2^20, larger), each a batch on its own stream at its
-// own priority (the smallest highest): a lane of small problems takes many short steps
-// while a step of larger problems is still on the GPU, so a small request is held
-// neither to the pace of the largest ones nor to that of mid-sized ones.  After every step of a lane (an FP64 cycle, or a
+// own priority (the smallest highest) and with its own stepping thread: a lane of small
+// problems takes many short steps while a step of larger problems is still on the GPU,
+// so a small request is held neither to the pace of the largest ones nor to that of
+// mid-sized ones, nor to the host work of another lane's re-forms.  After every step of a lane (an FP64 cycle, or a
 // refinement step with its inner FP32 cycles) its converged requests retire: their
 // statistics are recorded, their hierarchy is released and its budget returns to the
 // queue.  The per-request arithmetic is that of a batch, so a request's result does
@@ -70,7 +71,7 @@ struct Server {
   uint64_t next_ticket = 1;
   bool stop = false;
   std::string error;
-  std::thread th;
+  std::thread th[3];  // one stepping thread per lane
   // setup streams per lane; a smaller lane's streams (setups and steps) run at a higher
   // priority so that their short kernels are not queued behind larger problems' long ones
   static constexpr int kLanes = 3;
@@ -103,7 +104,8 @@ struct Server {
   static constexpr int64_t kLargeDofs = int64_t(1) << 20;  // finest-level DoFs of a large problem
   Lane lanes[kLanes];
 
-  void loop();
+  void loop(int lane);
+  void admit(int lane);
   void retire(Request* r, mg_status st, bool release = true);
   void release(Request* r);  // hierarchy and budget of a finished request (mu held)
   bool start_step(Lane& ln, int lane);   // re-form the batch if needed, enqueue a step
@@ -172,38 +174,62 @@ void Server::worker(int lane) {
   }
 }
 
-void Server::loop() {
+// admission of the queued requests of one lane by the shared HBM budget, in arrival
+// order with backfill (a request that does not fit yet keeps its place, later ones that
+// fit go ahead of it); mu held
+void Server::admit(int lane) {
+  bool admitted = false;
+  for (auto it = queue.begin(); it != queue.end();) {
+    Request* r = *it;
+    if (r->lane != lane || used + r->footprint > budget) {
+      ++it;
+      continue;
+    }
+    it = queue.erase(it);
+    used += r->footprint;
+    r->state = 1;
+    r->t_admit = Clock::now();
+    to_create[r->lane].push_back(r);
+    admitted = true;
+  }
+  if (admitted) cv.notify_all();
+}
+
+// One stepping thread per lane: a lane's re-forms (host tables, uploads) and its step
+// bookkeeping never hold back another lane's steps.  Each thread admits the queued
+// requests of its own lane (by the shared HBM budget, in arrival order with backfill),
+// moves its lane's finished setups into the running set, and steps its lane's batch.
+void Server::loop(int lane) {
   cudaSetDevice(device);
+  Lane& ln = lanes[lane];
   for (;;) {
     {
       std::unique_lock<std::mutex> lk(mu);
-      cv.wait(lk, [&] { return stop || !queue.empty() || !running.empty() || !pending.empty(); });
+      auto has_work = [&] {
+        if (stop) return true;
+        for (Request* r : queue)
+          if (r->lane == lane && used + r->footprint <= budget) return true;
+        for (Request* r : pending)
+          if (r->lane == lane) return true;
+        for (Request* r : running)
+          if (r->lane == lane) return true;
+        return !ln.members.empty();
+      };
+      // pending setups complete without a notification: look again every 100 us
+      while (!has_work()) cv.wait_for(lk, std::chrono::microseconds(100));
       if (stop) break;
-      // admission by HBM footprint, in arrival order with backfill: a request that does
-      // not fit yet keeps its place, later ones that fit go ahead of it
-      for (auto it = queue.begin(); it != queue.end();) {
-        Request* r = *it;
-        if (used + r->footprint > budget) {
-          ++it;
-          continue;
-        }
-        it = queue.erase(it);
-        used += r->footprint;
-        r->state = 1;
-        r->t_admit = Clock::now();
-        to_create[r->lane].push_back(r);
-      }
-      cv.notify_all();
-      // requests whose setup finished join the running set
+      admit(lane);
+      // requests of this lane whose setup finished join the running set
       std::vector<Request*> still;
       for (Request* r : pending) {
-        if (cudaEventQuery(r->ev) == cudaErrorNotReady) {
+        if (r->lane != lane || cudaEventQuery(r->ev) == cudaErrorNotReady) {
           still.push_back(r);
           continue;
         }
         const mg_status st = setup_status(*r->h, *reinterpret_cast<const int*>(r->h->h_pin + 15));
         if (st != MG_OK) {
           retire(r, st);
+          cv.notify_all();
         } else {
           r->state = 2;
           running.push_back(r);
@@ -211,34 +237,24 @@ void Server::loop() {
       }
       pending.swap(still);
     }
-    // each idle lane starts its next step; then wait until one of them completes
-    bool any = false;
-    for (int k = 0; k < kLanes; ++k) {
-      if (!lanes[k].in_flight) start_step(lanes[k], k);
-      any = any || lanes[k].in_flight;
+    if (!ln.in_flight && !start_step(ln, lane)) {
+      // nothing to step: wait for a setup of this lane or a new request
+      std::this_thread::sleep_for(std::chrono::microseconds(20));
+      continue;
     }
-    if (!any) continue;
-    // ... or until there is other work for the loop: a queued request that fits, a
-    // finished setup (its request joins an idle lane at once, not after the other
-    // lane's long step)
-    for (bool progressed = false; !progressed;) {
-      for (int k = 0; k < kLanes; ++k) {
-        Lane& ln = lanes[k];
-        if (!ln.in_flight) continue;
-        const cudaError_t q = cudaEventQuery(ln.done);
-        if (q == cudaErrorNotReady) continue;
-        finish_step(ln);
-        progressed = true;
-      }
-      if (progressed) break;
+    while (cudaEventQuery(ln.done) == cudaErrorNotReady) {
       {
         std::lock_guard<std::mutex> lk(mu);
-        progressed = stop;
-        for (Request* r : pending) progressed = progressed || cudaEventQuery(r->ev) != cudaErrorNotReady;
-        for (Request* r : queue) progressed = progressed || used + r->footprint <= budget;
+        if (stop) break;
+        admit(lane);  // new requests of the lane start their setups during a long step
       }
-      if (!progressed) std::this_thread::sleep_for(std::chrono::microseconds(20));
+      std::this_thread::sleep_for(std::chrono::microseconds(20));
     }
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      if (stop) break;
+    }
+    finish_step(ln);
   }
 }
 
@@ -407,7 +423,7 @@ mg_status mg_server_create(size_t hbm_budget_bytes, const mg_options* opt, mg_se
     return MG_ERR_CUDA;
   }
   try {
-    sv->th = std::thread([sv] { sv->loop(); });
+    for (int k = 0; k < Server::kLanes; ++k) sv->th[k] = std::thread([sv, k] { sv->loop(k); });
     for (int k = 0; k < Server::kLanes; ++k)
       for (int w = 0; w < Server::kWorkers[k]; ++w) sv->workers[k][w] = std::thread([sv, k] { sv->worker(k); });
   } catch (...) {
@@ -416,7 +432,8 @@ mg_status mg_server_create(size_t hbm_budget_bytes, const mg_options* opt, mg_se
       sv->stop = true;
       sv->cv.notify_all();
     }
-    if (sv->th.joinable()) sv->th.join();
+    for (auto& t : sv->th)
+      if (t.joinable()) t.join();
     for (int k = 0; k < Server::kLanes; ++k)
       for (auto& t : sv->workers[k])
         if (t.joinable()) t.join();
@@ -525,7 +542,8 @@ void mg_server_destroy(mg_server* server) {
     sv->stop = true;
     sv->cv.notify_all();
   }
-  if (sv->th.joinable()) sv->th.join();
+  for (auto& t : sv->th)
+    if (t.joinable()) t.join();
   for (int k = 0; k < Server::kLanes; ++k)
     for (auto& t : sv->workers[k])
       if (t.joinable()) t.join();

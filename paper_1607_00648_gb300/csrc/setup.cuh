@@ -242,10 +242,12 @@ __global__ void __launch_bounds__(kBlock) k_jacobi_dinv(LevelDesc L, const doubl
 template <int DIM>
 constexpr int rap_tpv() { return DIM == 2 ? 32 : 128; }
 
-// dynamic shared memory of k_rap<DIM, PMODE> (the staged P of the coarse neighbours)
+// dynamic shared memory of k_rap<DIM, PMODE>: the staged P of the coarse neighbours and
+// every thread's scaled fine stencil
 template <int DIM, int PMODE>
 constexpr size_t rap_dyn_smem() {
-  return static_cast<size_t>(128 / rap_tpv<DIM>()) * cpow(3, DIM) * cpow(5, DIM) * sizeof(double);
+  return (static_cast<size_t>(128 / rap_tpv<DIM>()) * cpow(3, DIM) * cpow(5, DIM) + 128 * cpow(3, DIM)) *
+         sizeof(double);
 }
 
 template <int DIM, int PMODE>
@@ -338,36 +340,41 @@ __global__ void __launch_bounds__(128) k_rap(LevelDesc Lc, LevelDesc Lf, const d
   }
   __syncthreads();
 
-  // c[q] = sum over stencil neighbours g of f with |g - 3W| <= 2 (W = V + o_q) of
-  // P(f,V) A_f(f,g) P(g,W).  Outer loop over g (not unrolled: a compact body), inner over
-  // the 3^d targets W with per-axis admissibility masks of the offset g - 3W
+  // c[q] = sum over stencil neighbours g = f + eps of f with |g - 3W| <= 2 (W = V + o_q)
+  // of P(f,V) A_f(f,g) P(g,W).  The scaled stencil goes to shared memory (zero where g is
+  // no DoF) and each target W loops over the admissible eps only: per axis
+  // eps in [max(-1, 3 o - 2 - d), min(1, 3 o + 2 - d)] (about 4 of the 3^d per target in
+  // 3D), so no fma is issued for a pair that contributes nothing
+  double* sst = pfull + VPB * N3 * N5 + threadIdx.x * N3;
+#pragma unroll
+  for (int e = 0; e < N3; ++e) sst[e] = ((gdof >> e) & 1u) ? st[e] : 0.0;
   double c[N3];
 #pragma unroll
   for (int q = 0; q < N3; ++q) c[q] = 0.0;
   if (gdof) {
     const double* pf = pfull + sub * N3 * N5;
-#pragma unroll 1
-    for (int e = 0; e < N3; ++e) {
-      if (!((gdof >> e) & 1u)) continue;
-      const double a = st[e];
-      int sg[3] = {0, 0, 0}, ee = e;
+#pragma unroll
+    for (int q = 0; q < N3; ++q) {
+      int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0}, pb[3] = {0, 0, 0};
+      int qq = q;
 #pragma unroll
       for (int i = 0; i < DIM; ++i) {
-        sg[i] = d[i] + ee % 3 - 1;  // g - 3V per axis, in [-3, 3]
-        ee /= 3;
+        const int o = qq % 3 - 1;
+        qq /= 3;
+        lo[i] = max(-1, 3 * o - 2 - d[i]);
+        hi[i] = min(1, 3 * o + 2 - d[i]);
+        pb[i] = d[i] - 3 * o + 2;  // offset index of g - 3W at eps = 0, per axis
       }
-      bool ok[3][3];
-#pragma unroll
-      for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int o = -1; o <= 1; ++o) ok[i][o + 1] = i < DIM ? abs(sg[i] - 3 * o) <= 2 : o == 0;
-      const int base = (sg[0] + 2) + 5 * (sg[1] + 2) + (DIM == 3 ? 25 * (sg[2] + 2) : 0);
-#pragma unroll
-      for (int q = 0; q < N3; ++q) {
-        const int ox = q % 3 - 1, oy = (q / 3) % 3 - 1, oz = DIM == 3 ? q / 9 - 1 : 0;
-        if (ok[0][ox + 1] && ok[1][oy + 1] && ok[2][oz + 1])
-          c[q] = fma(a, pf[q * N5 + base - 3 * (ox + 5 * oy + 25 * oz)], c[q]);
-      }
+      const double* pw = pf + q * N5;
+      double acc = 0.0;
+      for (int ez = lo[2]; ez <= hi[2]; ++ez)
+        for (int ey = lo[1]; ey <= hi[1]; ++ey)
+          for (int ex = lo[0]; ex <= hi[0]; ++ex) {
+            const int e = (ex + 1) + 3 * (ey + 1) + (DIM == 3 ? 9 * (ez + 1) : 0);
+            const int k = (pb[0] + ex) + 5 * (pb[1] + ey) + (DIM == 3 ? 25 * (pb[2] + ez) : 0);
+            acc = fma(sst[e], pw[k], acc);
+          }
+      c[q] = acc;
     }
   }
   // fixed-order reduction over the group: shuffles within each warp, then warps in order
