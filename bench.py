@@ -516,20 +516,27 @@ def run_ours(args):
     value = replica_throughput(n_dofs, args.steps, world, t64)
     value_mx = replica_throughput(n_dofs, args.steps, world, tmx) if domx else None
 
+    # the FP64 solve with float-float finest-level sweeps (FP64 vectors and setup)
+    ff = None
+    if do64 and not cyc and not smo and not args.no_ff:
+        Hff = mg.Hierarchy(grid, transfer=w["transfer"], coarse=w["coarse"], precision="fp64", ff_sweeps=1)
+        if not args.no_autotune:
+            Hff.setup(eps_dev)
+            tiles["fp64_ff"] = {str(k): v for k, v in Hff.autotune().items()}
+        with Clocks(torch.cuda.current_device()) as clk_ff:
+            tff, launchesff, stff = timed(Hff, args.steps, args.warmup, "fp64")
+        launches64 += launchesff
+        Hff.setup(eps_dev)
+        ff = {"value": replica_throughput(n_dofs, args.steps, world, tff), "unit": "DoF/s",
+              "dtype": "f64 vectors and setup, float-float finest-level sweeps",
+              "ms_per_step": tff / args.steps, "cycles": stff[-1]["cycles"],
+              "rel_residual": stff[-1]["rel_residual"], "clocks": clk_ff.summary(),
+              "sweep_us": sweep_time(Hff, L, b_dev, stream) * 1e6}
+        ff["speedup_vs_fp64"] = ff["value"] / value
+
     # dominant kernel: finest-level FP64 in-situ Jacobi sweep (two sweeps per call, no copy)
     H64.setup(eps_dev)
-    uu = torch.zeros_like(b_dev)
-    reps = 50
-    for _ in range(5):
-        H64.smooth(L, uu, b_dev, 2)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(reps):
-        H64.smooth(L, uu, b_dev, 2)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    sweep_s = e0.elapsed_time(e1) / 1e3 / (2 * reps)
+    sweep_s = sweep_time(H64, L, b_dev, stream)
     Hmx.setup(eps_dev)
     hbm_peak, peak_src = peaks()
     with Clocks(torch.cuda.current_device()) as clk_peak:
@@ -619,6 +626,7 @@ def run_ours(args):
                 "ms_per_step": tmx / args.steps, "inner_cycles": stmx[-1]["cycles"],
                 "outer_steps": stmx[-1]["outer_steps"], "rel_residual": stmx[-1]["rel_residual"],
                 "speedup_vs_fp64": value_mx / value},
+            "fp64_ff": ff,
             "roofline": roofline, "e2e": e2e, "clocks": clocks,
             "gpu_launches": launches64 + (launchesmx if domx else 0),
             "cpu_baseline": cpu,
@@ -627,6 +635,24 @@ def run_ours(args):
         print(json.dumps(out))
     if dist:
         dist.destroy_process_group()
+
+
+def sweep_time(H, L, b_dev, stream, reps=50):
+    """Seconds per finest-level Jacobi sweep of H (mg_smooth with two sweeps per call, CUDA
+    events on the launching stream, after 5 warm-up calls)."""
+    import torch
+
+    uu = torch.zeros_like(b_dev)
+    for _ in range(5):
+        H.smooth(L, uu, b_dev, 2)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        H.smooth(L, uu, b_dev, 2)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1e3 / (2 * reps)
 
 
 def run_codecs(args):
@@ -721,9 +747,12 @@ def run_sweeps(args):
     b64 = torch.from_numpy(grid.to_slots(L, syn.uniform_load(L, d, 1))).cuda()
     H = mg.Hierarchy(grid, precision="mixed_bf16")  # FP32 sweeps
     H.setup(eps_dev)
-    H64 = mg.Hierarchy(grid, precision="fp64") if args.sweep_prec != "fp32" else None
+    H64 = mg.Hierarchy(grid, precision="fp64") if args.sweep_prec in ("both", "fp64") else None
     if H64 is not None:
         H64.setup(eps_dev)
+    Hff = mg.Hierarchy(grid, precision="fp64", ff_sweeps=1) if args.sweep_prec in ("both", "ff") else None
+    if Hff is not None:
+        Hff.setup(eps_dev)
     u64 = torch.zeros_like(b64)
     b32 = b64.float()
     u32 = torch.zeros_like(b32)
@@ -740,10 +769,12 @@ def run_sweeps(args):
             torch.cuda.synchronize()
             ts.append(e0.elapsed_time(e1))
         out["setup_fp64_ms"] = min(ts)
-    for name, bpd in (("fp64", BYTES_PER_DOF_SWEEP_FP64), ("fp32", BYTES_PER_DOF_SWEEP_FP32)):
+    for name, bpd in (("fp64", BYTES_PER_DOF_SWEEP_FP64), ("ff", BYTES_PER_DOF_SWEEP_FP64),
+                      ("fp32", BYTES_PER_DOF_SWEEP_FP32)):
         if args.sweep_prec not in ("both", name):
             continue
-        fn, u, bb = (H64.smooth, u64, b64) if name == "fp64" else (H.smooth_f32, u32, b32)
+        fn, u, bb = {"fp64": (H64 and H64.smooth, u64, b64), "ff": (Hff and Hff.smooth, u64, b64),
+                     "fp32": (H.smooth_f32, u32, b32)}[name]
         for _ in range(3):
             fn(L, u, bb, 2)
         torch.cuda.synchronize()
@@ -759,7 +790,7 @@ def run_sweeps(args):
                      "peak_source": src, "Gdof/s": n_dofs / t / 1e9}
         if name == "fp64" and d == 2:
             out[name]["TFLOP/s"] = FLOPS_PER_DOF_SWEEP_2D * n_dofs / t / 1e12
-    if args.sweep_prec != "fp32":
+    if args.sweep_prec in ("both", "fp64"):
         out["fp64_peak_tflops"] = fp64_peak_tflops(mg, torch)
         if "TFLOP/s" in out.get("fp64", {}):
             out["fp64"]["fp64_frac"] = out["fp64"]["TFLOP/s"] / out["fp64_peak_tflops"]
@@ -1029,6 +1060,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="checker2d-l6", choices=sorted(WORKLOADS) + sorted(ADAPTIVE))
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline leg")
+    ap.add_argument("--no-ff", action="store_true",
+                    help="skip the FP64 solve with float-float finest-level sweeps")
     ap.add_argument("--no-a13", action="store_true",
                     help="skip the reduced batched and served measurements of the default line")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default slab depths (no mg_autotune)")
@@ -1053,7 +1086,8 @@ def main():
     ap.add_argument("--sweep-level", type=int, default=0,
                     help="time only the finest-level FP64 / FP32 sweeps on a uniform grid of this level")
     ap.add_argument("--sweep-dim", type=int, default=2, choices=(2, 3))
-    ap.add_argument("--sweep-prec", default="both", choices=("both", "fp64", "fp32"))
+    ap.add_argument("--sweep-prec", default="both", choices=("both", "fp64", "fp32", "ff"),
+                    help="both = fp64 + fp32 + ff (float-float finest sweeps of an FP64 hierarchy)")
     args = ap.parse_args()
     if args.precision == "bpa" and not args.breakdown:
         ap.error("--precision bpa goes with --breakdown (bench.py --codecs times the codecs)")

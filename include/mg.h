@@ -195,6 +195,21 @@ typedef struct mg_options {
                              default 0).  Uniform grids, Galerkin coarse operators, Jacobi smoother,
                              single hierarchies (not batches, the server, the persistent solve or
                              the bpa codec) */
+  int32_t ff_sweeps;      /* 1: the finest level's Jacobi and residual sweeps of an FP64 hierarchy run
+                             in float-float arithmetic (value = h + l of two binary32 numbers,
+                             error-free TwoSum / TwoProduct; GB300's FP64 units run at ~1/64 of its
+                             FP32 rate).  Vectors and the setup stay binary64; a sweep result
+                             differs from FP64 arithmetic by a few 2^-47 (instead of 2^-53) of the
+                             sum of its absolute terms, so mg_smooth, mg_residual and mg_vcycle
+                             return float-float results.  mg_solve runs float-float cycles while
+                             the relative residual exceeds 1000 x rel_tol (or until a cycle reduces
+                             it by less than 5%), then FP64 cycles: the solution carries the FP64
+                             residual floor (float-float alone stalls ~2^6 higher: near 1e-10 on
+                             the 2D level-6 1:1e-4 checkerboard).  Nonzero |values| must lie in
+                             [2^-103, 2^127): smaller ones count as zero, larger ones give NaN (a
+                             non-finite residual).  Single FP64 hierarchies with the Jacobi smoother
+                             and V-cycles, 2D and 3D (host-stepped solves; batches, the server and
+                             the persistent solve keep FP64 sweeps); default 0 */
 } mg_options;
 
 void mg_default_options(mg_options* opt); /* BoxMG, Galerkin, FP64, V(2,2), omega 0.6, coarsest 1, eps_mf 1e-4,

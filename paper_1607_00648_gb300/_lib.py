@@ -39,7 +39,7 @@ class Options(C.Structure):
                 ("coarsest_level", C.c_int32), ("inner_cycles", C.c_int32), ("use_graphs", C.c_int32),
                 ("persistent", C.c_int32), ("eps_mf", C.c_double), ("smoother", C.c_int32),
                 ("gs_sweeps", C.c_int32), ("cycle", C.c_int32), ("dynamic_coarsest", C.c_int32),
-                ("tensor_coefficients", C.c_int32)]
+                ("tensor_coefficients", C.c_int32), ("ff_sweeps", C.c_int32)]
 
 
 class SolveStats(C.Structure):

@@ -270,18 +270,22 @@ __device__ void full_stencil(const LevelDesc& L, const double* eps, const double
       kk /= 3;
       ham += o[i] != 0;
     }
+    // (elem_k scale) es: one multiply per entry; the 3D face entries have elem_k = 0
+    // (trilinear element) and are exact zeros
     double es = 0.0;
+    if (elem_k(DIM, ham) != 0.0) {
 #pragma unroll
-    for (int e = 0; e < (1 << DIM); ++e) {
-      bool ok = true;
+      for (int e = 0; e < (1 << DIM); ++e) {
+        bool ok = true;
 #pragma unroll
-      for (int i = 0; i < DIM; ++i) {
-        const int t = ((e >> i) & 1) + o[i];
-        ok = ok && t >= 0 && t <= 1;
+        for (int i = 0; i < DIM; ++i) {
+          const int t = ((e >> i) & 1) + o[i];
+          ok = ok && t >= 0 && t <= 1;
+        }
+        if (ok) es += ec[e];
       }
-      if (ok) es += ec[e];
     }
-    st[k] = elem_k(DIM, ham) * es * scale;
+    st[k] = (elem_k(DIM, ham) * scale) * es;
     if (ahat && slot >= 0) st[k] += ahat[plane_index(L, slot, k, N3)];
     if (aniso && ham > 0) {
 #pragma unroll

@@ -38,6 +38,8 @@ struct DevLevel {
   double* aniso = nullptr;   // finest level of a tensor hierarchy: per-axis coefficient deviations
   float* aniso32 = nullptr;  // (axis-major, cell slots) and their FP32 copy
   double* dinv = nullptr;  // FP64 hierarchies: omega / diag(A) for the Jacobi sweeps
+  double* eps_pair = nullptr;   // float-float finest sweeps: eps and omega / diag(A) as
+  double* dinv_pair = nullptr;  // (h, l) float pairs in binary64 containers
   double *ad = nullptr, *ar = nullptr;  // additive cycle: correction d_l, surplus residual rh_l
   double* ai = nullptr;                 // BPX: injected skipped c-point updates i_l
   int32_t* child = nullptr;             // additive cycle: level-(l+1) slot at position 3x (injection)
@@ -90,6 +92,8 @@ struct Hier {
   int32_t* c_slots = nullptr;
   int32_t* c_map = nullptr;
   double* c_mat = nullptr;
+  double* ap3 = nullptr;  // 3D Galerkin setup: A_f P of the fine level (two-stage product)
+  int64_t ap3_len = 0;
   int* d_status = nullptr;
   double* d_scal = nullptr;  // [0] norm2 fp64, [1] norm2 fp32 inner, [2] sigma
   double* h_pin = nullptr;   // pinned mirror of d_scal
@@ -100,6 +104,8 @@ struct Hier {
   cudaStream_t own = nullptr;
   bool ready = false;
   Graph g_cycle64, g_outer, g_inner, g_comp64, g_comp_outer, g_comp_inner, g_add;
+  Graph g_cycle_ff, g_comp_ff;  // FP64 solves: cycles with float-float finest sweeps
+  bool ff_active = true;   // float-float finest sweeps in use (when the setup split the pairs)
 };
 
 // ---- device memory of hierarchies and batches (solver.cu) ----

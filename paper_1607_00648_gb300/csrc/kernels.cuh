@@ -27,6 +27,11 @@ struct SweepArgs {
   int R;                // slab thickness along the last axis (divides B)
   const T* dinv;        // Jacobi: omega / diag(A) per vertex (setup), nullable
   int block;            // Jacobi of a block step (Sect. 4.2): iota vertices keep their value
+  // float-float sweeps of the finest FP64 level (sweep_ff.cuh): the cell coefficients and
+  // omega / diag(A) pre-split into (h, l) float pairs, each in a binary64 container (low
+  // word h); nullptr: FP64 arithmetic
+  const double* eps_pair;
+  const double* dinv_pair;
 };
 
 // iota vertex of brick slot s (local coordinates; bricks start at multiples of 3): no

@@ -6,6 +6,7 @@
 
 #include "kernels.cuh"
 #include "sweep_fast.cuh"
+#include "sweep_ff.cuh"
 
 namespace mg {
 
@@ -57,12 +58,18 @@ static void sweep_b(SweepArgs<T> a, int op, int amode, cudaStream_t s) {
     // instructions per vertex; Jacobi takes omega / diag(A) from the setup
     if constexpr (std::is_same<T, double>::value && ((DIM == 2 && B == 27) || (DIM == 3 && B == 9))) {
       const dim3 grid(static_cast<unsigned>(a.L.n_bricks), static_cast<unsigned>(B / R));
+      // float-float arithmetic on the finest level when the setup split its coefficients
+      const bool ff = a.eps_pair != nullptr && amode == 0 && !a.block;
 #define MG_SWR(AM, OP, RR)                                                                                  \
   do {                                                                                                      \
-    if constexpr (DIM == 2)                                                                                 \
-      launch_pdl(k_sweep2f<AM, OP, RR>, grid, RR >= 3 ? 96 : 32, 0, s, a);                                  \
-    else                                                                                                    \
+    if constexpr (DIM == 2) {                                                                               \
+      if (AM == 0 && ff) launch_pdl(k_sweep2x<OP, RR>, grid, RR >= 3 ? 96 : 32, 0, s, a);                   \
+      else launch_pdl(k_sweep2f<AM, OP, RR>, grid, RR >= 3 ? 96 : 32, 0, s, a);                             \
+    } else if (AM == 0 && ff) {                                                                             \
+      launch_pdl(k_sweep3x<OP, (RR > 9 ? 9 : RR)>, grid, 128, sweep_tile_bytes<DIM, T>(B, RR > 9 ? 9 : RR, true), s, a); \
+    } else {                                                                                                \
       launch_pdl(k_sweep3c<T, AM, OP, (RR > 9 ? 9 : RR)>, grid, 128, sweep_tile_bytes<DIM, T>(B, RR > 9 ? 9 : RR, true), s, a); \
+    }                                                                                                       \
   } while (0)
 #define MG_SW(AM, OP)                                                    \
   do {                                                                   \

@@ -17,6 +17,7 @@
 #include "internal.h"
 #include "kernels.cuh"
 #include "persist.cuh"
+#include "rap3.cuh"
 #include "setup.cuh"
 
 namespace mg {
@@ -27,6 +28,17 @@ extern template cudaError_t persist_launch_mixed<2>(const PSolve<float>*, int, i
 extern template cudaError_t persist_launch_mixed<3>(const PSolve<float>*, int, int, size_t, cudaStream_t, int*);
 
 // ----------------------------------------------------------------------------- small kernels
+
+// binary64 -> (h, l) float pair rounded to nearest twice (h = fl32(v), l = fl32(v - h)),
+// packed into a binary64 container (low word h, high word l) for the float-float sweeps
+__global__ void k_split_pairs(int64_t n, const double* v, double* out) {
+  const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (i >= n) return;
+  const double x = v[i];
+  const float h = __double2float_rn(x);
+  const float l = __double2float_rn(x - static_cast<double>(h));
+  out[i] = __hiloint2double(__float_as_int(l), __float_as_int(h));
+}
 
 __global__ void k_leaf_eps(LevelDesc L, const uint8_t* cflags, const double* eps_in, double* eps) {
   const int64_t s = blockIdx.x * static_cast<int64_t>(kBlock) + threadIdx.x;
@@ -617,6 +629,8 @@ static void free_hier(Hier* H, bool device_sync) {
   if (!H) return;
   if (device_sync) cudaDeviceSynchronize();
   H->g_cycle64.reset();
+  H->g_cycle_ff.reset();
+  H->g_comp_ff.reset();
   H->g_outer.reset();
   H->g_inner.reset();
   H->g_comp64.reset();
@@ -668,6 +682,11 @@ static mg_status create(const Grid* g, const mg_options& o, Hier** out, int prio
   const int n3 = ipow(3, d), n5 = ipow(5, d);
   H->lv.resize(H->L + 1);
   mg_status st;
+  if (d == 3 && H->galerkin && H->top > H->c && g->levels[H->top].B == 9) {
+    // two-stage 3D Galerkin product: AP scratch of the largest fine level (rap3.cuh)
+    H->ap3_len = static_cast<int64_t>(g->levels[H->top].n_bricks) * kApPerBrick;
+    if ((st = dalloc(*H, &H->ap3, static_cast<size_t>(H->ap3_len))) != MG_OK) return fail(st);
+  }
   for (int l = H->c; l <= H->L; ++l) {
     const HostLevel& hl = g->levels[l];
     DevLevel& D = H->lv[l];
@@ -710,6 +729,10 @@ static mg_status create(const Grid* g, const mg_options& o, Hier** out, int prio
     }
     if ((st = dalloc(*H, &D.partial, static_cast<size_t>(hl.n_bricks) * hl.B)) != MG_OK) return fail(st);
     if (!H->mixed && (st = dalloc(*H, &D.dinv, ns)) != MG_OK) return fail(st);
+    if (!H->mixed && o.ff_sweeps && l == H->L) {  // float-float finest sweeps: split coefficients
+      if ((st = dalloc(*H, &D.eps_pair, ns)) != MG_OK) return fail(st);
+      if ((st = dalloc(*H, &D.dinv_pair, ns)) != MG_OK) return fail(st);
+    }
     if ((st = dalloc(*H, &D.counter, 1)) != MG_OK) return fail(st);
     if (l < H->L) {
       if ((st = dalloc(*H, &D.u, ns)) != MG_OK) return fail(st);
@@ -860,6 +883,7 @@ mg_status hier_create(const Grid* g, const mg_options& o, int priority, Hier** o
       o.tensor_coefficients < 0 || o.tensor_coefficients > 1 ||
       (o.tensor_coefficients && (o.coarse != MG_COARSE_GALERKIN || o.smoother != MG_SMOOTH_JACOBI || o.persistent ||
                                  o.precision == MG_PREC_MIXED_BPA)) ||
+      o.ff_sweeps < 0 || o.ff_sweeps > 1 || (o.ff_sweeps && (o.precision != MG_PREC_FP64 || o.cycle != MG_CYCLE_V)) ||
       (o.precision == MG_PREC_MIXED_BPA && !(o.eps_mf >= 0.0 && o.eps_mf < 1e300))) {
     set_error("mg_hier_create: invalid options");
     return MG_ERR_INVALID_ARG;
@@ -908,7 +932,9 @@ size_t hier_footprint(const Grid& g, const mg_options& o) {
     if (o.cycle != MG_CYCLE_V) bytes += 2 * ns * 8 + (l < g.L ? ns * 4 : 0);
     if (o.cycle == MG_CYCLE_BPX && l < g.L) bytes += ns * 8;
     if (o.tensor_coefficients && l == g.L) bytes += ns * d * (mixed ? 12 : 8);
+    if (!mixed && o.ff_sweeps && l == g.L) bytes += 2 * ns * 8;  // split coefficients and omega / D
     if (l < top) bytes += (galerkin ? ns * n3 * 8 : 0) + (boxmg ? ns * n5 * 8 : 0);
+    if (d == 3 && galerkin && l == top && top > o.coarsest_level && hl.B == 9) bytes += nb * kApPerBrick * 8;
     if (mixed) {
       bytes += 5 * ns * 4;
       const size_t per = o.precision == MG_PREC_MIXED_BPA ? 8 : 2, sc = o.precision == MG_PREC_MIXED_BPA ? 8 : 4;
@@ -941,6 +967,10 @@ static SweepArgs<T> sweep_args(const Hier& H, int l, const T* u, const T* b, T* 
   if constexpr (std::is_same<T, double>::value) {
     a.eps = D.eps;
     a.dinv = D.dinv;
+    if (H.ff_active) {
+      a.eps_pair = D.eps_pair;
+      a.dinv_pair = D.dinv_pair;
+    }
     if (coarse) {
       *amode = 1;
       a.ahat = D.ahat;
@@ -1115,7 +1145,7 @@ static void set_coarsest(Hier& H, int c) {
   H.n_c = H.nc_lv[c];
   H.c_slots = H.cs_lv[c];
   H.c_map = H.cm_lv[c];
-  for (Graph* gr : {&H.g_cycle64, &H.g_outer, &H.g_inner, &H.g_comp64, &H.g_comp_outer, &H.g_comp_inner, &H.g_add})
+  for (Graph* gr : {&H.g_cycle64, &H.g_cycle_ff, &H.g_comp_ff, &H.g_outer, &H.g_inner, &H.g_comp64, &H.g_comp_outer, &H.g_comp_inner, &H.g_add})
     gr->reset();
 }
 
@@ -1226,6 +1256,24 @@ static mg_status run_setup(Hier& H, const double* eps_in, cudaStream_t s, bool c
           k_rap<2, 1><<<gr, 128, rap_dyn_smem<2, 1>(), s>>>(C.d, F.d, F.eps, ahat_f, C.eps, C.phat, C.ahat, F.aniso);
         else
           k_rap<2, 0><<<gr, 128, rap_dyn_smem<2, 0>(), s>>>(C.d, F.d, F.eps, ahat_f, C.eps, C.phat, C.ahat, F.aniso);
+      } else if (H.ap3 && F.d.B == 9 && F.d.n_bricks * kApPerBrick <= H.ap3_len) {
+        // two stages: AP = A_f P per fine vertex into the scratch, then P^T (AP) per coarse one
+        const unsigned g1 = static_cast<unsigned>((F.d.n_bricks * 27 * 27 + 127) / 128);
+        const unsigned g2 = static_cast<unsigned>((C.d.n_slots + kRapPtSlots - 1) / kRapPtSlots);
+        static const bool pt_opt_in = [] {
+          return cudaFuncSetAttribute(k_rap3_pt<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      static_cast<int>(rap3_pt_smem())) == cudaSuccess &&
+                 cudaFuncSetAttribute(k_rap3_pt<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      static_cast<int>(rap3_pt_smem())) == cudaSuccess;
+        }();
+        (void)pt_opt_in;
+        if (H.boxmg) {
+          k_rap3_ap<1><<<g1, 128, 0, s>>>(C.d, F.d, F.eps, ahat_f, C.phat, H.ap3, F.aniso);
+          k_rap3_pt<1><<<g2, 27 * 32, rap3_pt_smem(), s>>>(C.d, F.d, C.eps, C.phat, H.ap3, C.ahat);
+        } else {
+          k_rap3_ap<0><<<g1, 128, 0, s>>>(C.d, F.d, F.eps, ahat_f, C.phat, H.ap3, F.aniso);
+          k_rap3_pt<0><<<g2, 27 * 32, rap3_pt_smem(), s>>>(C.d, F.d, C.eps, C.phat, H.ap3, C.ahat);
+        }
       } else {
         const unsigned g3 = static_cast<unsigned>(C.d.n_slots);
         if (H.boxmg)
@@ -1251,6 +1299,10 @@ static mg_status run_setup(Hier& H, const double* eps_in, cudaStream_t s, bool c
         k_jacobi_dinv<2><<<nblk(D.d.n_slots), kBlock, 0, s>>>(D.d, D.eps, ah, H.opt.omega, D.dinv);
       else
         k_jacobi_dinv<3><<<nblk(D.d.n_slots), kBlock, 0, s>>>(D.d, D.eps, ah, H.opt.omega, D.dinv);
+    }
+    if (D.eps_pair) {
+      k_split_pairs<<<nblk(D.d.n_slots), kBlock, 0, s>>>(D.d.n_slots, D.eps, D.eps_pair);
+      k_split_pairs<<<nblk(D.d.n_slots), kBlock, 0, s>>>(D.d.n_slots, D.dinv, D.dinv_pair);
     }
   }
   coarse_factor(H, s);
@@ -1399,9 +1451,23 @@ static mg_status graph_launch(Hier& H, Graph& g, const void* k0, const void* k1,
   return MG_OK;
 }
 
+// FP64 solves with float-float finest sweeps switch to FP64 sweeps below this multiple of
+// the tolerance (their own residual floor is ~1e-10 on the 2D level-6 checkerboard, 1e-9
+// on level 7: a 1e-10 solve switches at 1e-7)
+constexpr double kFfSwitch = 1e3;
+
 static mg_status solve_fp64(Hier& H, double* u, const double* b, double tol, int max_cycles, mg_solve_stats* st,
                             cudaStream_t s) {
   DevLevel& F = H.lv[H.L];
+  // float-float finest sweeps (mg_options.ff_sweeps) carry the cycles while the residual
+  // is far above the tolerance; the last cycles run in FP64, whose residual floor lies
+  // ~2^6 below theirs (iterative refinement: the final iterate is the FP64 one)
+  const bool ff = F.eps_pair != nullptr;
+  struct Restore {
+    Hier& h;
+    ~Restore() { h.ff_active = true; }
+  } restore{H};
+  H.ff_active = false;  // r0 in FP64
   MG_TRY_CUDA(cudaMemsetAsync(u, 0, F.d.n_slots * sizeof(double), s));
   residual_norm<double>(H, u, b, F.r, 0, s);
   MG_TRY_CUDA(cudaMemcpyAsync(H.h_pin, H.d_scal, sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -1423,8 +1489,9 @@ static mg_status solve_fp64(Hier& H, double* u, const double* b, double tol, int
     set_coarsest(H, H.c_setup);
     coarse_factor(H, s);
   }
+  H.ff_active = ff && rel > kFfSwitch * tol;
   while (rel > tol && cycles < max_cycles) {
-    MG_CHECK(graph_launch(H, H.g_cycle64, u, b, s, [&](cudaStream_t ss) {
+    MG_CHECK(graph_launch(H, H.ff_active ? H.g_cycle_ff : H.g_cycle64, u, b, s, [&](cudaStream_t ss) {
       vcycle<double>(H, H.L, u, b, ss);
       residual_norm<double>(H, u, b, F.r, 0, ss);
       cudaMemcpyAsync(H.h_pin, H.d_scal, sizeof(double), cudaMemcpyDeviceToHost, ss);
@@ -1433,6 +1500,8 @@ static mg_status solve_fp64(Hier& H, double* u, const double* b, double tol, int
     ++cycles;
     const double prev = rel;
     rel = std::sqrt(H.h_pin[0]) / r0;
+    // leave float-float near the tolerance, or once its cycles stop contracting
+    if (H.ff_active && (rel <= kFfSwitch * tol || rel > 0.95 * prev)) H.ff_active = false;
     if (H.opt.dynamic_coarsest && rel > tol && rel > 0.95 * prev && H.c < H.c_max) {
       // Sect. 4.3, rule (b): the residual stagnated or grew, raise the coarsest level
       set_coarsest(H, H.c + 1);
@@ -1755,6 +1824,12 @@ static CompVecs comp_vecs(const Hier& H, double* u, const double* b) {
 static mg_status solve_comp_fp64(Hier& H, double* u, const double* b, double tol, int max_cycles,
                                  mg_solve_stats* st, cudaStream_t s) {
   const CompVecs v = comp_vecs(H, u, b);
+  const bool ff = H.lv[H.L].eps_pair != nullptr;  // float-float cycles first, as in solve_fp64
+  struct Restore {
+    Hier& h;
+    ~Restore() { h.ff_active = true; }
+  } restore{H};
+  H.ff_active = false;
   MG_TRY_CUDA(cudaMemsetAsync(v.uL, 0, H.lv[H.L].d.n_slots * sizeof(double), s));
   MG_TRY_CUDA(cudaMemsetAsync(v.ut, 0, H.lv[H.top].d.n_slots * sizeof(double), s));
   comp_residual_norm<double>(H, v.uL, v.bL, v.ut, v.bt, 0, 4, s);
@@ -1771,15 +1846,18 @@ static mg_status solve_comp_fp64(Hier& H, double* u, const double* b, double tol
   }
   double rel = r0 > 0 ? 1.0 : 0.0;
   int cycles = 0;
+  H.ff_active = ff && rel > kFfSwitch * tol;
   while (rel > tol && cycles < max_cycles) {
-    MG_CHECK(graph_launch(H, H.g_comp64, u, b, s, [&](cudaStream_t ss) {
+    MG_CHECK(graph_launch(H, H.ff_active ? H.g_comp_ff : H.g_comp64, u, b, s, [&](cudaStream_t ss) {
       composite_cycle<double>(H, v.uL, v.bL, v.ut, v.bt, ss);
       comp_residual_norm<double>(H, v.uL, v.bL, v.ut, v.bt, 0, 4, ss);
       cudaMemcpyAsync(H.h_pin, H.d_scal, 8 * sizeof(double), cudaMemcpyDeviceToHost, ss);
     }));
     MG_TRY_CUDA(cudaStreamSynchronize(s));
     ++cycles;
+    const double prev = rel;
     rel = std::sqrt(H.h_pin[0] + H.h_pin[4]) / r0;
+    if (H.ff_active && (rel <= kFfSwitch * tol || rel > 0.95 * prev)) H.ff_active = false;
     if (st && st->history && st->history_len < st->history_capacity) st->history[st->history_len++] = rel;
     if (!std::isfinite(rel)) {
       set_error("mg_solve: non-finite residual");
@@ -2276,6 +2354,8 @@ mg_status mg_autotune(mg_hier* h, int32_t* chosen, void* stream) {
   }
   // captured cycles carry the old launch shapes
   H->g_cycle64.reset();
+  H->g_cycle_ff.reset();
+  H->g_comp_ff.reset();
   H->g_outer.reset();
   H->g_inner.reset();
   H->g_comp64.reset();

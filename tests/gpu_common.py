@@ -31,6 +31,11 @@ U64 = 2.0 ** -53
 BOUNDS = {
     "cycle": (2.0 ** 14, 0.25),
     "solve": (2.0 ** 14, 0.5),
+    # float-float finest sweeps: their roundings are 2^-46 instead of 2^-53 (the C1 term
+    # grows by 2^7); the Galerkin setup stays FP64 (same C2 F term)
+    "ff_cycle": (2.0 ** 21, 0.25),
+    "ff_solve": (2.0 ** 21, 0.5),
+    "ff_composite_solve": (2.0 ** 26, 0.0),
     "composite_cycle": (2.0 ** 17, 0.0),
     "composite_solve": (2.0 ** 19, 0.0),
 }
@@ -86,7 +91,7 @@ class Case:
 
     def __init__(self, dim, L, eps_kind="checker", transfer="boxmg", coarse="galerkin", precision="fp64",
                  seed=0, omega=0.6, nu1=2, nu2=2, load="uniform", oracle=True, persistent=0, eps_mf=None,
-                 smoother="jacobi", gs_sweeps=1):
+                 smoother="jacobi", gs_sweeps=1, ff_sweeps=0):
         import torch
 
         self.mg = lib()
@@ -97,6 +102,8 @@ class Case:
         extra = {} if eps_mf is None else {"eps_mf": eps_mf}
         if smoother != "jacobi":
             extra.update(smoother=smoother, gs_sweeps=gs_sweeps)
+        if ff_sweeps:
+            extra.update(ff_sweeps=ff_sweeps)
         self.H = self.mg.Hierarchy(self.grid, transfer=transfer, coarse=coarse, precision=precision,
                                    omega=omega, nu1=nu1, nu2=nu2, persistent=persistent, **extra)
         eps_cat = self.grid.cells_to_concat({L: self.eps})
@@ -199,3 +206,16 @@ def galerkin_amplification(O, tree, L, dim):
         dof = tree.levels[lv].dof
         amp = max(amp, float((st[dof, c] / np.abs(O.ops[lv].st[dof, c])).max()))
     return amp
+
+
+_FULL: dict = {}
+
+
+def full_size_checker_solve():
+    """2D level 6 (529,984 DoFs), seeded 9x9 checkerboard {1, 1e-4}, BoxMG + Galerkin, FP64:
+    the Case and the oracle's solve to a 1e-10 drop (computed once per session)."""
+    if "c" not in _FULL:
+        c = Case(2, 6, "checker")
+        ref, hist = c.O.solve(c.b, 1e-10, 400)
+        _FULL.update(c=c, ref=ref, hist=hist)
+    return _FULL["c"], _FULL["ref"], _FULL["hist"]

@@ -15,7 +15,8 @@ import numpy as np
 import pytest
 
 from oracle import codec
-from tests.gpu_common import HIST_ATOL, HIST_RTOL, Case, lib, parity_check, rel_inf, rowwise_rel
+from tests.gpu_common import (HIST_ATOL, HIST_RTOL, Case, full_size_checker_solve, lib, parity_check, rel_inf,
+                              rowwise_rel)
 
 pytestmark = pytest.mark.gpu
 
@@ -322,10 +323,9 @@ def test_full_size_config2_solve_matches_oracle():
     # {1, 1e-4}, BoxMG + Galerkin, V(2,2), FP64, solved to a 1e-10 drop on both sides.
     # Same cycle count; iterate within u (C1 + C2 F) and residual history within the
     # history tolerance of the oracle's
-    c = Case(2, 6, "checker")
+    c, ref, hist = full_size_checker_solve()
     u = c.torch.zeros(c.n(6), dtype=c.torch.float64, device="cuda")
     res = c.H.solve(u, c.b_dev, rel_tol=1e-10, max_cycles=400)
-    ref, hist = c.O.solve(c.b, 1e-10, 400)
     assert res["cycles"] == len(hist) - 1, (res["cycles"], len(hist) - 1)
     amp = c.amplification()
     parity_check("solve 2d-l6-checker (full size)", rel_inf(c.host(u), ref), amp, "solve")
