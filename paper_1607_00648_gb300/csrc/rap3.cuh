@@ -23,6 +23,14 @@
 namespace mg {
 
 constexpr int kApPerBrick = 343 * 27;  // sum over classes of cnt[c] (= 7^3) x 27 positions
+// stage-1 threads run group by group: the 27 classes of kApGroup consecutive fine bricks
+// (Peano order) in consecutive CTAs, so the coarse P and the fine coefficients they read
+// stay in L2 while every class passes over them (class by class over the whole level,
+// each of the 27 passes re-read the coarse level's P from DRAM)
+constexpr int kApGroup = 32;
+__host__ __device__ constexpr int64_t ap_threads(int64_t n_bricks) {
+  return (n_bricks + kApGroup - 1) / kApGroup * (27 * 27 * kApGroup);
+}
 
 // per-axis admissible coarse offsets of a fine vertex with local coordinate x (mod 3)
 __host__ __device__ constexpr int ap_nofs(int xm3) { return xm3 == 0 ? 3 : 2; }
@@ -48,9 +56,16 @@ __global__ void __launch_bounds__(128) k_rap3_ap(LevelDesc Lc, LevelDesc Lf, con
     plin[k] = wlin1(k % 5 - 2) * wlin1((k / 5) % 5 - 2) * wlin1(k / 25 - 2);
   const int64_t per_class = Lf.n_bricks * 27;
   const int64_t gid = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
-  const bool live = gid < 27 * per_class;
-  const int c = live ? static_cast<int>(gid / per_class) : 0;
-  const int64_t r = live ? gid - c * per_class : 0;
+  // gid -> (group, class, (brick, position) within the group); a warp covers 32
+  // consecutive (brick, position) pairs of one class (27 kApGroup is a multiple of 32)
+  constexpr int64_t kGsz = 27 * kApGroup;
+  const int64_t grp = gid / (27 * kGsz);
+  const int64_t rem = gid - grp * (27 * kGsz);
+  const int cg = static_cast<int>(rem / kGsz);
+  const int64_t rg = grp * kGsz + (rem - cg * kGsz);
+  const bool live = rg < per_class;
+  const int c = live ? cg : 0;
+  const int64_t r = live ? rg : 0;
   const int64_t b = r / 27;
   const int p = static_cast<int>(r - b * 27);
   const int cm[3] = {c % 3, (c / 3) % 3, c / 9};

@@ -1258,7 +1258,7 @@ static mg_status run_setup(Hier& H, const double* eps_in, cudaStream_t s, bool c
           k_rap<2, 0><<<gr, 128, rap_dyn_smem<2, 0>(), s>>>(C.d, F.d, F.eps, ahat_f, C.eps, C.phat, C.ahat, F.aniso);
       } else if (H.ap3 && F.d.B == 9 && F.d.n_bricks * kApPerBrick <= H.ap3_len) {
         // two stages: AP = A_f P per fine vertex into the scratch, then P^T (AP) per coarse one
-        const unsigned g1 = static_cast<unsigned>((F.d.n_bricks * 27 * 27 + 127) / 128);
+        const unsigned g1 = static_cast<unsigned>((ap_threads(F.d.n_bricks) + 127) / 128);
         const unsigned g2 = static_cast<unsigned>((C.d.n_slots + kRapPtSlots - 1) / kRapPtSlots);
         static const bool pt_opt_in = [] {
           return cudaFuncSetAttribute(k_rap3_pt<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
