@@ -28,14 +28,14 @@ struct LevelDesc {
 __host__ __device__ constexpr int cpow(int b, int e) { return e == 0 ? 1 : b * cpow(b, e - 1); }
 
 // Programmatic dependent launch: the kernels of a cycle are launched with programmatic
-// stream serialization (launch_pdl), so a kernel's CTAs are scheduled while its
-// predecessor still runs; pdl_enter makes each wait for the predecessor's results and
-// then lets its own successor start launching.  Without the launch attribute both are
-// no-ops.
-__device__ __forceinline__ void pdl_enter() {
-  asm volatile("griddepcontrol.wait;\n" ::: "memory");
-  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
-}
+// stream serialization (launch_pdl), so the launch of a kernel is processed while its
+// predecessor still runs and its CTAs start as soon as the predecessor's CTAs exit;
+// pdl_enter makes each wait for the predecessor's results.  No kernel signals its
+// dependents early (griddepcontrol.launch_dependents): CTAs of the next kernel that
+// become resident early and wait beside a running FP64-bound sweep slowed it (2D level 6:
+// a residual sweep 33 -> 22 us, an FP64 V-cycle 250 -> 231 us without the early signal).
+// Without the launch attribute the wait is a no-op.
+__device__ __forceinline__ void pdl_enter() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
 
 template <typename... KArgs, typename... Args>
 inline void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
