@@ -12,6 +12,7 @@
 #include <string>
 #include <vector>
 
+#include "boxmg3.cuh"
 #include "bpa.cuh"
 #include "hier.h"
 #include "internal.h"
@@ -1239,7 +1240,8 @@ static mg_status run_setup(Hier& H, const double* eps_in, cudaStream_t s, bool c
       if (d == 2)
         k_boxmg<2><<<gp, 64, 0, s>>>(C.d, F.d, F.eps, ahat_f, C.phat, H.d_status, F.aniso);
       else
-        k_boxmg<3><<<gp, 64, 0, s>>>(C.d, F.d, F.eps, ahat_f, C.phat, H.d_status, F.aniso);
+        k_boxmg3c<<<static_cast<unsigned>((C.d.n_slots + kBoxCells - 1) / kBoxCells), 8 * kBoxCells, 0, s>>>(
+            C.d, F.d, F.eps, ahat_f, C.phat, H.d_status, F.aniso);
     }
     if (H.galerkin) {
       // 128-thread CTAs: 4 coarse vertices (2D) or 1 (3D) per CTA
