@@ -82,7 +82,7 @@ BYTES_PER_DOF_SWEEP_FP64_IMPL = 40
 # DRAM bytes per DoF of k_sweep2f from ncu (dram__bytes_read.sum + dram__bytes_write.sum)
 # on the 2D level-7 case (python bench.py --sweep-level 7 --sweep-dim 2 --sweep-prec
 # fp64), whose vectors exceed L2
-TRAFFIC_PER_DOF_SWEEP_FP64_2D = 38.40
+TRAFFIC_PER_DOF_SWEEP_FP64_2D = 38.34
 BYTES_PER_DOF_SWEEP_FP32 = 16
 
 
