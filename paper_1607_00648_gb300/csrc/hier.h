@@ -105,6 +105,7 @@ struct Hier {
   bool ready = false;
   Graph g_cycle64, g_outer, g_inner, g_comp64, g_comp_outer, g_comp_inner, g_add;
   Graph g_cycle_ff, g_comp_ff;  // FP64 solves: cycles with float-float finest sweeps
+  Graph g_fused[2][2];  // FP64 solves, norm fused into the next first sweep: [float-float][leading sweep]
   bool ff_active = true;   // float-float finest sweeps in use (when the setup split the pairs)
 };
 

@@ -80,6 +80,8 @@ static void sweep_b(SweepArgs<T> a, int op, int amode, cudaStream_t s) {
   } while (0)
       if (op == kJacobi) {
         if (amode == 1) MG_SW(1, kJacobi); else MG_SW(0, kJacobi);
+      } else if (op == kJacobiNorm) {  // finest levels (no stored deltas) of the FP64 solve
+        MG_SW(0, kJacobiNorm);
       } else {
         if (amode == 1) MG_SW(1, kResidual); else MG_SW(0, kResidual);
       }

@@ -631,6 +631,8 @@ static void free_hier(Hier* H, bool device_sync) {
   if (device_sync) cudaDeviceSynchronize();
   H->g_cycle64.reset();
   H->g_cycle_ff.reset();
+  for (auto& gr : H->g_fused)
+    for (Graph& g : gr) g.reset();
   H->g_comp_ff.reset();
   H->g_outer.reset();
   H->g_inner.reset();
@@ -1077,12 +1079,14 @@ static void coarse_solve(const Hier& H, const T* b, T* u, cudaStream_t s) {
 // nu smoothing steps, ping-pong through tmp, result in u: damped Jacobi sweeps, or block
 // Jacobi steps (Sect. 4.2: Gauss-Seidel on the patches' iota vertices in place, then the
 // Jacobi sweep with the iota values kept) on the uniform levels of a block hierarchy
+// first_done: the first sweep (u -> tmp) has already run (the fused FP64 solve runs it
+// with the previous cycle, beside its convergence norm)
 template <typename T>
-static void smooth(const Hier& H, int l, T* u, const T* b, T* tmp, int nu, cudaStream_t s) {
-  T* src = u;
-  T* dst = tmp;
+static void smooth(const Hier& H, int l, T* u, const T* b, T* tmp, int nu, cudaStream_t s, bool first_done = false) {
+  T* src = first_done ? tmp : u;
+  T* dst = first_done ? u : tmp;
   const bool block = H.opt.smoother == MG_SMOOTH_BLOCK && l <= H.top;
-  for (int k = 0; k < nu; ++k) {
+  for (int k = first_done ? 1 : 0; k < nu; ++k) {
     if (block) {
       int amode = 0;
       SweepArgs<T> g = sweep_args<T>(H, l, src, b, src, &amode);
@@ -1113,7 +1117,7 @@ static T* lvec(Hier& H, int l, int which) {  // 0 u, 1 b, 2 r, 3 t
 
 // V(nu1, nu2) cycle on level l (correction scheme; Alg. 1 semantics, Sect. 3 FAS reduced)
 template <typename T>
-static void vcycle(Hier& H, int l, T* u, const T* b, cudaStream_t s) {
+static void vcycle(Hier& H, int l, T* u, const T* b, cudaStream_t s, bool first_done = false) {
   if (l == H.c) {
     coarse_solve<T>(H, b, u, s);
     return;
@@ -1122,7 +1126,7 @@ static void vcycle(Hier& H, int l, T* u, const T* b, cudaStream_t s) {
   T* r = lvec<T>(H, l, 2);
   T* uc = lvec<T>(H, l - 1, 0);
   T* bc = lvec<T>(H, l - 1, 1);
-  smooth<T>(H, l, u, b, tmp, H.opt.nu1, s);
+  smooth<T>(H, l, u, b, tmp, H.opt.nu1, s, first_done);
   sweep<T>(H, l, kResidual, u, b, r, nullptr, s);
   transfer<T>(H, l, true, r, bc, s, nullptr, 0, uc);  // also zeroes the coarse correction uc
   vcycle<T>(H, l - 1, uc, bc, s);
@@ -1146,7 +1150,8 @@ static void set_coarsest(Hier& H, int c) {
   H.n_c = H.nc_lv[c];
   H.c_slots = H.cs_lv[c];
   H.c_map = H.cm_lv[c];
-  for (Graph* gr : {&H.g_cycle64, &H.g_cycle_ff, &H.g_comp_ff, &H.g_outer, &H.g_inner, &H.g_comp64, &H.g_comp_outer, &H.g_comp_inner, &H.g_add})
+  for (Graph* gr : {&H.g_cycle64, &H.g_cycle_ff, &H.g_comp_ff, &H.g_outer, &H.g_inner, &H.g_comp64, &H.g_comp_outer, &H.g_comp_inner, &H.g_add,
+                    &H.g_fused[0][0], &H.g_fused[0][1], &H.g_fused[1][0], &H.g_fused[1][1]})
     gr->reset();
 }
 
@@ -1492,18 +1497,43 @@ static mg_status solve_fp64(Hier& H, double* u, const double* b, double tol, int
     coarse_factor(H, s);
   }
   H.ff_active = ff && rel > kFfSwitch * tol;
+  // Fused convergence test: the first Jacobi sweep of a cycle forms b - A u at every DoF
+  // anyway, so cycle k's graph ends with the first sweep of cycle k + 1 (u_k -> F.t, u_k
+  // kept in u) and takes ||b - A u_k|| from it instead of a separate residual sweep; the
+  // next graph starts from that sweep.  A solve that stops after cycle k leaves the sweep
+  // unused.  The iterates are those of the plain loop.  Needs the finest level's column
+  // kernel, damped Jacobi with nu1 >= 1 and no anisotropy correction pass.
+  const int Bf = F.d.B;
+  const bool fused = H.opt.use_graphs && H.opt.smoother == MG_SMOOTH_JACOBI && H.opt.nu1 >= 1 && !H.tensor &&
+                     ((H.dim == 2 && Bf == 27) || (H.dim == 3 && Bf == 9));
+  bool pending = false;  // F.t holds the first sweep of the next cycle, formed from u
   while (rel > tol && cycles < max_cycles) {
-    MG_CHECK(graph_launch(H, H.ff_active ? H.g_cycle_ff : H.g_cycle64, u, b, s, [&](cudaStream_t ss) {
-      vcycle<double>(H, H.L, u, b, ss);
-      residual_norm<double>(H, u, b, F.r, 0, ss);
-      cudaMemcpyAsync(H.h_pin, H.d_scal, sizeof(double), cudaMemcpyDeviceToHost, ss);
-    }));
+    if (fused) {
+      const bool lead = !pending;
+      MG_CHECK(graph_launch(H, H.g_fused[H.ff_active ? 1 : 0][lead ? 1 : 0], u, b, s, [&](cudaStream_t ss) {
+        if (lead) sweep<double>(H, H.L, kJacobi, u, b, F.t, nullptr, ss);
+        vcycle<double>(H, H.L, u, b, ss, true);
+        sweep<double>(H, H.L, kJacobiNorm, u, b, F.t, H.d_scal, ss);
+        cudaMemcpyAsync(H.h_pin, H.d_scal, sizeof(double), cudaMemcpyDeviceToHost, ss);
+      }));
+      pending = true;
+    } else {
+      MG_CHECK(graph_launch(H, H.ff_active ? H.g_cycle_ff : H.g_cycle64, u, b, s, [&](cudaStream_t ss) {
+        vcycle<double>(H, H.L, u, b, ss);
+        residual_norm<double>(H, u, b, F.r, 0, ss);
+        cudaMemcpyAsync(H.h_pin, H.d_scal, sizeof(double), cudaMemcpyDeviceToHost, ss);
+      }));
+    }
     MG_TRY_CUDA(cudaStreamSynchronize(s));
     ++cycles;
     const double prev = rel;
     rel = std::sqrt(H.h_pin[0]) / r0;
-    // leave float-float near the tolerance, or once its cycles stop contracting
-    if (H.ff_active && (rel <= kFfSwitch * tol || rel > 0.95 * prev)) H.ff_active = false;
+    // leave float-float near the tolerance, or once its cycles stop contracting (the
+    // pending first sweep was a float-float one: the next FP64 cycle forms its own)
+    if (H.ff_active && (rel <= kFfSwitch * tol || rel > 0.95 * prev)) {
+      H.ff_active = false;
+      pending = false;
+    }
     if (H.opt.dynamic_coarsest && rel > tol && rel > 0.95 * prev && H.c < H.c_max) {
       // Sect. 4.3, rule (b): the residual stagnated or grew, raise the coarsest level
       set_coarsest(H, H.c + 1);
@@ -2357,6 +2387,8 @@ mg_status mg_autotune(mg_hier* h, int32_t* chosen, void* stream) {
   // captured cycles carry the old launch shapes
   H->g_cycle64.reset();
   H->g_cycle_ff.reset();
+  for (auto& gr : H->g_fused)
+    for (Graph& g : gr) g.reset();
   H->g_comp_ff.reset();
   H->g_outer.reset();
   H->g_inner.reset();

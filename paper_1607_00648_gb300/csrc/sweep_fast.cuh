@@ -361,7 +361,7 @@ __device__ __forceinline__ double sweep2f_item(const SweepArgs<double>& a, int64
     fv[k] = vl ? L.vflags[slot] : 0;
     const bool on = vl && is_dof(fv[k]);
     bv[k] = on ? a.b[slot] : 0.0;
-    dv[k] = (OP == kJacobi && on) ? a.dinv[slot] : 0.0;
+    dv[k] = (OP != kResidual && on) ? a.dinv[slot] : 0.0;
   }
   if (x <= B) {
     const int ox = x < 0 ? -1 : (x >= B ? 1 : 0);
@@ -411,7 +411,7 @@ __device__ __forceinline__ double sweep2f_item(const SweepArgs<double>& a, int64
     // iota vertices keep their value in the Jacobi part of a block step (Sect. 4.2);
     // hanging values come from the coarser level (Sect. 3)
     const bool keep = OP == kJacobi && a.block && x % 3 != 0 && (z0 + yl) % 3 != 0;
-    if constexpr (OP == kJacobi) {
+    if constexpr (OP != kResidual) {
       if ((vf & MG_V_HANGING) || keep) res = u0;
     }
     if (vl && is_dof(vf) && !keep) {
@@ -429,7 +429,12 @@ __device__ __forceinline__ double sweep2f_item(const SweepArgs<double>& a, int64
           }
         }
       }
-      if constexpr (OP == kJacobi) {
+      if constexpr (OP == kJacobiNorm) {
+        // the Jacobi update and, beside it, the residual b - A u of its input
+        res = fma(dv[k], t, om1 * u0);
+        const double r = fma(-fma(2.0 / 3.0, sW + sE, dc), u0, t);
+        part = fma(r, r, part);
+      } else if constexpr (OP == kJacobi) {
         res = fma(dv[k], t, om1 * u0);
       } else {
         const double D = fma(2.0 / 3.0, sW + sE, dc);
@@ -451,7 +456,7 @@ template <int AMODE, int OP, int R>
 __global__ void __launch_bounds__(96) k_sweep2f(SweepArgs<double> a) {
   pdl_enter();
   const double part = sweep2f_item<AMODE, OP, R>(a, blockIdx.x, blockIdx.y);
-  if constexpr (OP == kResidual) {
+  if constexpr (OP == kResidual || OP == kJacobiNorm) {
     if (a.partial) store_partial_and_finish(part, a.partial, a.counter, a.norm2);
   }
 }
@@ -560,20 +565,28 @@ __device__ __forceinline__ double sweep3c_item(const SweepArgs<T>& a, int64_t br
         s1 = fma(szp, ua, s1);
         s1 = fma(szm, ub, s1);
         const uint64_t akey = AMODE != 0 ? delta_row<AMODE>(a.ascale, slot) : 0;
-        if constexpr (std::is_same<T, double>::value && OP == kJacobi) {
+        if constexpr (std::is_same<T, double>::value && (OP == kJacobi || OP == kJacobiNorm)) {
           // FP64 Jacobi with omega / D from the setup: off = A u - D u
           //   = h/12 (sC u_v + sum_axis nbr S_n u_n - sum_c q_c)   (D = h/3 sC)
           T t2 = fma(-(hscale * static_cast<T>(1.0 / 12.0)), fma(sC, u0, s1 - Q), bv[zl]);
+          T dc = T(0);
           if (AMODE != 0 && delta_row_live<AMODE>(akey)) {
 #pragma unroll
             for (int k = 0; k < N3; ++k) {
-              if (k == N3 / 2) continue;
+              if (k == N3 / 2) {
+                if constexpr (OP == kJacobiNorm) dc = load_delta<AMODE, T>(a.ahat, a.ascale, (brick * N3 + k) * L.S + s, slot, k, akey);
+                continue;
+              }
               const int off = (k % 3 - 1) + Bu * ((k / 3) % 3 - 1) + UPL * (k / 9 - 1);
               t2 = fma(-load_delta<AMODE, T>(a.ahat, a.ascale, (brick * N3 + k) * L.S + s, slot, k, akey),
                        uc[off], t2);
             }
           }
           res = fma(a.dinv[slot], t2, om1 * u0);
+          if constexpr (OP == kJacobiNorm) {  // and the residual b - A u = t2 - D u of its input
+            const T r = fma(-fma(sC, hscale * static_cast<T>(1.0 / 3.0), dc), u0, t2);
+            part = fma(static_cast<double>(r), static_cast<double>(r), part);
+          }
         } else {
           T Au = fma(T(5) * sC, u0, s1 - Q) * (hscale * static_cast<T>(1.0 / 12.0));
           T D = sC * (hscale * static_cast<T>(1.0 / 3.0));
@@ -613,7 +626,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 8 ? 4 : 8) k_sweep3c(SweepAr
   extern __shared__ __align__(16) unsigned char smem_raw[];
   pdl_enter();
   const double part = sweep3c_item<T, AMODE, OP, R>(a, blockIdx.x, blockIdx.y, smem_raw);
-  if constexpr (OP == kResidual) {
+  if constexpr (OP == kResidual || OP == kJacobiNorm) {
     if (a.partial) store_partial_and_finish(part, a.partial, a.counter, a.norm2);
   }
 }

@@ -148,7 +148,7 @@ __device__ __forceinline__ double sweep2x_item(const SweepArgs<double>& a, int64
     fv[k] = vl ? L.vflags[slot] : 0;
     const bool on = vl && is_dof(fv[k]);
     bv[k] = on ? a.b[slot] : 0.0;
-    dv[k] = (OP == kJacobi && on) ? a.dinv_pair[slot] : 0.0;
+    dv[k] = (OP != kResidual && on) ? a.dinv_pair[slot] : 0.0;
   }
   if (x <= B) {
     const int ox = x < 0 ? -1 : (x >= B ? 1 : 0);
@@ -193,7 +193,7 @@ __device__ __forceinline__ double sweep2x_item(const SweepArgs<double>& a, int64
     const int64_t slot = base + (z0 + yl) * B + x;
     const uint8_t vf = fv[k];
     double res = 0.0;
-    if constexpr (OP == kJacobi) {
+    if constexpr (OP != kResidual) {
       if (vf & MG_V_HANGING) res = a.u[slot];  // hanging values come from the coarser level (Sect. 3)
     }
     if (vl && is_dof(vf)) {
@@ -217,10 +217,16 @@ __device__ __forceinline__ double sweep2x_item(const SweepArgs<double>& a, int64
         two_sum(b2.h, q6.h, s, e);
         t = {s, __fadd_rn(e, __fadd_rn(b2.l, q6.l))};
       }
-      if constexpr (OP == kJacobi) {
+      if constexpr (OP != kResidual) {
         const ff2 p1 = ff_mul(ff_unpack(dv[k]), t);
         const ff2 p2 = ff_mul(om1, u0);
         res = ff_to_double(ff_add(p1, p2));
+        if constexpr (OP == kJacobiNorm) {  // and the residual b - A u of its input
+          const ff2 D = ff_mul(ff_add(sW, sE), ff2{k23h, k23l});
+          const ff2 Du = ff_mul(D, u0);
+          const double r = ff_to_double(ff_add(t, ff2{-Du.h, -Du.l}));
+          part = fma(r, r, part);
+        }
       } else {
         const ff2 D = ff_mul(ff_add(sW, sE), ff2{k23h, k23l});
         const ff2 Du = ff_mul(D, u0);
@@ -242,7 +248,7 @@ template <int OP, int R>
 __global__ void __launch_bounds__(96) k_sweep2x(SweepArgs<double> a) {
   pdl_enter();
   const double part = sweep2x_item<OP, R>(a, blockIdx.x, blockIdx.y);
-  if constexpr (OP == kResidual) {
+  if constexpr (OP == kResidual || OP == kJacobiNorm) {
     if (a.partial) store_partial_and_finish(part, a.partial, a.counter, a.norm2);
   }
 }
@@ -273,7 +279,7 @@ __device__ __forceinline__ double sweep3x_item(const SweepArgs<double>& a, int64
     fv[zl] = t < PL ? L.vflags[slot] : 0;
     const bool on = t < PL && is_dof(fv[zl]);
     bv[zl] = on ? a.b[slot] : 0.0;
-    dv[zl] = (OP == kJacobi && on) ? a.dinv_pair[slot] : 0.0;
+    dv[zl] = (OP != kResidual && on) ? a.dinv_pair[slot] : 0.0;
   }
   if (t < UPL) {
     const int x = t % Bu - 1, y = t / Bu - 1;
@@ -342,7 +348,7 @@ __device__ __forceinline__ double sweep3x_item(const SweepArgs<double>& a, int64
       const int64_t slot = base + (z0 + zl) * PL + t;
       const uint8_t vf = fv[zl];
       double res = 0.0;
-      if constexpr (OP == kJacobi) {
+      if constexpr (OP != kResidual) {
         if (vf & MG_V_HANGING) res = a.u[slot];  // hanging values come from the coarser level (Sect. 3)
       }
       if (is_dof(vf)) {
@@ -359,7 +365,7 @@ __device__ __forceinline__ double sweep3x_item(const SweepArgs<double>& a, int64
         acc.add(szp, ua);
         acc.add(szm, ub);
         // Jacobi: sC u_v (off-diagonal part: A u - D u); residual: 5 sC u_v (A u)
-        acc.add(OP == kJacobi ? sC : ff_mul(sC, ff2{5.0f, 0.0f}), u0);
+        acc.add(OP != kResidual ? sC : ff_mul(sC, ff2{5.0f, 0.0f}), u0);
         {
           float s, e;
           two_sum(acc.s, -Q.h, s, e);
@@ -374,8 +380,13 @@ __device__ __forceinline__ double sweep3x_item(const SweepArgs<double>& a, int64
           two_sum(b2.h, -hq.h, s, e);
           t2 = {s, __fadd_rn(e, __fsub_rn(b2.l, hq.l))};
         }
-        if constexpr (OP == kJacobi) {
+        if constexpr (OP != kResidual) {
           res = ff_to_double(ff_add(ff_mul(ff_unpack(dv[zl]), t2), ff_mul(om1, u0)));
+          if constexpr (OP == kJacobiNorm) {  // and the residual t2 - D u, D = h/3 sC = 4 (h/12) sC
+            const ff2 du = ff_mul(ff_mul(sC, hk), u0);
+            const double r = ff_to_double(ff_add(t2, ff2{-4.0f * du.h, -4.0f * du.l}));
+            part = fma(r, r, part);
+          }
         } else {
           const double r = ff_to_double(t2);
           res = r;
@@ -398,7 +409,7 @@ __global__ void __launch_bounds__(128, 4) k_sweep3x(SweepArgs<double> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   pdl_enter();
   const double part = sweep3x_item<OP, R>(a, blockIdx.x, blockIdx.y, smem_raw);
-  if constexpr (OP == kResidual) {
+  if constexpr (OP == kResidual || OP == kJacobiNorm) {
     if (a.partial) store_partial_and_finish(part, a.partial, a.counter, a.norm2);
   }
 }
