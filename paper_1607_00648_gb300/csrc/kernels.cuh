@@ -743,6 +743,10 @@ inline int pick_slab(int B, int64_t n_bricks, int64_t target) {
 template <int DIM, typename T>
 void launch_sweep(SweepArgs<T> a, int op, int amode, cudaStream_t s);
 
+// two damped Jacobi sweeps a.u -> a.out in one launch (sweep_pair.cuh): 2D FP32 levels
+// of brick edge 27; amode 0, 2 or 3
+void launch_sweep_pair_2d_f32(SweepArgs<float> a, int amode, cudaStream_t s);
+
 // Gauss-Seidel part of a block Jacobi step (Sect. 4.2) on a.u in place
 template <int DIM, typename T>
 void launch_patch_gs(SweepArgs<T> a, int amode, int sweeps, cudaStream_t s);
