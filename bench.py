@@ -185,31 +185,27 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def kernel_count(L, c, nu1, nu2, transfer, coarse, precision, cycles, outer, chunk, block=False):
-    """Kernels of ours launched by one mg_setup + mg_solve (memsets / copies excluded)."""
-    levels = L - c
-    steps = (nu1 + nu2) * (2 if block else 1)  # a block step: patch Gauss-Seidel + masked Jacobi
-    per_cycle = levels * (steps + 3) + 1  # smoothing, residual, restrict, prolong per level; coarse solve
-    setup = (levels + 1) + levels + levels * ((transfer == "boxmg") + (coarse == "galerkin")) + (levels + 1) + 2
-    if precision == "fp64":
-        return setup + (levels + 1) + 2 + cycles * (per_cycle + 2)  # + the Jacobi factors per level
-    setup += (levels + 1) + levels * ((transfer == "boxmg") + (coarse == "galerkin"))
-    inner_chunks = max(1, math.ceil(cycles / max(chunk, 1)))
-    return setup + 2 + outer * 4 + cycles * per_cycle + inner_chunks * 2
+_PROFILER_WARM = False
 
 
-def kernel_count_adaptive(L, c, nu1, nu2, precision, cycles, outer, chunk):
-    """Kernels of ours launched by one mg_setup + composite mg_solve (memsets / copies excluded)."""
-    t = L - 1
-    vc = (t - c) * (nu1 + nu2 + 3) + 1  # the V-cycle of the uniform levels t .. c
-    cyc = nu1 + nu2 + 8 + vc  # sweeps, residuals L and t, inject, compose, restrict, add, prolong, hanging
-    res = 4  # residual L, inject, residual t, masked norm
-    setup = (L - c + 1) + (L - c) + 2 * (t - c) + (L - c + 1) + 2
-    if precision == "fp64":
-        return setup + (L - c + 1) + res + cycles * (cyc + res)
-    setup += (L - c + 1) + 2 * (t - c)
-    inner_chunks = max(1, math.ceil(cycles / max(chunk, 1)))
-    return setup + res + outer * (3 + res + 3) + cycles * cyc + inner_chunks * res
+def measured_launches(step):
+    """Kernels of this library (names in namespace mg) that one call of step() launches,
+    counted from the CUDA activity trace of torch.profiler (kernels replayed from CUDA
+    graphs included); an untimed run beside the timed ones."""
+    global _PROFILER_WARM
+    import torch
+    from torch.profiler import ProfilerActivity, profile
+
+    if not _PROFILER_WARM:  # the first trace of a process misses kernels
+        with profile(activities=[ProfilerActivity.CUDA]):
+            torch.zeros(8, device="cuda").sum()
+            torch.cuda.synchronize()
+        _PROFILER_WARM = True
+    torch.cuda.synchronize()
+    with profile(activities=[ProfilerActivity.CUDA]) as prof:
+        step()
+        torch.cuda.synchronize()
+    return sum(1 for ev in prof.events() if ev.device_type.name == "CUDA" and "mg::" in ev.name)
 
 
 def adaptive_problem(mg, w):
@@ -259,9 +255,8 @@ def run_adaptive(args):
             e1.record(stream)
             torch.cuda.synchronize()
             total += e0.elapsed_time(e1)
-            o = H.options
-            launches += kernel_count_adaptive(L, o.coarsest_level, o.nu1, o.nu2, prec, res["cycles"],
-                                              res["outer_steps"], o.inner_cycles)
+        launches = args.steps * measured_launches(
+            lambda: (H.setup(eps_dev), H.solve(u_dev, b_dev, rel_tol=w["tol"], max_cycles=w["max_cycles"])))
         return total, launches, res
 
     Hmx = mg.Hierarchy(grid, precision="mixed_bf16")
@@ -482,15 +477,8 @@ def run_ours(args):
             barrier()
             total_ms += e0.elapsed_time(e1)
             stats.append(res)
-            o = H.options
-            if o.cycle in (1, 2):  # setup and r0 as for V-cycles; per traversal and level: 3 prolongations,
-                # negate, 2 residuals, correction, inject, restrict; the finest residual norm
-                lv = L - o.coarsest_level
-                launches += kernel_count(L, o.coarsest_level, o.nu1, o.nu2, w["transfer"], w["coarse"], prec,
-                                         0, 0, o.inner_cycles) + res["cycles"] * (9 * lv + 3 + 1)
-            else:
-                launches += kernel_count(L, o.coarsest_level, o.nu1, o.nu2, w["transfer"], w["coarse"], prec,
-                                         res["cycles"], res["outer_steps"], o.inner_cycles, block=o.smoother == 1)
+        launches = K * measured_launches(
+            lambda: (H.setup(eps_dev), H.solve(u_dev, b_dev, rel_tol=w["tol"], max_cycles=w["max_cycles"])))
         return max_over_ranks(total_ms, dist, dev), launches, stats
 
     smo = {} if args.smoother == "jacobi" else {"smoother": args.smoother, "gs_sweeps": args.gs_sweeps}
