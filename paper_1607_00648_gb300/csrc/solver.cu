@@ -1115,26 +1115,28 @@ static T* lvec(Hier& H, int l, int which) {  // 0 u, 1 b, 2 r, 3 t
   }
 }
 
-// FP32 V-cycle smoothing of a 2D level of brick edge 27 (damped Jacobi, no anisotropy
-// pass): nu sweeps from the iterate in cur, two per launch where nu allows
-// (launch_sweep_pair_2d_f32, bit for bit two sweeps); returns the buffer holding the result
+// V-cycle smoothing of a 2D level of brick edge 27 (damped Jacobi, no anisotropy pass): nu
+// sweeps from the iterate in cur, two per launch where nu allows (launch_sweep_pair_2d_*,
+// bit for bit two sweeps); returns the buffer holding the result
 static bool pair_smoothing(const Hier& H, int l) {
   return H.dim == 2 && H.lv[l].d.B == 27 && H.opt.smoother == MG_SMOOTH_JACOBI && !(H.tensor && l == H.L) &&
          !(H.fmt == 4 && l < H.top);
 }
 
-static float* smooth_pairs(const Hier& H, int l, float* cur, float* oth, const float* b, int nu, cudaStream_t s) {
+template <typename T>
+static T* smooth_pairs(const Hier& H, int l, T* cur, T* oth, const T* b, int nu, cudaStream_t s) {
   for (int k = 0; k < nu;) {
     int amode = 0;
-    SweepArgs<float> a = sweep_args<float>(H, l, cur, b, oth, &amode);
+    SweepArgs<T> a = sweep_args<T>(H, l, cur, b, oth, &amode);
     if (nu - k >= 2) {
-      launch_sweep_pair_2d_f32(a, amode, s);
+      if constexpr (std::is_same<T, float>::value) launch_sweep_pair_2d_f32(a, amode, s);
+      else launch_sweep_pair_2d_f64(a, amode, s);
       k += 2;
     } else {
-      launch<float>(H, a, kJacobi, amode, s);
+      launch<T>(H, a, kJacobi, amode, s);
       k += 1;
     }
-    float* t = cur;
+    T* t = cur;
     cur = oth;
     oth = t;
   }
@@ -1152,14 +1154,18 @@ static void vcycle(Hier& H, int l, T* u, const T* b, cudaStream_t s, bool first_
   T* r = lvec<T>(H, l, 2);
   T* uc = lvec<T>(H, l - 1, 0);
   T* bc = lvec<T>(H, l - 1, 1);
-  if constexpr (std::is_same<T, float>::value) {
-    if (pair_smoothing(H, l)) {  // the iterate moves between u and tmp; it ends in u
-      T* cur = smooth_pairs(H, l, u, tmp, b, H.opt.nu1, s);
+  // FP32 levels, and the coarse levels of FP64 cycles of FP64 hierarchies (their sweeps
+  // take omega / diag(A) from the setup, which mixed hierarchies do not store; the finest
+  // FP64 level is bound by the FP64 units: a pair's ring would cost more than the launch
+  // it saves)
+  if (pair_smoothing(H, l) && (std::is_same<T, float>::value || (l < H.L && H.lv[l].dinv != nullptr))) {
+    {  // the iterate moves between u and tmp; it ends in u
+      T* cur = smooth_pairs<T>(H, l, u, tmp, b, H.opt.nu1, s);
       sweep<T>(H, l, kResidual, cur, b, r, nullptr, s);
       transfer<T>(H, l, true, r, bc, s, nullptr, 0, uc);
       vcycle<T>(H, l - 1, uc, bc, s);
       transfer<T>(H, l, false, uc, cur, s);
-      T* fin = smooth_pairs(H, l, cur, cur == u ? tmp : u, b, H.opt.nu2, s);
+      T* fin = smooth_pairs<T>(H, l, cur, cur == u ? tmp : u, b, H.opt.nu2, s);
       if (fin != u) cudaMemcpyAsync(u, fin, H.lv[l].d.n_slots * sizeof(T), cudaMemcpyDeviceToDevice, s);
       return;
     }

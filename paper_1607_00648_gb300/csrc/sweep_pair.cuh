@@ -1,17 +1,18 @@
-// Two damped Jacobi sweeps in one launch (2D, brick edge 27, FP32 cycles of the mixed
-// path).  The levels of an FP32 V-cycle are L2-resident, so a sweep costs its launch and
+// Two damped Jacobi sweeps in one launch (2D, brick edge 27: the FP32 cycles of the mixed
+// path and the coarse levels of FP64 cycles).  The levels of an FP32 V-cycle are L2-resident, so a sweep costs its launch and
 // the dependency on its predecessor (a round trip through L2), not bandwidth; smoothing
 // with nu = 2 therefore pays that latency twice per level and side.  Here one CTA per
 // (brick, slab of R rows) stages u with a two-vertex halo and the cell coefficients with
 // a two-cell halo, forms the first sweep on the slab and a one-vertex ring around it in
 // shared memory (the ring's b, flags and stored deltas come from the neighbouring
 // bricks), and the second sweep of the slab from it.  Every vertex update is the
-// arithmetic of sweep2c_item (stencil2, then the deltas in entry order, then
-// u + omega r / D), so the result is bit for bit that of two separate sweeps.  Levels
+// arithmetic of the single-sweep kernel it replaces (FP32: sweep2c_item's stencil2, the
+// deltas in entry order, u + omega r / D; FP64: sweep2f_item's), so the result is bit for
+// bit that of two separate sweeps.  Levels
 // with hanging vertices, block smoothing and the anisotropy pass keep separate sweeps.
 #pragma once
 
-#include "kernels.cuh"
+#include "sweep_fast.cuh"
 
 namespace mg {
 
@@ -43,6 +44,40 @@ __device__ __forceinline__ T pair_update(const SweepArgs<T>& a, const T* c, int 
   return fma(a.omega * r, recip_nr(D), u0);
 }
 
+// FP64 hierarchies: the operations of sweep2f_item in its order (edge pair sums of cell
+// coefficients, corners doubled, b + acc / 6 minus the stored deltas, then omega / D from
+// the setup), so that a pair equals two k_sweep2f sweeps bit for bit
+template <int AMODE>
+__device__ __forceinline__ double pair_update_f64(const SweepArgs<double>& a, const double* c, int ws,
+                                                  const double* ce, int wc, int64_t slot, int64_t plane_base,
+                                                  uint8_t vf, double bv) {
+  const double u0 = c[0];
+  if (!is_dof(vf)) return (vf & MG_V_HANGING) ? u0 : 0.0;
+  const double um_l = c[-ws - 1], um = c[-ws], um_r = c[-ws + 1];
+  const double u0_l = c[-1], u0_r = c[1];
+  const double up_l = c[ws - 1], upc = c[ws], up_r = c[ws + 1];
+  // cells: em_l = (x-1, y-1), em = (x, y-1), e0_l = (x-1, y), e0 = (x, y)
+  const double em_l = ce[-wc - 1], em = ce[-wc], e0_l = ce[-1], e0 = ce[0];
+  const double sE = em + e0, sW = em_l + e0_l, sN = e0_l + e0, sS = em_l + em;
+  double acc = em_l * um_l;
+  acc = fma(em, um_r, acc);
+  acc = fma(e0_l, up_l, acc);
+  acc = fma(e0, up_r, acc);
+  acc = acc + acc;
+  acc = fma(sW, u0_l, acc);
+  acc = fma(sE, u0_r, acc);
+  acc = fma(sS, um, acc);
+  acc = fma(sN, upc, acc);
+  double t = fma(1.0 / 6.0, acc, bv);
+  if constexpr (AMODE != 0) {
+    const double nbv[9] = {um_l, um, um_r, u0_l, u0, u0_r, up_l, upc, up_r};
+#pragma unroll
+    for (int q = 0; q < 9; ++q)
+      if (q != 4) t = fma(-load_delta<AMODE, double>(a.ahat, a.ascale, plane_base + q * a.L.S, slot), nbv[q], t);
+  }
+  return fma(a.dinv[slot], t, (1.0 - a.omega) * u0);
+}
+
 template <typename T, int AMODE, int R>
 __device__ __forceinline__ void sweep_pair_item(const SweepArgs<T>& a, int64_t brick, int slab) {
   constexpr int B = 27;
@@ -67,8 +102,9 @@ __device__ __forceinline__ void sweep_pair_item(const SweepArgs<T>& a, int64_t b
     int64_t nb;
     int li;
     locate(x, y, nb, li);
-    cp_async4(su + i, a.u + (nb >= 0 ? nb * L.S + li : 0), nb >= 0);
-    if (i % WU < WE && i / WU < HE) cp_async4(se + (i / WU) * WE + i % WU, a.eps + (nb >= 0 ? nb * L.S + li : 0), nb >= 0);
+    cp_async_el(su + i, a.u + (nb >= 0 ? nb * L.S + li : 0), nb >= 0);
+    if (i % WU < WE && i / WU < HE)
+      cp_async_el(se + (i / WU) * WE + i % WU, a.eps + (nb >= 0 ? nb * L.S + li : 0), nb >= 0);
   }
   cp_async_wait_all();
   __syncthreads();
@@ -84,8 +120,12 @@ __device__ __forceinline__ void sweep_pair_item(const SweepArgs<T>& a, int64_t b
       const int64_t slot = nb * L.S + li;
       const uint8_t vf = L.vflags[slot];
       const T bv = is_dof(vf) ? a.b[slot] : T(0);
-      v = pair_update<T, AMODE>(a, su + (cy + 1) * WU + cx + 1, WU, se + (cy + 1) * WE + cx + 1, WE, slot,
-                                nb * 9 * L.S + li, vf, bv);
+      if constexpr (std::is_same<T, double>::value)
+        v = pair_update_f64<AMODE>(a, su + (cy + 1) * WU + cx + 1, WU, se + (cy + 1) * WE + cx + 1, WE, slot,
+                                   nb * 9 * L.S + li, vf, bv);
+      else
+        v = pair_update<T, AMODE>(a, su + (cy + 1) * WU + cx + 1, WU, se + (cy + 1) * WE + cx + 1, WE, slot,
+                                  nb * 9 * L.S + li, vf, bv);
     }
     s1[i] = v;
   }
@@ -98,8 +138,12 @@ __device__ __forceinline__ void sweep_pair_item(const SweepArgs<T>& a, int64_t b
     const int64_t slot = base + li;
     const uint8_t vf = L.vflags[slot];
     const T bv = is_dof(vf) ? a.b[slot] : T(0);
-    a.out[slot] = pair_update<T, AMODE>(a, s1 + (yl + 1) * W1 + x + 1, W1, se + (yl + 2) * WE + x + 2, WE, slot,
-                                         brick * 9 * L.S + li, vf, bv);
+    if constexpr (std::is_same<T, double>::value)
+      a.out[slot] = pair_update_f64<AMODE>(a, s1 + (yl + 1) * W1 + x + 1, W1, se + (yl + 2) * WE + x + 2, WE, slot,
+                                           brick * 9 * L.S + li, vf, bv);
+    else
+      a.out[slot] = pair_update<T, AMODE>(a, s1 + (yl + 1) * W1 + x + 1, W1, se + (yl + 2) * WE + x + 2, WE, slot,
+                                           brick * 9 * L.S + li, vf, bv);
   }
 }
 
