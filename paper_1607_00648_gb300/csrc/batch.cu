@@ -238,8 +238,44 @@ mg_status make_groups(Batch& bt, std::map<std::pair<int, int>, std::vector<int4>
   return MG_OK;
 }
 
+// Paired smoothing (FP32 V(2,2) cycles, 2D): the groups of brick edge 27 smooth with two
+// sweeps per launch, u -> t before the coarse correction (the residual reads t, the
+// prolongation adds into t) and t -> u after it; the other groups sweep one at a time.
+template <int DIM, typename T>
+static bool emit_paired_cycle(Batch& bt, const BatchArgs<T>& ba, int amc, int pm, cudaStream_t s) {
+  if constexpr (DIM == 2 && std::is_same<T, float>::value) {
+    if (bt.nu1 != 2 || bt.nu2 != 2) return false;
+    BatchArgs<T> nb = ba;
+    nb.partial = nullptr;
+    nb.pair_t = 1;
+    for (int j = 0; j < bt.Dmax; ++j) {
+      for (const BatchGroup& g : bt.sw[j])
+        if (g.B == 27) blaunch_sweep_pair_2d_f32(nb, g, amc, kSelU, kSelT, s);
+      for (int k = 0; k < 2; ++k)
+        for (const BatchGroup& g : bt.sw[j])
+          if (g.B != 27) blaunch_sweep<DIM, T>(nb, g, kJacobi, amc, k == 0 ? kSelU : kSelT, k == 0 ? kSelT : kSelU, s);
+      for (const BatchGroup& g : bt.sw[j])
+        blaunch_sweep<DIM, T>(nb, g, kResidual, amc, g.B == 27 ? kSelT : kSelU, kSelR, s);
+      for (const BatchGroup& g : bt.rs[j]) blaunch_transfer<DIM, T>(nb, g, true, pm, s);
+    }
+    k_bcoarse<T><<<static_cast<unsigned>((bt.n + 127) / 128), 128, 0, s>>>(
+        ba.lv, bt.d_c, ba.active, bt.d_chol, bt.d_cslots, bt.d_nc, bt.n);
+    for (int j = bt.Dmax - 1; j >= 0; --j) {
+      for (const BatchGroup& g : bt.pr[j]) blaunch_transfer<DIM, T>(nb, g, false, pm, s);
+      for (const BatchGroup& g : bt.sw[j])
+        if (g.B == 27) blaunch_sweep_pair_2d_f32(nb, g, amc, kSelT, kSelU, s);
+      for (int k = 0; k < 2; ++k)
+        for (const BatchGroup& g : bt.sw[j])
+          if (g.B != 27) blaunch_sweep<DIM, T>(nb, g, kJacobi, amc, k == 0 ? kSelU : kSelT, k == 0 ? kSelT : kSelU, s);
+    }
+    return true;
+  }
+  return false;
+}
+
 template <int DIM, typename T>
 void emit_cycle(Batch& bt, const BatchArgs<T>& ba, int amc, int pm, bool first_done, cudaStream_t s) {
+  if (!first_done && emit_paired_cycle<DIM, T>(bt, ba, amc, pm, s)) return;
   BatchArgs<T> nb = ba;
   nb.partial = nullptr;
   for (int j = 0; j < bt.Dmax; ++j) {
