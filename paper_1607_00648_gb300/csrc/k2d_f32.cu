@@ -11,14 +11,18 @@ void launch_sweep_pair_2d_f32(SweepArgs<float> a, int amode, cudaStream_t s) {
   // slab depth: whole bricks where they fill the GPU, thinner slabs on small levels (the
   // first sweep's ring costs (R + 2) (B + 2) / (R B) of a slab's work)
   const int64_t nb = a.L.n_bricks;
-  const int R = nb >= 152 ? 27 : (nb * 3 >= 152 ? 9 : 3);
+  const int B = a.L.B;  // 27, or 9 (2D level 2)
+  const int R = B == 9 ? (nb >= 152 ? 9 : 3) : (nb >= 152 ? 27 : (nb * 3 >= 152 ? 9 : 3));
   a.R = R;
-  const dim3 grid(static_cast<unsigned>(nb), static_cast<unsigned>(27 / R));
-#define MG_SP(AM)                                                            \
-  do {                                                                       \
-    if (R == 27) launch_pdl(k_sweep_pair<float, AM, 27>, grid, 256, 0, s, a); \
-    else if (R == 9) launch_pdl(k_sweep_pair<float, AM, 9>, grid, 256, 0, s, a); \
-    else launch_pdl(k_sweep_pair<float, AM, 3>, grid, 256, 0, s, a);         \
+  const dim3 grid(static_cast<unsigned>(nb), static_cast<unsigned>(B / R));
+#define MG_SP(AM)                                                                      \
+  do {                                                                                 \
+    if (B == 9) {                                                                      \
+      if (R == 9) launch_pdl(k_sweep_pair<float, AM, 9, 9>, grid, 256, 0, s, a);          \
+      else launch_pdl(k_sweep_pair<float, AM, 3, 9>, grid, 256, 0, s, a);                 \
+    } else if (R == 27) launch_pdl(k_sweep_pair<float, AM, 27>, grid, 256, 0, s, a);       \
+    else if (R == 9) launch_pdl(k_sweep_pair<float, AM, 9>, grid, 256, 0, s, a);           \
+    else launch_pdl(k_sweep_pair<float, AM, 3>, grid, 256, 0, s, a);                       \
   } while (0)
   if (amode == 2) MG_SP(2);
   else if (amode == 3) MG_SP(3);

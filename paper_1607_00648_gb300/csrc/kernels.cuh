@@ -744,7 +744,7 @@ template <int DIM, typename T>
 void launch_sweep(SweepArgs<T> a, int op, int amode, cudaStream_t s);
 
 // two damped Jacobi sweeps a.u -> a.out in one launch (sweep_pair.cuh): 2D FP32 levels
-// of brick edge 27; amode 0, 2 or 3
+// of brick edge 27 or 9; amode 0, 2 or 3
 void launch_sweep_pair_2d_f32(SweepArgs<float> a, int amode, cudaStream_t s);
 // the same for FP64 hierarchies (coarse levels: amode 0 or 1, omega / diag(A) in a.dinv)
 void launch_sweep_pair_2d_f64(SweepArgs<double> a, int amode, cudaStream_t s);

@@ -1115,12 +1115,12 @@ static T* lvec(Hier& H, int l, int which) {  // 0 u, 1 b, 2 r, 3 t
   }
 }
 
-// V-cycle smoothing of a 2D level of brick edge 27 (damped Jacobi, no anisotropy pass): nu
+// V-cycle smoothing of a 2D level of brick edge 27 or 9 (damped Jacobi, no anisotropy pass): nu
 // sweeps from the iterate in cur, two per launch where nu allows (launch_sweep_pair_2d_*,
 // bit for bit two sweeps); returns the buffer holding the result
 static bool pair_smoothing(const Hier& H, int l) {
-  return H.dim == 2 && H.lv[l].d.B == 27 && H.opt.smoother == MG_SMOOTH_JACOBI && !(H.tensor && l == H.L) &&
-         !(H.fmt == 4 && l < H.top);
+  return H.dim == 2 && (H.lv[l].d.B == 27 || H.lv[l].d.B == 9) && H.opt.smoother == MG_SMOOTH_JACOBI &&
+         !(H.tensor && l == H.L) && !(H.fmt == 4 && l < H.top);
 }
 
 template <typename T>

@@ -78,9 +78,47 @@ __device__ __forceinline__ double pair_update_f64(const SweepArgs<double>& a, co
   return fma(a.dinv[slot], t, (1.0 - a.omega) * u0);
 }
 
-template <typename T, int AMODE, int R>
+// brick edge 9 (2D level 2): the operations of the generic sweep_item in its order
+// (off-diagonal part and diagonal apart, the deltas into them, then the update), with
+// omega / D from the setup where the hierarchy stores it (FP64)
+template <typename T, int AMODE>
+__device__ __forceinline__ T pair_update_gen(const SweepArgs<T>& a, const T* c, int ws, const T* ce, int wc,
+                                             int64_t slot, int64_t plane_base, uint8_t vf, T bv) {
+  const T u0 = c[0];
+  if (!is_dof(vf)) return (vf & MG_V_HANGING) ? u0 : T(0);
+  const T e_sw = ce[-wc - 1], e_se = ce[-wc], e_nw = ce[-1], e_ne = ce[0];
+  const T sW = e_sw + e_nw, sE = e_se + e_ne, sS = e_sw + e_se, sN = e_nw + e_ne;
+  const T sC = sW + sE;
+  T a1 = sW * c[-1];
+  a1 = fma(sE, c[1], a1);
+  a1 = fma(sS, c[-ws], a1);
+  a1 = fma(sN, c[ws], a1);
+  T a2 = e_sw * c[-ws - 1];
+  a2 = fma(e_se, c[-ws + 1], a2);
+  a2 = fma(e_nw, c[ws - 1], a2);
+  a2 = fma(e_ne, c[ws + 1], a2);
+  const T k0 = static_cast<T>(elem_k(2, 0)), k1 = static_cast<T>(elem_k(2, 1)), k2 = static_cast<T>(elem_k(2, 2));
+  T D = k0 * sC;
+  T off = fma(k1, a1, k2 * a2);
+  const uint64_t akey = AMODE != 0 ? delta_row<AMODE>(a.ascale, slot) : 0;
+  if (AMODE != 0 && delta_row_live<AMODE>(akey)) {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const T d = load_delta<AMODE, T>(a.ahat, a.ascale, plane_base + static_cast<int64_t>(k) * a.L.S, slot, k, akey,
+                                       a_lo_off<AMODE>(a.L, 9));
+      if (k == 4)
+        D += d;
+      else
+        off = fma(d, c[(k % 3 - 1) + ws * (k / 3 - 1)], off);
+    }
+  }
+  if (a.dinv) return fma(a.dinv[slot], bv - off, (T(1) - a.omega) * u0);
+  const T r = bv - fma(D, u0, off);
+  return fma(a.omega * r, recip_nr(D), u0);
+}
+
+template <typename T, int AMODE, int R, int B = 27>
 __device__ __forceinline__ void sweep_pair_item(const SweepArgs<T>& a, int64_t brick, int slab) {
-  constexpr int B = 27;
   constexpr int WU = B + 4, HU = R + 4;  // u: columns -2 .. B + 1, rows z0 - 2 .. z0 + R + 1
   constexpr int WE = B + 3, HE = R + 3;  // cells: lower corners -2 .. B, z0 - 2 .. z0 + R
   constexpr int W1 = B + 2, H1 = R + 2;  // first sweep: columns -1 .. B, rows z0 - 1 .. z0 + R
@@ -120,7 +158,10 @@ __device__ __forceinline__ void sweep_pair_item(const SweepArgs<T>& a, int64_t b
       const int64_t slot = nb * L.S + li;
       const uint8_t vf = L.vflags[slot];
       const T bv = is_dof(vf) ? a.b[slot] : T(0);
-      if constexpr (std::is_same<T, double>::value)
+      if constexpr (B != 27)
+        v = pair_update_gen<T, AMODE>(a, su + (cy + 1) * WU + cx + 1, WU, se + (cy + 1) * WE + cx + 1, WE, slot,
+                                      nb * 9 * L.S + li, vf, bv);
+      else if constexpr (std::is_same<T, double>::value)
         v = pair_update_f64<AMODE>(a, su + (cy + 1) * WU + cx + 1, WU, se + (cy + 1) * WE + cx + 1, WE, slot,
                                    nb * 9 * L.S + li, vf, bv);
       else
@@ -138,7 +179,10 @@ __device__ __forceinline__ void sweep_pair_item(const SweepArgs<T>& a, int64_t b
     const int64_t slot = base + li;
     const uint8_t vf = L.vflags[slot];
     const T bv = is_dof(vf) ? a.b[slot] : T(0);
-    if constexpr (std::is_same<T, double>::value)
+    if constexpr (B != 27)
+      a.out[slot] = pair_update_gen<T, AMODE>(a, s1 + (yl + 1) * W1 + x + 1, W1, se + (yl + 2) * WE + x + 2, WE, slot,
+                                              brick * 9 * L.S + li, vf, bv);
+    else if constexpr (std::is_same<T, double>::value)
       a.out[slot] = pair_update_f64<AMODE>(a, s1 + (yl + 1) * W1 + x + 1, W1, se + (yl + 2) * WE + x + 2, WE, slot,
                                            brick * 9 * L.S + li, vf, bv);
     else
@@ -147,10 +191,10 @@ __device__ __forceinline__ void sweep_pair_item(const SweepArgs<T>& a, int64_t b
   }
 }
 
-template <typename T, int AMODE, int R>
+template <typename T, int AMODE, int R, int B = 27>
 __global__ void __launch_bounds__(256) k_sweep_pair(SweepArgs<T> a) {
   pdl_enter();
-  sweep_pair_item<T, AMODE, R>(a, blockIdx.x, blockIdx.y);
+  sweep_pair_item<T, AMODE, R, B>(a, blockIdx.x, blockIdx.y);
 }
 
 }  // namespace mg
