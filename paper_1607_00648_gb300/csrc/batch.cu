@@ -238,7 +238,7 @@ mg_status make_groups(Batch& bt, std::map<std::pair<int, int>, std::vector<int4>
   return MG_OK;
 }
 
-// Paired smoothing (FP32 V(2,2) cycles, 2D): the groups of brick edge 27 smooth with two
+// Paired smoothing (FP32 V(2,2) cycles, 2D): the groups of brick edge 27 and 9 smooth with two
 // sweeps per launch, u -> t before the coarse correction (the residual reads t, the
 // prolongation adds into t) and t -> u after it; the other groups sweep one at a time.
 template <int DIM, typename T>
@@ -250,12 +250,12 @@ static bool emit_paired_cycle(Batch& bt, const BatchArgs<T>& ba, int amc, int pm
     nb.pair_t = 1;
     for (int j = 0; j < bt.Dmax; ++j) {
       for (const BatchGroup& g : bt.sw[j])
-        if (g.B == 27) blaunch_sweep_pair_2d_f32(nb, g, amc, kSelU, kSelT, s);
+        if (g.B == 27 || g.B == 9) blaunch_sweep_pair_2d_f32(nb, g, amc, kSelU, kSelT, s);
       for (int k = 0; k < 2; ++k)
         for (const BatchGroup& g : bt.sw[j])
-          if (g.B != 27) blaunch_sweep<DIM, T>(nb, g, kJacobi, amc, k == 0 ? kSelU : kSelT, k == 0 ? kSelT : kSelU, s);
+          if (g.B != 27 && g.B != 9) blaunch_sweep<DIM, T>(nb, g, kJacobi, amc, k == 0 ? kSelU : kSelT, k == 0 ? kSelT : kSelU, s);
       for (const BatchGroup& g : bt.sw[j])
-        blaunch_sweep<DIM, T>(nb, g, kResidual, amc, g.B == 27 ? kSelT : kSelU, kSelR, s);
+        blaunch_sweep<DIM, T>(nb, g, kResidual, amc, (g.B == 27 || g.B == 9) ? kSelT : kSelU, kSelR, s);
       for (const BatchGroup& g : bt.rs[j]) blaunch_transfer<DIM, T>(nb, g, true, pm, s);
     }
     k_bcoarse<T><<<static_cast<unsigned>((bt.n + 127) / 128), 128, 0, s>>>(
@@ -263,10 +263,10 @@ static bool emit_paired_cycle(Batch& bt, const BatchArgs<T>& ba, int amc, int pm
     for (int j = bt.Dmax - 1; j >= 0; --j) {
       for (const BatchGroup& g : bt.pr[j]) blaunch_transfer<DIM, T>(nb, g, false, pm, s);
       for (const BatchGroup& g : bt.sw[j])
-        if (g.B == 27) blaunch_sweep_pair_2d_f32(nb, g, amc, kSelT, kSelU, s);
+        if (g.B == 27 || g.B == 9) blaunch_sweep_pair_2d_f32(nb, g, amc, kSelT, kSelU, s);
       for (int k = 0; k < 2; ++k)
         for (const BatchGroup& g : bt.sw[j])
-          if (g.B != 27) blaunch_sweep<DIM, T>(nb, g, kJacobi, amc, k == 0 ? kSelU : kSelT, k == 0 ? kSelT : kSelU, s);
+          if (g.B != 27 && g.B != 9) blaunch_sweep<DIM, T>(nb, g, kJacobi, amc, k == 0 ? kSelU : kSelT, k == 0 ? kSelT : kSelU, s);
     }
     return true;
   }

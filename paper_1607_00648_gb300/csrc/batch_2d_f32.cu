@@ -7,7 +7,7 @@
 MG_BATCH_INSTANTIATE(2, float)
 
 namespace mg {
-template <int AMC>
+template <int AMC, int B>
 __global__ void __launch_bounds__(256) k_bsweep_pair(BatchArgs<float> ba, const int4* items, int src, int dst) {
   const int4 it = items[blockIdx.x];
   const int p = it.x, l = it.y;
@@ -23,18 +23,24 @@ __global__ void __launch_bounds__(256) k_bsweep_pair(BatchArgs<float> ba, const 
   a.ahat = P.ahat;
   a.ascale = P.ascale;
   a.omega = ba.omega;
-  a.R = 27;
+  a.R = B;  // whole bricks
   if (finest)
-    sweep_pair_item<float, 0, 27>(a, it.z, 0);
+    sweep_pair_item<float, 0, B, B>(a, it.z, 0);
   else
-    sweep_pair_item<float, AMC, 27>(a, it.z, 0);
+    sweep_pair_item<float, AMC, B, B>(a, it.z, 0);
 }
 
 void blaunch_sweep_pair_2d_f32(const BatchArgs<float>& ba, const BatchGroup& g, int amc, int src, int dst,
                                cudaStream_t s) {
   const unsigned grid = static_cast<unsigned>(g.count);
-  if (amc == 2) k_bsweep_pair<2><<<grid, 256, 0, s>>>(ba, g.items, src, dst);
-  else if (amc == 3) k_bsweep_pair<3><<<grid, 256, 0, s>>>(ba, g.items, src, dst);
-  else k_bsweep_pair<0><<<grid, 256, 0, s>>>(ba, g.items, src, dst);
+#define MG_BP(B)                                                                    \
+  do {                                                                              \
+    if (amc == 2) k_bsweep_pair<2, B><<<grid, 256, 0, s>>>(ba, g.items, src, dst);  \
+    else if (amc == 3) k_bsweep_pair<3, B><<<grid, 256, 0, s>>>(ba, g.items, src, dst); \
+    else k_bsweep_pair<0, B><<<grid, 256, 0, s>>>(ba, g.items, src, dst);           \
+  } while (0)
+  if (g.B == 9) MG_BP(9);
+  else MG_BP(27);
+#undef MG_BP
 }
 }  // namespace mg

@@ -22,7 +22,7 @@ struct BatchArgs {
   double* partial;       // per item of a norm phase (nullable)
   T omega;
   // paired smoothing of a lockstep FP32 cycle: the iterate of 2D levels of brick edge 27
-  // sits in t between pre- and post-smoothing, so the prolongation adds into t there
+  // or 9 sits in t between pre- and post-smoothing, so the prolongation adds into t there
   int pair_t = 0;
 };
 
@@ -203,7 +203,7 @@ __global__ void __launch_bounds__(kBlock) k_bprolong(BatchArgs<T> ba, const int4
   const PLevel<T>& F = ba.lv[p * kMaxLevels + lf];
   const int64_t fs = static_cast<int64_t>(it.z) * kBlock + threadIdx.x;
   if (fs >= F.d.n_slots) return;
-  T* uf = (DIM == 2 && ba.pair_t && F.d.B == 27) ? F.t : (lf == ba.Lp[p] ? ba.ufin[p] : F.u);
+  T* uf = (DIM == 2 && ba.pair_t && (F.d.B == 27 || F.d.B == 9)) ? F.t : (lf == ba.Lp[p] ? ba.ufin[p] : F.u);
   prolong_one<DIM, T, PM, BC, BF>(C.d, F.d, C.u, uf, C.phat, C.pscale, fs);
 }
 
@@ -223,7 +223,7 @@ template <int DIM, typename T>
 void blaunch_sweep(const BatchArgs<T>& ba, const BatchGroup& g, int op, int amc, int src, int dst, cudaStream_t s);
 
 // two Jacobi sweeps src -> dst per item (whole bricks) of a 2D FP32 group of brick edge 27
-// (sweep_pair.cuh; bit for bit two k_bsweep_col sweeps)
+// or 9 (sweep_pair.cuh; bit for bit two k_bsweep_col / k_bsweep sweeps)
 void blaunch_sweep_pair_2d_f32(const BatchArgs<float>& ba, const BatchGroup& g, int amc, int src, int dst,
                                cudaStream_t s);
 
