@@ -1,15 +1,16 @@
-// Two damped Jacobi sweeps in one launch (2D, brick edge 27: the FP32 cycles of the mixed
-// path and the coarse levels of FP64 cycles).  The levels of an FP32 V-cycle are L2-resident, so a sweep costs its launch and
-// the dependency on its predecessor (a round trip through L2), not bandwidth; smoothing
-// with nu = 2 therefore pays that latency twice per level and side.  Here one CTA per
-// (brick, slab of R rows) stages u with a two-vertex halo and the cell coefficients with
-// a two-cell halo, forms the first sweep on the slab and a one-vertex ring around it in
-// shared memory (the ring's b, flags and stored deltas come from the neighbouring
-// bricks), and the second sweep of the slab from it.  Every vertex update is the
-// arithmetic of the single-sweep kernel it replaces (FP32: sweep2c_item's stencil2, the
-// deltas in entry order, u + omega r / D; FP64: sweep2f_item's), so the result is bit for
-// bit that of two separate sweeps.  Levels
-// with hanging vertices, block smoothing and the anisotropy pass keep separate sweeps.
+// Two damped Jacobi sweeps in one launch (2D levels of brick edge 27 and 9: the FP32
+// cycles of the mixed path, the coarse levels of FP64 cycles, lockstep FP32 batches).
+// These levels are L2-resident, so a sweep costs its launch and the dependency on its
+// predecessor (a round trip through L2), not bandwidth; smoothing with nu = 2 therefore
+// pays that latency twice per level and side.  Here one CTA per (brick, slab of R rows)
+// stages u with a two-vertex halo and the cell coefficients with a two-cell halo, forms
+// the first sweep on the slab and a one-vertex ring around it in shared memory (the
+// ring's b, flags and stored deltas come from the neighbouring bricks), and the second
+// sweep of the slab from it.  Every vertex update is the arithmetic of the single-sweep
+// kernel it replaces (brick edge 27, FP32: sweep2c_item's stencil2, the deltas in entry
+// order, u + omega r / D; FP64: sweep2f_item's; brick edge 9: the generic sweep_item's),
+// so the result is bit for bit that of two separate sweeps.  Levels with hanging
+// vertices, block smoothing and the anisotropy pass keep separate sweeps.
 #pragma once
 
 #include "sweep_fast.cuh"
